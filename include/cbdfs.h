@@ -1,0 +1,250 @@
+/*
+ * cbdfs.h -- C ABI of the batched cost-bounded DFS heuristic library (sm_103a).
+ *
+ * The library evaluates heuristics for batches of search states on one GPU, the way the
+ * batch-processing thread of the paper's Batch CB-DFS does (arXiv 2507.11916, section
+ * "SingleGPU Batch CB-DFS": copy the batch to the GPU, evaluate h_M, return the values),
+ * and runs the CPU side of that search (Algorithms 1-3) with C++ worker threads.
+ *
+ * Conventions shared by every call:
+ *   - The return value is a status (cbdfs_status); results come back through out-pointers.
+ *     On failure a message is available from cbdfs_last_error() in the calling thread.
+ *   - "Host" pointers are ordinary CPU memory owned by the caller; the library copies from
+ *     them before the call returns (page-locked memory makes those copies faster).
+ *     "Device" pointers are CUDA global memory on the context's device, owned by the caller.
+ *     The library owns everything it allocates (weights, tables, scratch, streams).
+ *   - Packed states (the ABI's state format):
+ *       sliding-tile puzzle (CBDFS_DOM_STP3 3x3, CBDFS_DOM_STP4 4x4): one uint64 per state;
+ *         nibble p (bits 4p..4p+3) = tile on cell p, 0 = blank; the goal has tile t on
+ *         cell t.  Blank moves: 0 up, 1 left, 2 right, 3 down.
+ *       Rubik's cube (CBDFS_DOM_RC3): two uint64 per state.  Word 0: for corner cubie
+ *         c = 0..7 the 5-bit field (bits 5c..) slot*3 + twist; word 1: for edge cubie
+ *         e = 0..11 the field slot*2 + flip.  Corner slots URF UFL ULB UBR DFR DLF DBL DRB,
+ *         edge slots UR UF UL UB DR DF DL DB FR FL BL BR; cubie i is home in slot i.
+ *         Move m = 3*face + (quarter turns - 1), faces U R F D L B, clockwise turns.
+ *   - Heuristic values are uint8; the goal state always gets h = 0.
+ *   - A context is bound to one device.  heur_submit_batch and cbdfs_solve may be called
+ *     from several threads at once on one context; the other calls may not.
+ */
+#ifndef CBDFS_H
+#define CBDFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CBDFS_OK = 0,
+    CBDFS_EINVAL = -1,      /* bad argument: null pointer, unknown id, size out of range */
+    CBDFS_ENOMEM = -2,      /* device or host allocation failed, or the memory budget is spent */
+    CBDFS_ETIMEDOUT = -3,   /* a bounded wait (host or device) ran out */
+    CBDFS_EDEVICE = -4,     /* a CUDA call failed; the message names it */
+    CBDFS_ECANCELED = -5,   /* cbdfs_cancel() stopped the call */
+    CBDFS_ENOTFOUND = -6    /* the search space holds no solution within the limits */
+} cbdfs_status;
+
+typedef enum { CBDFS_DOM_STP3 = 0, CBDFS_DOM_STP4 = 1, CBDFS_DOM_RC3 = 2 } cbdfs_domain;
+typedef enum { CBDFS_PREC_FP32 = 0, CBDFS_PREC_BF16 = 1, CBDFS_PREC_FP8 = 2 } cbdfs_prec;
+typedef enum { CBDFS_HEAD_REGRESSION = 0, CBDFS_HEAD_CLASSIFIER = 1 } cbdfs_head;
+typedef enum { CBDFS_ALGO_IDA = 0, CBDFS_ALGO_BTS = 1 } cbdfs_algo;
+
+/* Built-in heuristic ids (network and PDB ids from the load calls are >= 0). */
+#define CBDFS_HEUR_ZERO (-1)    /* h = 0 */
+#define CBDFS_HEUR_MD (-2)      /* Manhattan distance, sliding-tile domains only */
+
+typedef struct cbdfs_ctx cbdfs_ctx;
+
+typedef struct {
+    int device;             /* CUDA device ordinal */
+    size_t mem_budget;      /* bytes of device memory the context may allocate; 0 = no limit */
+    uint32_t max_batch;     /* largest n one heuristic call accepts (sizes the scratch); 0 = 65536 */
+    int n_slots;            /* concurrent evaluation slots (stream + scratch each); 0 = 4 */
+} cbdfs_config;
+
+/* Create a context on cfg->device.  *out receives it.  Errors: EINVAL, EDEVICE, ENOMEM. */
+int cbdfs_create(const cbdfs_config *cfg, cbdfs_ctx **out);
+/* Free everything the context owns.  Safe on NULL. */
+void cbdfs_destroy(cbdfs_ctx *ctx);
+/* The last failure message of the calling thread ("" if none).  Valid until its next call. */
+const char *cbdfs_last_error(void);
+/* Device memory the context holds now, in bytes. */
+size_t cbdfs_mem_used(const cbdfs_ctx *ctx);
+
+/* ---------------------------------------------------------------------------------------
+ * Network heuristic h_M (paper: "Experimental Setup" -- a classifier and a regression
+ * network, evaluated in batches; Algorithm 3 adds TensorRepresentation(s) to the batch).
+ * The network input is the one-hot encoding of the packed state:
+ *   STP with N cells: index tile*N + cell (blank included), width N*N (81 or 256);
+ *   RC: corner cubie c at c*24 + (slot*3 + twist), edge e at 192 + e*24 + (slot*2 + flip),
+ *   width 480.
+ * Layers: z_l = W_l a_{l-1} + b_l, ReLU after every layer but the last.  The last layer
+ * always runs in FP32.  With CBDFS_PREC_BF16 / _FP8 the hidden layers run on the tensor
+ * cores with FP32 accumulation (FP8: E4M3, per-tensor weight scale amax/448 and the given
+ * static activation scales).
+ * Integer h (the fused epilogue):
+ *   regression: h = max(rint(y), 0) (round half to even), max'ed with Manhattan distance
+ *               when max_with_md != 0, clamped to 255;
+ *   classifier: h = argmax over the outputs (lowest index on ties), max'ed with Manhattan
+ *               distance when max_with_md != 0.
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+    int domain;                     /* cbdfs_domain */
+    int n_layers;                   /* L >= 2 */
+    const int *dims;                /* L+1 widths; dims[0] must equal the domain's one-hot width */
+    const float *const *weights;    /* host, L pointers; layer l is dims[l+1] x dims[l], row-major */
+    const float *const *biases;     /* host, L pointers of dims[l+1] floats */
+    int prec;                       /* cbdfs_prec */
+    int head;                       /* cbdfs_head */
+    int max_with_md;                /* STP only */
+    const float *act_scales;        /* FP8 only: L-1 activation scales (host), else NULL */
+} cbdfs_net_desc;
+
+/* Copy a network into device memory.  Weights are rounded there to the precision (FP32
+ * master values -> BF16 round-to-nearest-even, or -> E4M3 with the scale).  *heur_id
+ * receives its id.  Hidden widths must be multiples of 128 for BF16/FP8.
+ * Errors: EINVAL (shape), ENOMEM, EDEVICE. */
+int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id);
+
+/* ---------------------------------------------------------------------------------------
+ * Additive pattern database (paper: "Background, Heuristics": abstraction distances are
+ * admissible; Experimental Setup uses additive tile PDBs for the STP).  Pattern q lists
+ * k[q] tiles; its table is indexed by the lexicographic rank of the cells holding those
+ * tiles (in list order) among all k-permutations of the N cells:
+ *   rank = sum_i d_i * (N-1-i)!/(N-k)!,  d_i = cell_i - #{j < i : cell_j < cell_i}.
+ * h = sum over patterns of table_q[rank_q].
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+    int domain;                     /* CBDFS_DOM_STP3 or CBDFS_DOM_STP4 */
+    int n_patterns;                 /* 1..4 */
+    const int *k;                   /* tiles per pattern */
+    const int *tiles;               /* concatenated tile lists */
+    const uint8_t *const *tables;   /* host tables, N!/(N-k)! entries each; NULL: build them
+                                       on the GPU with pdb_build */
+} cbdfs_pdb_desc;
+
+/* Register an additive PDB (copying the tables to the device, or building them there).
+ * *heur_id receives its id.  Errors: EINVAL, ENOMEM, EDEVICE. */
+int cbdfs_pdb_load(cbdfs_ctx *ctx, const cbdfs_pdb_desc *d, int *heur_id);
+
+/* Build one pattern's table on the GPU by breadth-first search over the abstract space
+ * (pattern-tile cells plus the blank cell; a blank move that displaces a pattern tile costs
+ * 1, any other costs 0; the entry is the least distance over blank cells).  table_out
+ * (host, cap bytes) receives N!/(N-k)! entries; *entries receives that count.
+ * Errors: EINVAL (cap too small, bad tiles), ENOMEM, EDEVICE. */
+int pdb_build(cbdfs_ctx *ctx, int domain, const int *pattern_tiles, int k, uint8_t *table_out,
+              size_t cap, size_t *entries);
+
+/* ---------------------------------------------------------------------------------------
+ * Batched heuristic evaluation with the bound test (Algorithm 3: a node is expanded when
+ * f = g + h is within the bound; the smallest f above the bound is the next IDA*
+ * threshold, "lowest unexpanded f-cost").
+ *   states  n packed states (1 or 2 words each, see above)
+ *   g       n path costs (uint8)
+ *   bound   the cost bound
+ *   h_out   n heuristic values
+ *   mask_out ceil(n/32) words: bit i%32 of word i/32 is set iff g_i + h_i <= bound
+ *   minf_out the least g_i + h_i above the bound, 0xFFFFFFFF if none
+ *   y_out   optional (may be NULL): the raw FP32 network outputs, n x dims[L] row-major
+ *           (ignored for PDB / built-in heuristics)
+ * n = 0 is allowed (mask nothing, minf 0xFFFFFFFF).  n > max_batch: EINVAL.
+ * ------------------------------------------------------------------------------------- */
+
+/* Host buffers; returns when the results are in h_out/mask_out/minf_out. */
+int heur_submit_batch(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *states,
+                      const uint8_t *g, uint32_t bound, uint32_t n, uint8_t *h_out,
+                      uint32_t *mask_out, uint32_t *minf_out, float *y_out);
+
+/* Device buffers, enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream);
+ * returns without waiting.  All device-buffer calls on one context share one set of
+ * activation scratch, and the library orders each call after the previous one on the GPU.
+ * The call may be captured into a CUDA graph (the library then leaves the ordering to the
+ * graph): replays of such a graph must not overlap other device-buffer calls on the same
+ * context.  Errors are those detected before enqueueing; a device-side timeout sets the
+ * flag read by cbdfs_device_status(). */
+int heur_eval_device(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_states,
+                     const uint8_t *d_g, uint32_t bound, uint32_t n, uint8_t *d_h,
+                     uint32_t *d_mask, uint32_t *d_minf, float *d_y, void *stream);
+
+/* Like heur_eval_device, and then waits: stage_ms[i] receives the device time of the i-th
+ * kernel of the pipeline (network: layer 1 .. layer L-1, then the head; PDB / built-in: the
+ * one kernel), measured with CUDA events recorded between the launches on `stream`.
+ * *n_stages receives the number of kernels (at most cap are written).  The pipeline's
+ * results are written as for heur_eval_device.  Errors: those of heur_eval_device, EDEVICE. */
+int cbdfs_eval_profile(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_states,
+                       const uint8_t *d_g, uint32_t bound, uint32_t n, uint8_t *d_h,
+                       uint32_t *d_mask, uint32_t *d_minf, void *stream, float *stage_ms, int cap,
+                       int *n_stages);
+
+/* Reads and clears the device-side error flag (0 = none; otherwise a code naming the
+ * wait that ran out).  Synchronises the context's device. */
+int cbdfs_device_status(cbdfs_ctx *ctx);
+
+/* ---------------------------------------------------------------------------------------
+ * Domain helpers (product-side domain code; the search uses the same routines).
+ * ------------------------------------------------------------------------------------- */
+
+/* Apply `n` moves to a packed state (words as above).  Returns EINVAL on an illegal STP
+ * move (blank off the board) or a move number out of range. */
+int cbdfs_apply_moves(int domain, const uint64_t *start, const int *moves, int n, uint64_t *out);
+/* Manhattan distance of an STP state (host). */
+int cbdfs_manhattan(int domain, uint64_t state);
+
+/* ---------------------------------------------------------------------------------------
+ * Batch CB-DFS search: IDA* (Algorithm 1) or BTS (Batch BTS enhancements) over C++ worker
+ * threads (Algorithm 2), each round-robining over work_num subtree stacks (Algorithm 3),
+ * with heuristic evaluation batched on the GPU through the slots.
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+    int threads;            /* worker threads (>= 1) */
+    int work_num;           /* subtrees per thread (>= 1) */
+    int d_init;             /* depth of the initial partition (GenerateWork); -1 = automatic */
+    uint32_t batch;         /* target states per GPU batch (<= max_batch) */
+    uint32_t timeout_us;    /* flush a partly filled batch after this long (paper: 4 ms) */
+    int complete_final;     /* finish the iteration that reaches a goal and return the least
+                               goal cost in it (deterministic counts); 0 = stop at the first */
+    int fixed_tree_heur;    /* -1: prune with heur_id; else prune with this heuristic while
+                               still evaluating heur_id on every generated node */
+    uint64_t bts_n0;        /* BTS: initial growth base (paper: 10,000) */
+    int bts_c1, bts_c2;     /* BTS: accept >= c1*N expansions, limit c2*N (0 = 2 and 8) */
+    uint64_t node_limit;    /* stop with ECANCELED after this many expansions; 0 = none */
+    double time_limit_s;    /* stop with ETIMEDOUT after this long; 0 = none */
+} cbdfs_search_cfg;
+
+#define CBDFS_MAX_ITERS 256
+
+typedef struct {
+    int cost;                       /* solution cost (-1 if none) */
+    int path_len;                   /* moves in path[] */
+    int path[256];                  /* moves from the start to the goal */
+    int n_iters;                    /* CB-DFS searches run (IDA* iterations / BTS searches) */
+    int64_t iter_bound[CBDFS_MAX_ITERS];
+    int64_t iter_expanded[CBDFS_MAX_ITERS];
+    int64_t iter_generated[CBDFS_MAX_ITERS];
+    int64_t iter_limit[CBDFS_MAX_ITERS];   /* BTS expansion limit (-1 none) */
+    int iter_cut[CBDFS_MAX_ITERS];         /* BTS: the limit stopped that search */
+    int64_t expanded, generated;    /* totals over all searches */
+    int64_t batches;                /* GPU batches evaluated */
+    int64_t evaluated;              /* states evaluated on the GPU */
+    double seconds;                 /* wall time of the solve */
+    int d_init;                     /* initial partition depth used */
+    int64_t work_items;             /* subtrees in the shared work queue */
+} cbdfs_result;
+
+/* Solve from `start` (packed words).  heur_id: a network, a PDB or a built-in id.
+ * Errors: EINVAL, ENOTFOUND (tree exhausted), ETIMEDOUT, ECANCELED, EDEVICE. */
+int cbdfs_solve(cbdfs_ctx *ctx, int domain, const uint64_t *start, int algo, int heur_id,
+                const cbdfs_search_cfg *cfg, cbdfs_result *out);
+
+/* Fill a search configuration with the defaults documented above. */
+void cbdfs_search_defaults(cbdfs_search_cfg *cfg);
+
+/* Ask running calls on ctx to stop (they return ECANCELED). */
+void cbdfs_cancel(cbdfs_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CBDFS_H */

@@ -1,0 +1,296 @@
+"""Python binding of libcbdfs.so, the batched CB-DFS heuristic library for sm_103a.
+
+Argument marshalling only: every function forwards to the C entry point of the same name
+declared in include/cbdfs.h, and raises CbdfsError when it returns a non-zero status.
+Arrays may be numpy arrays (host) or torch tensors (host or, for heur_eval_device, CUDA).
+There is no fallback: if libcbdfs.so is missing, importing this package fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcbdfs.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run `python paper_2507_11916_b300/build.py`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+def load_builder():
+    """The build module, loaded by path (see build.py)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("_cbdfs_build", os.path.join(HERE, "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+# ---- constants (cbdfs.h) ----
+CBDFS_OK, CBDFS_EINVAL, CBDFS_ENOMEM, CBDFS_ETIMEDOUT = 0, -1, -2, -3
+CBDFS_EDEVICE, CBDFS_ECANCELED, CBDFS_ENOTFOUND = -4, -5, -6
+DOM_STP3, DOM_STP4, DOM_RC3 = 0, 1, 2
+PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
+HEAD_REGRESSION, HEAD_CLASSIFIER = 0, 1
+ALGO_IDA, ALGO_BTS = 0, 1
+HEUR_ZERO, HEUR_MD = -1, -2
+MAX_ITERS = 256
+
+_STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ETIMEDOUT", -4: "EDEVICE", -5: "ECANCELED",
+           -6: "ENOTFOUND"}
+
+
+class CbdfsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("mem_budget", ctypes.c_size_t),
+                ("max_batch", ctypes.c_uint32), ("n_slots", ctypes.c_int)]
+
+
+class NetDesc(ctypes.Structure):
+    _fields_ = [("domain", ctypes.c_int), ("n_layers", ctypes.c_int),
+                ("dims", ctypes.POINTER(ctypes.c_int)),
+                ("weights", ctypes.POINTER(ctypes.POINTER(ctypes.c_float))),
+                ("biases", ctypes.POINTER(ctypes.POINTER(ctypes.c_float))),
+                ("prec", ctypes.c_int), ("head", ctypes.c_int), ("max_with_md", ctypes.c_int),
+                ("act_scales", ctypes.POINTER(ctypes.c_float))]
+
+
+class PdbDesc(ctypes.Structure):
+    _fields_ = [("domain", ctypes.c_int), ("n_patterns", ctypes.c_int),
+                ("k", ctypes.POINTER(ctypes.c_int)), ("tiles", ctypes.POINTER(ctypes.c_int)),
+                ("tables", ctypes.POINTER(ctypes.c_void_p))]
+
+
+class SearchCfg(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int), ("work_num", ctypes.c_int), ("d_init", ctypes.c_int),
+                ("batch", ctypes.c_uint32), ("timeout_us", ctypes.c_uint32),
+                ("complete_final", ctypes.c_int), ("fixed_tree_heur", ctypes.c_int),
+                ("bts_n0", ctypes.c_uint64), ("bts_c1", ctypes.c_int), ("bts_c2", ctypes.c_int),
+                ("node_limit", ctypes.c_uint64), ("time_limit_s", ctypes.c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("cost", ctypes.c_int), ("path_len", ctypes.c_int), ("path", ctypes.c_int * 256),
+                ("n_iters", ctypes.c_int),
+                ("iter_bound", ctypes.c_int64 * MAX_ITERS),
+                ("iter_expanded", ctypes.c_int64 * MAX_ITERS),
+                ("iter_generated", ctypes.c_int64 * MAX_ITERS),
+                ("iter_limit", ctypes.c_int64 * MAX_ITERS),
+                ("iter_cut", ctypes.c_int * MAX_ITERS),
+                ("expanded", ctypes.c_int64), ("generated", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("evaluated", ctypes.c_int64),
+                ("seconds", ctypes.c_double), ("d_init", ctypes.c_int),
+                ("work_items", ctypes.c_int64)]
+
+
+_vp, _u64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)
+_lib.cbdfs_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(_vp)]
+_lib.cbdfs_destroy.argtypes = [_vp]
+_lib.cbdfs_destroy.restype = None
+_lib.cbdfs_last_error.restype = ctypes.c_char_p
+_lib.cbdfs_mem_used.argtypes = [_vp]
+_lib.cbdfs_mem_used.restype = ctypes.c_size_t
+_lib.cbdfs_net_load.argtypes = [_vp, ctypes.POINTER(NetDesc), ctypes.POINTER(ctypes.c_int)]
+_lib.cbdfs_pdb_load.argtypes = [_vp, ctypes.POINTER(PdbDesc), ctypes.POINTER(ctypes.c_int)]
+_lib.pdb_build.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _vp,
+                           ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+_lib.heur_submit_batch.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint32,
+                                   ctypes.c_uint32, _vp, _vp, _vp, _vp]
+_lib.heur_eval_device.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint32,
+                                  ctypes.c_uint32, _vp, _vp, _vp, _vp, _vp]
+_lib.cbdfs_device_status.argtypes = [_vp]
+_lib.cbdfs_eval_profile.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint32,
+                                    ctypes.c_uint32, _vp, _vp, _vp, _vp,
+                                    ctypes.POINTER(ctypes.c_float), ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int)]
+_lib.cbdfs_apply_moves.argtypes = [ctypes.c_int, _u64p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                   _u64p]
+_lib.cbdfs_manhattan.argtypes = [ctypes.c_int, ctypes.c_uint64]
+_lib.cbdfs_solve.argtypes = [_vp, ctypes.c_int, _u64p, ctypes.c_int, ctypes.c_int,
+                             ctypes.POINTER(SearchCfg), ctypes.POINTER(Result)]
+_lib.cbdfs_search_defaults.argtypes = [ctypes.POINTER(SearchCfg)]
+_lib.cbdfs_search_defaults.restype = None
+_lib.cbdfs_cancel.argtypes = [_vp]
+_lib.cbdfs_cancel.restype = None
+
+# every symbol include/cbdfs.h declares
+EXPORTED = ["cbdfs_create", "cbdfs_destroy", "cbdfs_last_error", "cbdfs_mem_used", "cbdfs_net_load",
+            "cbdfs_pdb_load", "pdb_build", "heur_submit_batch", "heur_eval_device",
+            "cbdfs_device_status", "cbdfs_eval_profile", "cbdfs_apply_moves", "cbdfs_manhattan", "cbdfs_solve",
+            "cbdfs_search_defaults", "cbdfs_cancel"]
+
+
+def _check(status):
+    if status != CBDFS_OK:
+        raise CbdfsError(status, cbdfs_last_error())
+    return status
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def cbdfs_last_error() -> str:
+    return _lib.cbdfs_last_error().decode()
+
+
+def cbdfs_create(device=0, mem_budget=0, max_batch=0, n_slots=0):
+    cfg = Config(device, mem_budget, max_batch, n_slots)
+    h = _vp()
+    _check(_lib.cbdfs_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def cbdfs_destroy(ctx):
+    _lib.cbdfs_destroy(ctx)
+
+
+def cbdfs_mem_used(ctx) -> int:
+    return _lib.cbdfs_mem_used(ctx)
+
+
+def cbdfs_net_load(ctx, domain, weights, biases, prec=PREC_BF16, head=HEAD_REGRESSION,
+                   max_with_md=0, act_scales=None) -> int:
+    Ws = [np.ascontiguousarray(w, dtype=np.float32) for w in weights]
+    bs = [np.ascontiguousarray(b, dtype=np.float32) for b in biases]
+    dims = [Ws[0].shape[1]] + [w.shape[0] for w in Ws]
+    FP = ctypes.POINTER(ctypes.c_float)
+    wp = (FP * len(Ws))(*(w.ctypes.data_as(FP) for w in Ws))
+    bp = (FP * len(bs))(*(b.ctypes.data_as(FP) for b in bs))
+    sc = None
+    if act_scales is not None:
+        sc_arr = np.ascontiguousarray(act_scales, dtype=np.float32)
+        sc = sc_arr.ctypes.data_as(FP)
+    d = NetDesc(domain, len(Ws), (ctypes.c_int * len(dims))(*dims), wp, bp, prec, head,
+                max_with_md, sc)
+    out = ctypes.c_int()
+    _check(_lib.cbdfs_net_load(ctx, ctypes.byref(d), ctypes.byref(out)))
+    return out.value
+
+
+def cbdfs_pdb_load(ctx, domain, patterns, tables=None) -> int:
+    ks = [len(p) for p in patterns]
+    tiles = [t for p in patterns for t in p]
+    tabs = None
+    if tables is not None:
+        tables = [np.ascontiguousarray(t, dtype=np.uint8) for t in tables]
+        tabs = (ctypes.c_void_p * len(tables))(*(t.ctypes.data for t in tables))
+    d = PdbDesc(domain, len(patterns), (ctypes.c_int * len(ks))(*ks),
+                (ctypes.c_int * len(tiles))(*tiles), tabs)
+    out = ctypes.c_int()
+    _check(_lib.cbdfs_pdb_load(ctx, ctypes.byref(d), ctypes.byref(out)))
+    return out.value
+
+
+def pdb_build(ctx, domain, tiles) -> np.ndarray:
+    n = 9 if domain == DOM_STP3 else 16
+    P = 1
+    for i in range(len(tiles)):
+        P *= n - i
+    table = np.empty(P, dtype=np.uint8)
+    entries = ctypes.c_size_t()
+    _check(_lib.pdb_build(ctx, domain, (ctypes.c_int * len(tiles))(*tiles), len(tiles),
+                          table.ctypes.data, table.nbytes, ctypes.byref(entries)))
+    return table[:entries.value]
+
+
+def heur_submit_batch(ctx, heur_id, domain, states, g, bound, want_y=False, n_out=1):
+    """Host arrays in, host arrays out: (h uint8[n], mask uint32[ceil(n/32)], minf[, y])."""
+    states = np.ascontiguousarray(states, dtype=np.uint64)
+    g = np.ascontiguousarray(g, dtype=np.uint8)
+    n = len(g)
+    h = np.empty(n, dtype=np.uint8)
+    mask = np.empty((n + 31) // 32, dtype=np.uint32)
+    minf = np.empty(1, dtype=np.uint32)
+    y = np.empty((n, n_out), dtype=np.float32) if want_y else None
+    _check(_lib.heur_submit_batch(ctx, heur_id, domain, _ptr(states), _ptr(g), bound, n,
+                                  _ptr(h), _ptr(mask), _ptr(minf), _ptr(y)))
+    return (h, mask, int(minf[0]), y) if want_y else (h, mask, int(minf[0]))
+
+
+def heur_eval_device(ctx, heur_id, domain, d_states, d_g, bound, n, d_h, d_mask, d_minf, d_y=None,
+                     stream=None):
+    """Device tensors in and out; enqueued on `stream` (a torch.cuda.Stream or raw handle)."""
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(_lib.heur_eval_device(ctx, heur_id, domain, _ptr(d_states), _ptr(d_g), bound, n,
+                                 _ptr(d_h), _ptr(d_mask), _ptr(d_minf), _ptr(d_y), s))
+
+
+def cbdfs_eval_profile(ctx, heur_id, domain, d_states, d_g, bound, n, d_h, d_mask, d_minf,
+                       stream=None):
+    """Runs the pipeline once and returns the device milliseconds of each of its kernels."""
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    ms = (ctypes.c_float * 16)()
+    k = ctypes.c_int()
+    _check(_lib.cbdfs_eval_profile(ctx, heur_id, domain, _ptr(d_states), _ptr(d_g), bound, n,
+                                   _ptr(d_h), _ptr(d_mask), _ptr(d_minf), s, ms, 16, ctypes.byref(k)))
+    return list(ms[:k.value])
+
+
+def cbdfs_device_status(ctx) -> int:
+    r = _lib.cbdfs_device_status(ctx)
+    if r < 0:
+        _check(r)
+    return r
+
+
+def cbdfs_apply_moves(domain, start, moves):
+    """start: an int (STP) or a pair of ints (RC); returns the same shape."""
+    words = list(start) if isinstance(start, (tuple, list)) else [int(start)]
+    inp = (ctypes.c_uint64 * 2)(*(words + [0] * (2 - len(words))))
+    out = (ctypes.c_uint64 * 2)()
+    mv = (ctypes.c_int * max(1, len(moves)))(*moves)
+    _check(_lib.cbdfs_apply_moves(domain, inp, mv, len(moves), out))
+    return (out[0], out[1]) if domain == DOM_RC3 else out[0]
+
+
+def cbdfs_manhattan(domain, state) -> int:
+    r = _lib.cbdfs_manhattan(domain, ctypes.c_uint64(int(state)))
+    return _check(r) if r < 0 else r
+
+
+def cbdfs_search_defaults() -> dict:
+    c = SearchCfg()
+    _lib.cbdfs_search_defaults(ctypes.byref(c))
+    return {name: getattr(c, name) for name, _ in SearchCfg._fields_}
+
+
+def cbdfs_solve(ctx, domain, start, algo=ALGO_IDA, heur_id=HEUR_MD, partial_ok=False, **cfg) -> dict:
+    """Returns the result as a dict.  With partial_ok, a search stopped by its node or time
+    limit returns its partial counts with "status" set instead of raising."""
+    c = SearchCfg()
+    _lib.cbdfs_search_defaults(ctypes.byref(c))
+    for k, v in cfg.items():
+        if not hasattr(c, k):
+            raise TypeError(f"unknown search option {k}")
+        setattr(c, k, v)
+    words = list(start) if isinstance(start, (tuple, list)) else [int(start)]
+    st = (ctypes.c_uint64 * 2)(*(words + [0] * (2 - len(words))))
+    r = Result()
+    status = _lib.cbdfs_solve(ctx, domain, st, algo, heur_id, ctypes.byref(c), ctypes.byref(r))
+    if not (partial_ok and status in (CBDFS_ETIMEDOUT, CBDFS_ECANCELED)):
+        _check(status)
+    k = min(r.n_iters, MAX_ITERS)
+    return dict(status=status, cost=r.cost, path=list(r.path[:r.path_len]),
+                iters=[(r.iter_bound[i], r.iter_expanded[i], r.iter_generated[i]) for i in range(k)],
+                iter_limit=list(r.iter_limit[:k]), iter_cut=list(r.iter_cut[:k]),
+                n_iters=r.n_iters, expanded=r.expanded, generated=r.generated,
+                batches=r.batches, evaluated=r.evaluated, seconds=r.seconds, d_init=r.d_init,
+                work_items=r.work_items)
+
+
+def cbdfs_cancel(ctx):
+    _lib.cbdfs_cancel(ctx)

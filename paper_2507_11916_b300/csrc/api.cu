@@ -1,0 +1,665 @@
+// api.cu -- the C entry points around the heuristic kernels: context and slots, loading of
+// networks and pattern databases (with the precision conversion), the evaluation
+// pipeline, and the host-buffer / device-buffer evaluation calls.
+#include <cuda_fp8.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace cbdfs {
+
+// kernels defined in the other translation units
+int tc_layer(bool first, int domain, bool fp8, bool out_fp8, int bn, const CUtensorMap &tmA,
+             const CUtensorMap &tmB, const uint64_t *states, uint32_t n, uint32_t rows_pad, int K,
+             int N, const float *bias, void *out, float acc_scale, float out_qscale, int *err,
+             cudaStream_t st);
+int first_gather(int domain, const uint64_t *states, uint32_t n, const float *W1T, const float *b1,
+                 int H, float *out, cudaStream_t st);
+int sgemm_relu(const float *A, const float *W, const float *b, float *C, int M, int N, int K,
+               int relu, cudaStream_t st);
+int head(bool bf16_in, int domain, int head_kind, const void *act, int K, int C, const float *W,
+         const float *b, const uint64_t *states, const uint8_t *g, uint32_t bound, uint32_t n,
+         int max_with_md, uint8_t *h, uint32_t *mask, uint32_t *minf, float *y, cudaStream_t st);
+struct PdbParams {
+    int n_patterns;
+    int k[4];
+    int tiles[4][8];
+    uint32_t weight[4][8];
+    const uint8_t *table[4];
+};
+int pdb_gather(int domain, const PdbParams &P, const uint64_t *states, uint32_t n, const uint8_t *g,
+               uint32_t bound, uint8_t *h, uint32_t *mask, uint32_t *minf, cudaStream_t st);
+int pdb_build_device(Ctx *c, int side, const int *tiles, int k, uint8_t *table, cudaStream_t st);
+uint64_t npk(int n, int k);
+
+// ------------------------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------------------------
+static thread_local char g_err[512];
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+// ------------------------------------------------------------------------------------
+// memory
+// ------------------------------------------------------------------------------------
+int dev_alloc(Ctx *c, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return CBDFS_OK;
+    if (c->mem_budget && c->mem_used + bytes > c->mem_budget)
+        return fail(CBDFS_ENOMEM, "device memory budget of %zu bytes exceeded (%zu in use, %zu asked)",
+                    c->mem_budget, c->mem_used, bytes);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(CBDFS_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    c->mem_used += bytes;
+    return CBDFS_OK;
+}
+void dev_free(Ctx *c, void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    c->mem_used -= bytes;
+}
+
+// ------------------------------------------------------------------------------------
+// TMA descriptors
+// ------------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+int make_tmap_2d(CUtensorMap *map, void *base, CUtensorMapDataType dt, int elem_bytes,
+                 uint64_t inner, uint64_t outer, uint32_t box_inner, uint32_t box_outer) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return fail(CBDFS_EDEVICE, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {inner * elem_bytes};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(map, dt, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(CBDFS_EDEVICE, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return CBDFS_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// built-in heuristics: zero and Manhattan distance, with the bound test
+// ------------------------------------------------------------------------------------
+namespace {
+template <int DOMAIN, bool MD>
+__global__ void k_builtin(const uint64_t *__restrict__ states, uint32_t n, const uint8_t *__restrict__ g,
+                          uint32_t bound, uint8_t *__restrict__ h, uint32_t *__restrict__ mask,
+                          uint32_t *__restrict__ minf) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    uint32_t f = 0xFFFFFFFFu;
+    bool pass = false;
+    if (i < n) {
+        uint32_t hv = 0;
+        if (MD && DOMAIN != CBDFS_DOM_RC3) {
+            constexpr int SIDE = DOMAIN == CBDFS_DOM_STP3 ? 3 : 4;
+            hv = dev::manhattan<SIDE>(states[i]);
+        }
+        h[i] = (uint8_t)hv;
+        f = (uint32_t)g[i] + hv;
+        pass = f <= bound;
+    }
+    const uint32_t bits = __ballot_sync(0xFFFFFFFFu, pass);
+    const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, pass ? 0xFFFFFFFFu : f);
+    if (lane == 0 && i < n) {
+        mask[i >> 5] = bits;
+        if (mn != 0xFFFFFFFFu) atomicMin(minf, mn);
+    }
+}
+
+int builtin(int heur, int domain, const uint64_t *s, uint32_t n, const uint8_t *g, uint32_t bound,
+            uint8_t *h, uint32_t *mask, uint32_t *minf, cudaStream_t st) {
+    const unsigned b = (n + 255) / 256;
+    if (heur == CBDFS_HEUR_MD) {
+        if (domain == CBDFS_DOM_STP3) k_builtin<CBDFS_DOM_STP3, true><<<b, 256, 0, st>>>(s, n, g, bound, h, mask, minf);
+        else if (domain == CBDFS_DOM_STP4) k_builtin<CBDFS_DOM_STP4, true><<<b, 256, 0, st>>>(s, n, g, bound, h, mask, minf);
+        else return fail(CBDFS_EINVAL, "Manhattan distance is defined for sliding-tile domains only");
+    } else {
+        if (domain == CBDFS_DOM_RC3) k_builtin<CBDFS_DOM_RC3, false><<<b, 256, 0, st>>>(s, n, g, bound, h, mask, minf);
+        else k_builtin<CBDFS_DOM_STP4, false><<<b, 256, 0, st>>>(s, n, g, bound, h, mask, minf);
+    }
+    CUDA_TRY(cudaGetLastError());
+    return CBDFS_OK;
+}
+
+uint16_t f32_to_bf16_rne(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7FFFu + lsb;
+    return (uint16_t)(u >> 16);
+}
+
+int ensure_act(Ctx *c, size_t width) {
+    if (width <= c->max_width) return CBDFS_OK;
+    const size_t bytes = (size_t)c->max_batch_pad * width * 4;
+    for (auto &s : c->slots) {
+        for (int i = 0; i < 2; ++i) {
+            dev_free(c, s.act[i], c->act_bytes);
+            s.act[i] = nullptr;
+        }
+        s.tm_act.clear();
+    }
+    c->act_bytes = 0;
+    for (auto &s : c->slots)
+        for (int i = 0; i < 2; ++i) {
+            int rc = dev_alloc(c, &s.act[i], bytes);
+            if (rc) return rc;
+        }
+    c->act_bytes = bytes;
+    c->max_width = width;
+    return CBDFS_OK;
+}
+
+const CUtensorMap *act_map(Slot &s, Ctx *c, int buf, int K, int elem_bytes) {
+    const long long key = ((long long)buf << 40) | ((long long)elem_bytes << 32) | K;
+    auto it = s.tm_act.find(key);
+    if (it != s.tm_act.end()) return &it->second;
+    CUtensorMap m;
+    if (make_tmap_2d(&m, s.act[buf],
+                     elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                     elem_bytes, (uint64_t)K, c->max_batch_pad, 128 / elem_bytes, kBM))
+        return nullptr;
+    return &s.tm_act.emplace(key, m).first->second;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+// the evaluation pipeline
+// ------------------------------------------------------------------------------------
+static int mark(Slot &s, cudaStream_t st) {
+    if (!s.prof) return CBDFS_OK;
+    cudaEvent_t e;
+    CUDA_TRY(cudaEventCreate(&e));
+    CUDA_TRY(cudaEventRecord(e, st));
+    s.prof->push_back(e);
+    return CBDFS_OK;
+}
+
+int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states, const uint8_t *d_g,
+             uint32_t bound, uint32_t n, uint8_t *d_h, uint32_t *d_mask, uint32_t *d_minf, float *d_y,
+             cudaStream_t st) {
+    CUDA_TRY(cudaMemsetAsync(d_minf, 0xFF, sizeof(uint32_t), st));
+    if (n == 0) return CBDFS_OK;
+    if (int r = mark(s, st)) return r;
+    if (heur_id < 0) {
+        int r = builtin(heur_id, domain, d_states, n, d_g, bound, d_h, d_mask, d_minf, st);
+        return r ? r : mark(s, st);
+    }
+    if (c->heur_kind[heur_id] == 1) {
+        const PdbGPU &p = *c->pdbs[c->heur_index[heur_id]];
+        if (p.domain != domain) return fail(CBDFS_EINVAL, "PDB %d is for another domain", heur_id);
+        PdbParams P{};
+        P.n_patterns = p.n_patterns;
+        const int N = p.side * p.side;
+        for (int q = 0; q < p.n_patterns; ++q) {
+            P.k[q] = p.k[q];
+            P.table[q] = p.table[q];
+            for (int i = 0; i < p.k[q]; ++i) {
+                P.tiles[q][i] = p.tiles[q][i];
+                P.weight[q][i] = (uint32_t)npk(N - 1 - i, p.k[q] - 1 - i);
+            }
+        }
+        int r = pdb_gather(domain, P, d_states, n, d_g, bound, d_h, d_mask, d_minf, st);
+        return r ? r : mark(s, st);
+    }
+    const NetGPU &net = *c->nets[c->heur_index[heur_id]];
+    if (net.domain != domain) return fail(CBDFS_EINVAL, "network %d is for another domain", heur_id);
+    const uint32_t rows_pad = (n + kBM - 1) / kBM * kBM;
+    const int L = net.L;
+    int rc;
+    if (net.prec == CBDFS_PREC_FP32) {
+        float *a = (float *)s.act[0], *b = (float *)s.act[1];
+        rc = first_gather(domain, d_states, n, net.w32[0], net.b32[0], net.dims[1], a, st);
+        if (rc || (rc = mark(s, st))) return rc;
+        for (int l = 1; l < L - 1; ++l) {
+            rc = sgemm_relu(a, net.w32[l], net.b32[l], b, (int)rows_pad, net.dims[l + 1], net.dims[l], 1, st);
+            if (rc || (rc = mark(s, st))) return rc;
+            std::swap(a, b);
+        }
+        rc = head(false, domain, net.head, a, net.dims[L - 1], net.dims[L], net.w32[L - 1],
+                    net.b32[L - 1], d_states, d_g, bound, n, net.max_with_md, d_h, d_mask, d_minf, d_y, st);
+        return rc ? rc : mark(s, st);
+    }
+    const bool fp8 = net.prec == CBDFS_PREC_FP8;
+    int cur = 0;
+    for (int l = 0; l < L - 1; ++l) {
+        const bool first = l == 0;
+        const bool out_fp8 = fp8 && l < L - 2;  // the head reads BF16
+        const int K = first ? net.k1pad : net.dims[l];
+        const CUtensorMap *tmA = &net.tm_w[0];  // placeholder for the first layer
+        if (!first) {
+            tmA = act_map(s, c, cur, K, fp8 ? 1 : 2);
+            if (!tmA) return CBDFS_EDEVICE;
+        }
+        const int out_buf = first ? 0 : cur ^ 1;
+        const float acc_scale = fp8 ? net.w_scale[l] * (first ? 1.f : net.a_scale[l - 1]) : 1.f;
+        const float out_q = out_fp8 ? 1.f / net.a_scale[l] : 1.f;
+        rc = tc_layer(first, domain, fp8, out_fp8, net.bn[l], *tmA, net.tm_w[l], d_states, n, rows_pad,
+                      K, net.dims[l + 1], net.b32[l], s.act[out_buf], acc_scale, out_q, c->d_err, st);
+        if (rc || (rc = mark(s, st))) return rc;
+        cur = out_buf;
+    }
+    rc = head(true, domain, net.head, s.act[cur], net.dims[L - 1], net.dims[L], net.w32[L - 1],
+              net.b32[L - 1], d_states, d_g, bound, n, net.max_with_md, d_h, d_mask, d_minf, d_y, st);
+    return rc ? rc : mark(s, st);
+}
+
+}  // namespace cbdfs
+
+using namespace cbdfs;
+
+// ======================================================================================
+// C ABI
+// ======================================================================================
+extern "C" {
+
+const char *cbdfs_last_error(void) { return g_err; }
+
+size_t cbdfs_mem_used(const cbdfs_ctx *ctx) {
+    return ctx ? reinterpret_cast<const Ctx *>(ctx)->mem_used : 0;
+}
+
+void cbdfs_destroy(cbdfs_ctx *ctx) {
+    if (!ctx) return;
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto &s : c->slots) {
+        for (int i = 0; i < 2; ++i) dev_free(c, s.act[i], c->act_bytes);
+        dev_free(c, s.d_states, (size_t)c->max_batch_pad * 16);
+        dev_free(c, s.d_g, c->max_batch_pad);
+        dev_free(c, s.d_h, c->max_batch_pad);
+        dev_free(c, s.d_mask, c->max_batch_pad / 8);
+        dev_free(c, s.d_minf, 4);
+        if (s.stream) cudaStreamDestroy(s.stream);
+        if (s.done) cudaEventDestroy(s.done);
+    }
+    for (auto &n : c->nets) {
+        for (int l = 0; l < kMaxLayers; ++l) {
+            if (n->w_lp[l]) cudaFree(n->w_lp[l]);
+            if (n->w32[l]) cudaFree(n->w32[l]);
+            if (n->b32[l]) cudaFree(n->b32[l]);
+        }
+    }
+    for (auto &p : c->pdbs)
+        for (int q = 0; q < 4; ++q)
+            if (p->table[q]) cudaFree(p->table[q]);
+    if (c->d_err) cudaFree(c->d_err);
+    delete c;
+}
+
+int cbdfs_create(const cbdfs_config *cfg, cbdfs_ctx **out) {
+    if (!cfg || !out) return fail(CBDFS_EINVAL, "null argument");
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        return fail(CBDFS_EDEVICE, "no CUDA device");
+    if (cfg->device < 0 || cfg->device >= ndev) return fail(CBDFS_EINVAL, "device %d out of range", cfg->device);
+    CUDA_TRY(cudaSetDevice(cfg->device));
+    Ctx *c = new Ctx();
+    c->device = cfg->device;
+    c->mem_budget = cfg->mem_budget;
+    c->max_batch = cfg->max_batch ? cfg->max_batch : 65536;
+    c->max_batch_pad = (c->max_batch + kBM - 1) / kBM * kBM;
+    const int nslots = 1 + (cfg->n_slots > 0 ? cfg->n_slots : 4);  // slot 0: device-buffer calls
+    c->slots.resize(nslots);
+    int rc = dev_alloc(c, (void **)&c->d_err, sizeof(int));
+    if (!rc && cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) rc = fail(CBDFS_EDEVICE, "memset");
+    for (int i = 0; i < nslots && !rc; ++i) {
+        Slot &s = c->slots[i];
+        if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
+            rc = fail(CBDFS_EDEVICE, "stream/event creation");
+            break;
+        }
+        if (i == 0) continue;
+        rc = dev_alloc(c, (void **)&s.d_states, (size_t)c->max_batch_pad * 16);
+        if (!rc) rc = dev_alloc(c, (void **)&s.d_g, c->max_batch_pad);
+        if (!rc) rc = dev_alloc(c, (void **)&s.d_h, c->max_batch_pad);
+        if (!rc) rc = dev_alloc(c, (void **)&s.d_mask, c->max_batch_pad / 8);
+        if (!rc) rc = dev_alloc(c, (void **)&s.d_minf, 4);
+    }
+    if (rc) {
+        cbdfs_destroy(reinterpret_cast<cbdfs_ctx *>(c));
+        return rc;
+    }
+    *out = reinterpret_cast<cbdfs_ctx *>(c);
+    return CBDFS_OK;
+}
+
+int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
+    if (!ctx || !d || !heur_id || !d->dims || !d->weights || !d->biases)
+        return fail(CBDFS_EINVAL, "null argument");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    CUDA_TRY(cudaSetDevice(c->device));
+    const int L = d->n_layers;
+    if (L < 2 || L > kMaxLayers) return fail(CBDFS_EINVAL, "n_layers %d outside 2..%d", L, kMaxLayers);
+    if (d->domain < 0 || d->domain > 2) return fail(CBDFS_EINVAL, "domain %d", d->domain);
+    if (d->dims[0] != dom_onehot(d->domain))
+        return fail(CBDFS_EINVAL, "dims[0]=%d but the domain's one-hot width is %d", d->dims[0], dom_onehot(d->domain));
+    if (d->prec < 0 || d->prec > 2) return fail(CBDFS_EINVAL, "precision %d", d->prec);
+    if (d->head != CBDFS_HEAD_REGRESSION && d->head != CBDFS_HEAD_CLASSIFIER) return fail(CBDFS_EINVAL, "head %d", d->head);
+    if (d->head == CBDFS_HEAD_REGRESSION && d->dims[L] != 1) return fail(CBDFS_EINVAL, "a regression head has one output");
+    if (d->max_with_md && d->domain == CBDFS_DOM_RC3) return fail(CBDFS_EINVAL, "Manhattan distance needs a sliding-tile domain");
+    for (int l = 1; l < L; ++l)
+        if (d->dims[l] % 128 != 0) return fail(CBDFS_EINVAL, "hidden width %d is not a multiple of 128", d->dims[l]);
+    if (d->dims[L] < 1 || d->dims[L] > 256) return fail(CBDFS_EINVAL, "output width %d outside 1..256", d->dims[L]);
+    if (d->prec == CBDFS_PREC_FP8 && !d->act_scales) return fail(CBDFS_EINVAL, "FP8 needs activation scales");
+    auto net = std::make_unique<NetGPU>();
+    NetGPU &N = *net;
+    N.domain = d->domain; N.L = L; N.prec = d->prec; N.head = d->head; N.max_with_md = d->max_with_md;
+    for (int l = 0; l <= L; ++l) N.dims[l] = d->dims[l];
+    size_t maxw = 0;
+    for (int l = 1; l < L; ++l) maxw = std::max(maxw, (size_t)d->dims[l]);
+    int rc = ensure_act(c, maxw);
+    if (rc) return rc;
+    auto upload = [&](void **dst, const void *src, size_t bytes) -> int {
+        int r = dev_alloc(c, dst, bytes);
+        if (r) return r;
+        N.bytes += bytes;
+        if (cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(CBDFS_EDEVICE, "weight upload");
+        return CBDFS_OK;
+    };
+    // FP32 copies: biases always; weights of the last layer always; all layers for FP32
+    for (int l = 0; l < L; ++l) {
+        const int O = d->dims[l + 1], I = d->dims[l];
+        if ((rc = upload((void **)&N.b32[l], d->biases[l], sizeof(float) * O))) return rc;
+        if (l == L - 1 || d->prec == CBDFS_PREC_FP32) {
+            if (l == 0) {  // the gather form reads W1 transposed
+                std::vector<float> t((size_t)I * O);
+                for (int o = 0; o < O; ++o)
+                    for (int i = 0; i < I; ++i) t[(size_t)i * O + o] = d->weights[0][(size_t)o * I + i];
+                if ((rc = upload((void **)&N.w32[0], t.data(), sizeof(float) * t.size()))) return rc;
+            } else if ((rc = upload((void **)&N.w32[l], d->weights[l], sizeof(float) * (size_t)O * I))) {
+                return rc;
+            }
+        }
+    }
+    if (d->prec != CBDFS_PREC_FP32) {
+        const bool fp8 = d->prec == CBDFS_PREC_FP8;
+        const int kblk = fp8 ? 128 : 64;
+        N.k1pad = (d->dims[0] + kblk - 1) / kblk * kblk;
+        for (int l = 0; l < L - 1; ++l) {
+            const int O = d->dims[l + 1], I = d->dims[l];
+            const int Kp = l == 0 ? N.k1pad : I;
+            const float *W = d->weights[l];
+            std::vector<uint8_t> buf((size_t)O * Kp * (fp8 ? 1 : 2), 0);
+            if (fp8) {
+                float amax = 0.f;
+                for (size_t i = 0; i < (size_t)O * I; ++i) amax = std::max(amax, std::fabs(W[i]));
+                const float scale = amax > 0.f ? amax / 448.0f : 1.0f;
+                N.w_scale[l] = scale;
+                for (int o = 0; o < O; ++o)
+                    for (int i = 0; i < I; ++i)
+                        buf[(size_t)o * Kp + i] =
+                            (uint8_t)__nv_cvt_float_to_fp8(W[(size_t)o * I + i] / scale, __NV_SATFINITE, __NV_E4M3);
+                if (l < L - 1) N.a_scale[l] = d->act_scales[l];
+            } else {
+                N.w_scale[l] = 1.f;
+                uint16_t *b16 = reinterpret_cast<uint16_t *>(buf.data());
+                for (int o = 0; o < O; ++o)
+                    for (int i = 0; i < I; ++i) b16[(size_t)o * Kp + i] = f32_to_bf16_rne(W[(size_t)o * I + i]);
+            }
+            if ((rc = upload(&N.w_lp[l], buf.data(), buf.size()))) return rc;
+            N.bn[l] = (O % 256 == 0) ? 256 : 128;
+            if ((rc = make_tmap_2d(&N.tm_w[l], N.w_lp[l],
+                                   fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                                   fp8 ? 1 : 2, (uint64_t)Kp, (uint64_t)O, kblk, N.bn[l])))
+                return rc;
+        }
+    }
+    if ((size_t)d->dims[L] * 4 * 4 > 48 * 1024) return fail(CBDFS_EINVAL, "output width too large");
+    c->nets.push_back(std::move(net));
+    c->heur_kind.push_back(0);
+    c->heur_index.push_back((int)c->nets.size() - 1);
+    *heur_id = (int)c->heur_kind.size() - 1;
+    return CBDFS_OK;
+}
+
+int cbdfs_pdb_load(cbdfs_ctx *ctx, const cbdfs_pdb_desc *d, int *heur_id) {
+    if (!ctx || !d || !heur_id || !d->k || !d->tiles) return fail(CBDFS_EINVAL, "null argument");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    CUDA_TRY(cudaSetDevice(c->device));
+    if (d->domain != CBDFS_DOM_STP3 && d->domain != CBDFS_DOM_STP4)
+        return fail(CBDFS_EINVAL, "pattern databases are for sliding-tile domains");
+    if (d->n_patterns < 1 || d->n_patterns > 4) return fail(CBDFS_EINVAL, "n_patterns %d outside 1..4", d->n_patterns);
+    auto p = std::make_unique<PdbGPU>();
+    p->domain = d->domain;
+    p->side = dom_side(d->domain);
+    p->n_patterns = d->n_patterns;
+    const int N = p->side * p->side;
+    int off = 0;
+    uint32_t used = 0;
+    for (int q = 0; q < d->n_patterns; ++q) {
+        if (d->k[q] < 1 || d->k[q] > 8) return fail(CBDFS_EINVAL, "pattern size %d outside 1..8", d->k[q]);
+        p->k[q] = d->k[q];
+        for (int i = 0; i < d->k[q]; ++i) {
+            const int t = d->tiles[off + i];
+            if (t < 1 || t >= N || (used & (1u << t))) return fail(CBDFS_EINVAL, "bad or repeated tile %d", t);
+            used |= 1u << t;
+            p->tiles[q][i] = t;
+        }
+        off += d->k[q];
+        p->entries[q] = npk(N, d->k[q]);
+        int rc = dev_alloc(c, (void **)&p->table[q], p->entries[q]);
+        if (rc) return rc;
+        p->bytes += p->entries[q];
+        if (d->tables && d->tables[q]) {
+            CUDA_TRY(cudaMemcpy(p->table[q], d->tables[q], p->entries[q], cudaMemcpyHostToDevice));
+        } else {
+            rc = pdb_build_device(c, p->side, p->tiles[q], p->k[q], p->table[q], c->slots[0].stream);
+            if (rc) return rc;
+        }
+    }
+    c->pdbs.push_back(std::move(p));
+    c->heur_kind.push_back(1);
+    c->heur_index.push_back((int)c->pdbs.size() - 1);
+    *heur_id = (int)c->heur_kind.size() - 1;
+    return CBDFS_OK;
+}
+
+int pdb_build(cbdfs_ctx *ctx, int domain, const int *pattern_tiles, int k, uint8_t *table_out,
+              size_t cap, size_t *entries) {
+    if (!ctx || !pattern_tiles || !table_out || !entries) return fail(CBDFS_EINVAL, "null argument");
+    if (domain != CBDFS_DOM_STP3 && domain != CBDFS_DOM_STP4) return fail(CBDFS_EINVAL, "domain %d", domain);
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    CUDA_TRY(cudaSetDevice(c->device));
+    const int side = dom_side(domain), N = side * side;
+    if (k < 1 || k > 8) return fail(CBDFS_EINVAL, "pattern size %d outside 1..8", k);
+    uint32_t used = 0;
+    for (int i = 0; i < k; ++i) {
+        const int t = pattern_tiles[i];
+        if (t < 1 || t >= N || (used & (1u << t))) return fail(CBDFS_EINVAL, "bad or repeated tile %d", t);
+        used |= 1u << t;
+    }
+    const size_t P = npk(N, k);
+    *entries = P;
+    if (cap < P) return fail(CBDFS_EINVAL, "table buffer holds %zu bytes, %zu needed", cap, P);
+    uint8_t *d_tab = nullptr;
+    int rc = dev_alloc(c, (void **)&d_tab, P);
+    if (rc) return rc;
+    rc = pdb_build_device(c, side, pattern_tiles, k, d_tab, c->slots[0].stream);
+    if (!rc && cudaMemcpy(table_out, d_tab, P, cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = fail(CBDFS_EDEVICE, "table download");
+    dev_free(c, d_tab, P);
+    return rc;
+}
+
+static int check_eval_args(Ctx *c, int heur_id, int domain, uint32_t n) {
+    if (domain < 0 || domain > 2) return fail(CBDFS_EINVAL, "domain %d", domain);
+    if (n > c->max_batch) return fail(CBDFS_EINVAL, "n=%u exceeds max_batch=%u", n, c->max_batch);
+    if (heur_id >= (int)c->heur_kind.size() || heur_id < CBDFS_HEUR_MD)
+        return fail(CBDFS_EINVAL, "unknown heuristic id %d", heur_id);
+    if (heur_id == CBDFS_HEUR_MD && domain == CBDFS_DOM_RC3)
+        return fail(CBDFS_EINVAL, "Manhattan distance is defined for sliding-tile domains only");
+    return CBDFS_OK;
+}
+
+int heur_eval_device(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_states, const uint8_t *d_g,
+                     uint32_t bound, uint32_t n, uint8_t *d_h, uint32_t *d_mask, uint32_t *d_minf,
+                     float *d_y, void *stream) {
+    if (!ctx || !d_minf || (n && (!d_states || !d_g || !d_h || !d_mask))) return fail(CBDFS_EINVAL, "null argument");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    int rc = check_eval_args(c, heur_id, domain, n);
+    if (rc) return rc;
+    CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lk(c->device_call_mu);
+    Slot &s = c->slots[0];
+    // slot 0 owns this call's activation scratch; order the call after its last use (a call
+    // being captured into a CUDA graph is ordered by the graph instead)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    const bool capturing = cs != cudaStreamCaptureStatusNone;
+    if (!capturing) CUDA_TRY(cudaStreamWaitEvent(st, s.done, 0));
+    rc = run_eval(c, s, heur_id, domain, d_states, d_g, bound, n, d_h, d_mask, d_minf, d_y, st);
+    if (!capturing) CUDA_TRY(cudaEventRecord(s.done, st));
+    return rc;
+}
+
+int heur_submit_batch(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *states, const uint8_t *g,
+                      uint32_t bound, uint32_t n, uint8_t *h_out, uint32_t *mask_out, uint32_t *minf_out,
+                      float *y_out) {
+    if (!ctx || !minf_out || (n && (!states || !g || !h_out || !mask_out))) return fail(CBDFS_EINVAL, "null argument");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    int rc = check_eval_args(c, heur_id, domain, n);
+    if (rc) return rc;
+    CUDA_TRY(cudaSetDevice(c->device));
+    int si;
+    {
+        std::unique_lock<std::mutex> lk(c->slot_mu);
+        for (;;) {
+            si = -1;
+            for (int i = 1; i < (int)c->slots.size(); ++i)
+                if (!c->slots[i].busy) { si = i; break; }
+            if (si >= 0) break;
+            c->slot_cv.wait(lk);
+        }
+        c->slots[si].busy = true;
+    }
+    Slot &s = c->slots[si];
+    cudaStream_t st = s.stream;
+    const int w = dom_words(domain);
+    int C = 0;
+    if (y_out && heur_id >= 0 && c->heur_kind[heur_id] == 0) {
+        const NetGPU &net = *c->nets[c->heur_index[heur_id]];
+        C = net.dims[net.L];
+    }
+    float *d_y = nullptr;
+    if (C) {
+        rc = dev_alloc(c, (void **)&d_y, (size_t)n * C * 4 + 4);
+    }
+    if (!rc && n) {
+        if (cudaMemcpyAsync(s.d_states, states, (size_t)n * 8 * w, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(s.d_g, g, n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            rc = fail(CBDFS_EDEVICE, "batch upload");
+    }
+    if (!rc) rc = run_eval(c, s, heur_id, domain, s.d_states, s.d_g, bound, n, s.d_h, s.d_mask, s.d_minf, d_y, st);
+    if (!rc) {
+        if ((n && (cudaMemcpyAsync(h_out, s.d_h, n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                   cudaMemcpyAsync(mask_out, s.d_mask, (size_t)(n + 31) / 32 * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)) ||
+            cudaMemcpyAsync(minf_out, s.d_minf, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            (C && cudaMemcpyAsync(y_out, d_y, (size_t)n * C * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess))
+            rc = fail(CBDFS_EDEVICE, "result download");
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (!rc && e != cudaSuccess) rc = fail(CBDFS_EDEVICE, "evaluation: %s", cudaGetErrorString(e));
+    if (d_y) dev_free(c, d_y, (size_t)n * C * 4 + 4);
+    if (!rc) {
+        int flag = 0;
+        if (cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && flag)
+            rc = fail(CBDFS_ETIMEDOUT, "a device wait ran out (code %d)", flag);
+    }
+    {
+        std::lock_guard<std::mutex> lk(c->slot_mu);
+        s.busy = false;
+    }
+    c->slot_cv.notify_one();
+    return rc;
+}
+
+int cbdfs_eval_profile(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_states,
+                       const uint8_t *d_g, uint32_t bound, uint32_t n, uint8_t *d_h, uint32_t *d_mask,
+                       uint32_t *d_minf, void *stream, float *stage_ms, int cap, int *n_stages) {
+    if (!ctx || !stage_ms || !n_stages || !d_minf || (n && (!d_states || !d_g || !d_h || !d_mask)))
+        return fail(CBDFS_EINVAL, "null argument");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    int rc = check_eval_args(c, heur_id, domain, n);
+    if (rc) return rc;
+    CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lk(c->device_call_mu);
+    Slot &s = c->slots[0];
+    std::vector<cudaEvent_t> evs;
+    CUDA_TRY(cudaStreamWaitEvent(st, s.done, 0));
+    s.prof = &evs;
+    rc = run_eval(c, s, heur_id, domain, d_states, d_g, bound, n, d_h, d_mask, d_minf, nullptr, st);
+    s.prof = nullptr;
+    if (!rc && cudaEventRecord(s.done, st) != cudaSuccess) rc = fail(CBDFS_EDEVICE, "event record");
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(CBDFS_EDEVICE, "profile sync");
+    *n_stages = 0;
+    for (size_t i = 1; i < evs.size() && !rc; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, evs[i - 1], evs[i]) != cudaSuccess) {
+            rc = fail(CBDFS_EDEVICE, "event timing");
+            break;
+        }
+        if (*n_stages < cap) stage_ms[(*n_stages)++] = ms;
+    }
+    for (auto e : evs) cudaEventDestroy(e);
+    return rc;
+}
+
+int cbdfs_device_status(cbdfs_ctx *ctx) {
+    if (!ctx) return fail(CBDFS_EINVAL, "null argument");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    CUDA_TRY(cudaSetDevice(c->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    int flag = 0;
+    CUDA_TRY(cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int)));
+    return flag;
+}
+
+}  // extern "C"

@@ -1,0 +1,316 @@
+// common.cuh -- internal declarations shared by the library's translation units:
+// the context, the loaded heuristics, the device-side PTX wrappers (mbarrier, TMA,
+// tcgen05) and the packed-state decoders.  Not part of the public ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/cbdfs.h"
+
+namespace cbdfs {
+
+// ------------------------------------------------------------------------------------
+// host-side error plumbing
+// ------------------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+int fail(int code, const char *fmt, ...);
+
+#define CUDA_TRY(expr)                                                                   \
+    do {                                                                                 \
+        cudaError_t _e = (expr);                                                         \
+        if (_e != cudaSuccess)                                                           \
+            return ::cbdfs::fail(CBDFS_EDEVICE, "%s failed: %s (%s:%d)", #expr,          \
+                                 cudaGetErrorString(_e), __FILE__, __LINE__);            \
+    } while (0)
+
+// device error codes written to the context's flag by a wait that ran out
+enum DevErr : int {
+    DEVERR_NONE = 0,
+    DEVERR_TMA_FULL = 1,     // MMA issuer waited for a TMA stage
+    DEVERR_STAGE_EMPTY = 2,  // producer waited for the MMA to free a stage
+    DEVERR_ACCUM = 3,        // epilogue waited for the accumulator
+    DEVERR_ENCODE = 4,
+};
+
+// ------------------------------------------------------------------------------------
+// loaded heuristics
+// ------------------------------------------------------------------------------------
+constexpr int kMaxLayers = 8;
+constexpr int kBM = 128;  // rows (states) per tensor-core tile
+
+struct NetGPU {
+    int domain = 0, L = 0, prec = 0, head = 0, max_with_md = 0;
+    int dims[kMaxLayers + 1] = {};
+    int k1pad = 0;                     // one-hot width padded to the MMA K block
+    // tensor-core layers 0..L-2: low-precision weights [dims[l+1]][Kpad] (K-major)
+    void *w_lp[kMaxLayers] = {};
+    float w_scale[kMaxLayers] = {};    // FP8: weight scale per layer (1 for BF16)
+    float a_scale[kMaxLayers] = {};    // FP8: activation scale of layer l's OUTPUT
+    CUtensorMap tm_w[kMaxLayers];      // TMA maps of w_lp
+    int bn[kMaxLayers] = {};           // N tile per layer
+    // FP32 weights for every layer (the FP32 path; the last layer for every path)
+    float *w32[kMaxLayers] = {};
+    float *b32[kMaxLayers] = {};
+    size_t bytes = 0;
+};
+
+struct PdbGPU {
+    int domain = 0, side = 0, n_patterns = 0;
+    int k[4] = {}, tiles[4][16] = {};
+    uint8_t *table[4] = {};
+    size_t entries[4] = {};
+    size_t bytes = 0;
+};
+
+// one evaluation slot: a stream plus the scratch a batch needs
+struct Slot {
+    cudaStream_t stream = nullptr;
+    void *act[2] = {};                 // ping-pong activations (max_batch_pad x max_width x 4 B)
+    uint64_t *d_states = nullptr;      // staging for host-buffer calls
+    uint8_t *d_g = nullptr, *d_h = nullptr;
+    uint32_t *d_mask = nullptr, *d_minf = nullptr;
+    float *d_y = nullptr;
+    // TMA maps of the activation buffers, keyed by (buffer, width, dtype bytes)
+    std::map<long long, CUtensorMap> tm_act;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    std::vector<cudaEvent_t> *prof = nullptr;  // when set, an event follows every launch
+};
+
+struct Ctx {
+    int device = 0;
+    size_t mem_budget = 0, mem_used = 0;
+    uint32_t max_batch = 0, max_batch_pad = 0;
+    size_t act_bytes = 0;              // bytes per activation buffer
+    int *d_err = nullptr;              // device error flag
+    std::vector<std::unique_ptr<NetGPU>> nets;    // heur ids 0..: nets and PDBs interleaved
+    std::vector<std::unique_ptr<PdbGPU>> pdbs;
+    std::vector<int> heur_kind;        // 0 = net, 1 = pdb
+    std::vector<int> heur_index;
+    std::vector<Slot> slots;
+    std::mutex slot_mu;
+    std::condition_variable slot_cv;
+    std::mutex device_call_mu;         // heur_eval_device scratch (slot 0)
+    std::atomic<int> cancel{0};
+    size_t max_width = 0;
+};
+
+// allocation through the context's budget
+int dev_alloc(Ctx *c, void **p, size_t bytes);
+void dev_free(Ctx *c, void *p, size_t bytes);
+
+// TMA map creation (driver entry point fetched once)
+int make_tmap_2d(CUtensorMap *map, void *base, CUtensorMapDataType dt, int elem_bytes,
+                 uint64_t inner, uint64_t outer, uint32_t box_inner, uint32_t box_outer);
+
+// the evaluation pipeline on a stream with a slot's scratch (device pointers)
+int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
+             const uint8_t *d_g, uint32_t bound, uint32_t n, uint8_t *d_h, uint32_t *d_mask,
+             uint32_t *d_minf, float *d_y, cudaStream_t st);
+
+// per-domain facts
+inline int dom_words(int d) { return d == CBDFS_DOM_RC3 ? 2 : 1; }
+inline int dom_side(int d) { return d == CBDFS_DOM_STP3 ? 3 : 4; }
+inline int dom_onehot(int d) { return d == CBDFS_DOM_STP3 ? 81 : d == CBDFS_DOM_STP4 ? 256 : 480; }
+
+}  // namespace cbdfs
+
+// ======================================================================================
+// device helpers
+// ======================================================================================
+#ifdef __CUDACC__
+namespace cbdfs {
+namespace dev {
+
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on every device wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---- mbarrier ----
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after kWaitNs (or 2^30 polls), records `code` in *err and
+// returns false.  Never traps.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t i = 1; i < (1u << 30); ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 0 && globaltimer() - t0 > kWaitNs) break;
+    }
+    atomicExch(err, code);
+    return false;
+}
+
+// ---- TMA ----
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_map(const CUtensorMap *map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
+}
+
+// ---- tcgen05 ----
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulate
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// same with E4M3 inputs (kind::f8f6f4)
+__device__ __forceinline__ void umma_fp8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+// 32 lanes x 32 columns of 32-bit: thread i of the warp gets row (lane base + i),
+// columns col..col+31
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand stored in the 128-byte swizzle
+// layout that TMA's SWIZZLE_128B writes: rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address
+    d |= (uint64_t)1 << 16;                    // leading byte offset (unused here)
+    d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                    // descriptor version for sm_100 family
+    d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulator, K-major A and B, M x N tile.
+// a_fmt/b_fmt: kind::f16 -> 1 = BF16; kind::f8f6f4 -> 0 = E4M3.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N, int a_fmt, int b_fmt) {
+    return (1u << 4) | ((uint32_t)a_fmt << 7) | ((uint32_t)b_fmt << 10) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ---- packed-state helpers ----
+template <int SIDE>
+__device__ __forceinline__ int manhattan(uint64_t s) {
+    constexpr int N = SIDE * SIDE;
+    int md = 0;
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+        int t = (int)((s >> (4 * p)) & 15u);
+        int dr = p / SIDE - t / SIDE, dc = p % SIDE - t % SIDE;
+        int d = (dr < 0 ? -dr : dr) + (dc < 0 ? -dc : dc);
+        md += t ? d : 0;
+    }
+    return md;
+}
+template <int SIDE>
+__device__ __forceinline__ bool stp_is_goal(uint64_t s) {
+    constexpr int N = SIDE * SIDE;
+    uint64_t g = 0;
+#pragma unroll
+    for (int t = 0; t < N; ++t) g |= (uint64_t)t << (4 * t);
+    return s == g;
+}
+__device__ __forceinline__ bool rc_is_goal(uint64_t w0, uint64_t w1) {
+    uint64_t g0 = 0, g1 = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) g0 |= (uint64_t)(k * 3) << (5 * k);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) g1 |= (uint64_t)(k * 2) << (5 * k);
+    return w0 == g0 && w1 == g1;
+}
+
+}  // namespace dev
+}  // namespace cbdfs
+#endif

@@ -1,0 +1,207 @@
+"""Parity of the GPU heuristic path with the oracle: built-in Manhattan distance, additive
+PDB gather, the FP32 and BF16 network forms, the integer-h epilogue and the bound test."""
+import numpy as np
+import pytest
+
+import workloads as W
+from helpers import PREC, check_h, check_logits, oracle_net
+
+pytestmark = pytest.mark.gpu
+
+RAGGED = [1, 31, 33, 127, 129, 300, 1000]
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2507_11916_b300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def ctx(P):
+    c = P.cbdfs_create(0, max_batch=16384, n_slots=2)
+    yield c
+    P.cbdfs_destroy(c)
+
+
+def _g(n, seed, hi=40):
+    return (W.splitmix64_array(seed, n) % np.uint64(hi)).astype(np.uint8)
+
+
+def _check_bound(orc, h, g, bound, mask, minf):
+    want_mask, want_minf = orc.bound_test(g, h, bound)
+    assert np.array_equal(mask, want_mask)
+    assert minf == want_minf
+
+
+@pytest.mark.parametrize("n", RAGGED)
+def test_manhattan(P, ctx, orc, n):
+    for side, dom in ((3, P.DOM_STP3), (4, P.DOM_STP4)):
+        s = W.random_stp_states(side, n, 10 + n)
+        s[0] = W.stp_goal(side)
+        g = _g(n, n)
+        h, mask, minf = P.heur_submit_batch(ctx, P.HEUR_MD, dom, s, g, 45)
+        want = orc.md_states(dom, s)
+        want[0] = 0
+        assert np.array_equal(h, want)
+        _check_bound(orc, h, g, 45, mask, minf)
+
+
+def test_empty_batch(P, ctx):
+    h, mask, minf = P.heur_submit_batch(ctx, P.HEUR_MD, P.DOM_STP4, np.zeros(0, np.uint64),
+                                        np.zeros(0, np.uint8), 10)
+    assert len(h) == 0 and minf == 0xFFFFFFFF
+
+
+def test_rejects_bad_arguments(P, ctx):
+    with pytest.raises(P.CbdfsError):
+        P.heur_submit_batch(ctx, 99, P.DOM_STP4, np.zeros(4, np.uint64), np.zeros(4, np.uint8), 1)
+    with pytest.raises(P.CbdfsError):
+        P.heur_submit_batch(ctx, P.HEUR_MD, P.DOM_RC3, np.zeros(8, np.uint64), np.zeros(4, np.uint8), 1)
+    with pytest.raises(P.CbdfsError):
+        big = 16385
+        P.heur_submit_batch(ctx, P.HEUR_MD, P.DOM_STP4, np.zeros(big, np.uint64), np.zeros(big, np.uint8), 1)
+
+
+@pytest.fixture(scope="module")
+def pdb8(orc):
+    pats = [[1, 2, 3, 4], [5, 6, 7, 8]]
+    return pats, [orc.pdb_build(3, p) for p in pats]
+
+
+@pytest.fixture(scope="module")
+def pdb15(orc):
+    pats = [[1, 2, 3, 5, 6], [4, 8, 9, 12, 13], [7, 10, 11, 14, 15]]
+    return pats, [orc.pdb_build(4, p) for p in pats]
+
+
+@pytest.mark.parametrize("n", RAGGED)
+def test_pdb_gather(P, ctx, orc, pdb8, pdb15, n):
+    for side, dom, (pats, tabs) in ((3, P.DOM_STP3, pdb8), (4, P.DOM_STP4, pdb15)):
+        hid = P.cbdfs_pdb_load(ctx, dom, pats, tabs)
+        s = W.random_stp_states(side, n, 20 + n)
+        g = _g(n, 7 * n)
+        h, mask, minf = P.heur_submit_batch(ctx, hid, dom, s, g, 50)
+        want = orc.PDB(side, pats, tabs).hs(s)
+        want[orc.is_goal_states(dom, s)] = 0
+        assert np.array_equal(h, want)
+        _check_bound(orc, h, g, 50, mask, minf)
+
+
+@pytest.mark.parametrize("tiles", [[1, 2, 3, 4], [5, 6, 7, 8], [1, 3, 5, 7, 8]])
+def test_pdb_build_8puzzle(P, ctx, orc, tiles):
+    assert np.array_equal(P.pdb_build(ctx, P.DOM_STP3, tiles), orc.pdb_build(3, tiles))
+
+
+def test_pdb_build_15puzzle_small(P, ctx, orc):
+    for tiles in ([10, 11, 15], [1, 2, 3, 5], [4, 8, 12, 13, 14]):
+        assert np.array_equal(P.pdb_build(ctx, P.DOM_STP4, tiles), orc.pdb_build(4, tiles))
+
+
+@pytest.mark.slow
+def test_pdb_build_663(P, ctx, orc):
+    for tiles in orc.PATTERNS_663:
+        assert np.array_equal(P.pdb_build(ctx, P.DOM_STP4, tiles), orc.pdb_build(4, tiles))
+
+
+# ---- network heuristic ------------------------------------------------------------------
+
+def _net(P, ctx, cfg, dom, prec, head, md):
+    Ws, bs = W.net_weights(**cfg)
+    hid = P.cbdfs_net_load(ctx, dom, Ws, bs, PREC[prec], head, md)
+    return Ws, bs, hid
+
+
+@pytest.mark.parametrize("n", RAGGED)
+def test_c0_fp32_regression(P, ctx, orc, n):
+    Ws, bs, hid = _net(P, ctx, W.NET_C0, P.DOM_STP3, "fp32", P.HEAD_REGRESSION, 1)
+    s = W.random_stp_states(3, n, 40 + n)
+    g = _g(n, n + 1)
+    h, mask, minf, y = P.heur_submit_batch(ctx, hid, P.DOM_STP3, s, g, 30, want_y=True)
+    y64, h64, margin = oracle_net(orc, 0, Ws, bs, "fp32", s, "regression", True)
+    check_logits(y, y64, "fp32")
+    check_h(h, h64, margin)
+    _check_bound(orc, h, g, 30, mask, minf)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("n", [1, 127, 129, 1000])
+def test_c1_regression(P, ctx, orc, prec, n):
+    Ws, bs, hid = _net(P, ctx, W.NET_C1, P.DOM_STP4, prec, P.HEAD_REGRESSION, 1)
+    s = W.random_stp_states(4, n, 50 + n)
+    g = _g(n, n + 2)
+    h, mask, minf, y = P.heur_submit_batch(ctx, hid, P.DOM_STP4, s, g, 60, want_y=True)
+    y64, h64, margin = oracle_net(orc, 1, Ws, bs, prec, s, "regression", True)
+    check_logits(y, y64, prec)
+    check_h(h, h64, margin)
+    _check_bound(orc, h, g, 60, mask, minf)
+
+
+def test_c1_regression_without_md_exposes_rounding(P, ctx, orc):
+    # without the max with Manhattan distance the integer h is the network's own rounding
+    Ws, bs = W.net_weights(**W.NET_C1)
+    Ws[-1] = Ws[-1] * 20.0  # spread y over many integers
+    hid = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, PREC["bf16"], P.HEAD_REGRESSION, 0)
+    n = 2000
+    s = W.random_stp_states(4, n, 77)
+    h, mask, minf, y = P.heur_submit_batch(ctx, hid, P.DOM_STP4, s, np.zeros(n, np.uint8), 255,
+                                           want_y=True)
+    y64, h64, margin = oracle_net(orc, 1, Ws, bs, "bf16", s, "regression", False)
+    check_logits(y, y64, "bf16")
+    assert len(set(h64.tolist())) > 5
+    check_h(h, h64, margin)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("n", [1, 129, 1000])
+def test_c2_classifier(P, ctx, orc, prec, n):
+    Ws, bs, hid = _net(P, ctx, W.NET_C2, P.DOM_RC3, prec, P.HEAD_CLASSIFIER, 0)
+    s = W.random_rc_states(n, 60 + n)
+    s[0] = W.rc_goal()
+    g = _g(n, n + 3, 20)
+    h, mask, minf, y = P.heur_submit_batch(ctx, hid, P.DOM_RC3, s.reshape(-1), g, 25, want_y=True,
+                                           n_out=21)
+    y64, h64, margin = oracle_net(orc, 2, Ws, bs, prec, s, "classifier", False)
+    check_logits(y, y64, prec)
+    nm = check_h(h, h64, margin)
+    assert h[0] == 0
+    _check_bound(orc, h, g, 25, mask, minf)
+    print(f"margin mismatches: {nm} of {n}")
+
+
+def test_c1_full_batch_sampled(P, ctx, orc):
+    """The bench's launch shape (8192 states, BF16): every h checked against the rule on the
+    GPU's own y, and a sample of rows against the oracle."""
+    Ws, bs, hid = _net(P, ctx, W.NET_C1, P.DOM_STP4, "bf16", P.HEAD_REGRESSION, 1)
+    n = 8192
+    s = W.random_stp_states(4, n, 8192)
+    g = _g(n, 5)
+    h, mask, minf, y = P.heur_submit_batch(ctx, hid, P.DOM_STP4, s, g, 60, want_y=True)
+    idx = np.random.default_rng(0).choice(n, 512, replace=False)
+    y64, h64, margin = oracle_net(orc, 1, Ws, bs, "bf16", s[idx], "regression", True)
+    check_logits(y[idx], y64, "bf16")
+    check_h(h[idx], h64, margin)
+    _check_bound(orc, h, g, 60, mask, minf)
+
+
+def test_device_entry_matches_host_entry(P, ctx):
+    import torch
+    Ws, bs, hid = _net(P, ctx, W.NET_C1, P.DOM_STP4, "bf16", P.HEAD_REGRESSION, 1)
+    n = 3000
+    s = W.random_stp_states(4, n, 99)
+    g = _g(n, 9)
+    h, mask, minf = P.heur_submit_batch(ctx, hid, P.DOM_STP4, s, g, 55)
+    dev = torch.device("cuda:0")
+    ds = torch.from_numpy(s.view(np.int64)).to(dev)
+    dg = torch.from_numpy(g).to(dev)
+    dh = torch.empty(n, dtype=torch.uint8, device=dev)
+    dm = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
+    dmin = torch.empty(1, dtype=torch.int32, device=dev)
+    for _ in range(2):
+        P.heur_eval_device(ctx, hid, P.DOM_STP4, ds, dg, 55, n, dh, dm, dmin,
+                           stream=torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert np.array_equal(dh.cpu().numpy(), h)
+        assert np.array_equal(dm.cpu().numpy().view(np.uint32), mask)
+        assert int(dmin.cpu().numpy().view(np.uint32)[0]) == minf
+    assert P.cbdfs_device_status(ctx) == 0
