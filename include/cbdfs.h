@@ -54,6 +54,7 @@ typedef enum { CBDFS_ALGO_IDA = 0, CBDFS_ALGO_BTS = 1 } cbdfs_algo;
 /* Built-in heuristic ids (network and PDB ids from the load calls are >= 0). */
 #define CBDFS_HEUR_ZERO (-1)    /* h = 0 */
 #define CBDFS_HEUR_MD (-2)      /* Manhattan distance, sliding-tile domains only */
+#define CBDFS_HEUR_NONE (-100)  /* "no heuristic" (cbdfs_search_cfg.fixed_tree_heur: off) */
 
 typedef struct cbdfs_ctx cbdfs_ctx;
 
@@ -205,8 +206,9 @@ typedef struct {
     uint32_t timeout_us;    /* flush a partly filled batch after this long (paper: 4 ms) */
     int complete_final;     /* finish the iteration that reaches a goal and return the least
                                goal cost in it (deterministic counts); 0 = stop at the first */
-    int fixed_tree_heur;    /* -1: prune with heur_id; else prune with this heuristic while
-                               still evaluating heur_id on every generated node */
+    int fixed_tree_heur;    /* CBDFS_HEUR_NONE: prune with heur_id; else prune with this
+                               heuristic while still evaluating heur_id on every generated node
+                               (the paper's fixed-tree evaluation) */
     uint64_t bts_n0;        /* BTS: initial growth base (paper: 10,000) */
     int bts_c1, bts_c2;     /* BTS: accept >= c1*N expansions, limit c2*N (0 = 2 and 8) */
     uint64_t node_limit;    /* stop with ECANCELED after this many expansions; 0 = none */

@@ -36,7 +36,7 @@ DOM_STP3, DOM_STP4, DOM_RC3 = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 HEAD_REGRESSION, HEAD_CLASSIFIER = 0, 1
 ALGO_IDA, ALGO_BTS = 0, 1
-HEUR_ZERO, HEUR_MD = -1, -2
+HEUR_ZERO, HEUR_MD, HEUR_NONE = -1, -2, -100
 MAX_ITERS = 256
 
 _STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ETIMEDOUT", -4: "EDEVICE", -5: "ECANCELED",

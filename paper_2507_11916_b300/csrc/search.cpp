@@ -823,7 +823,7 @@ int cbdfs_solve(cbdfs_ctx *ctx, int domain, const uint64_t *start, int algo, int
                (h == CBDFS_HEUR_MD && domain == CBDFS_DOM_RC3);
     };
     if (bad_heur(heur_id)) return fail(CBDFS_EINVAL, "heuristic id %d", heur_id);
-    if (cfg.fixed_tree_heur != -1 && bad_heur(cfg.fixed_tree_heur))
+    if (cfg.fixed_tree_heur != CBDFS_HEUR_NONE && bad_heur(cfg.fixed_tree_heur))
         return fail(CBDFS_EINVAL, "fixed-tree heuristic id %d", cfg.fixed_tree_heur);
     memset(out, 0, sizeof(*out));
     out->cost = -1;
@@ -834,7 +834,7 @@ int cbdfs_solve(cbdfs_ctx *ctx, int domain, const uint64_t *start, int algo, int
     Solver sv(c, domain);
     sv.cfg = cfg;
     sv.heur = heur_id;
-    sv.prune = cfg.fixed_tree_heur != -1 ? cfg.fixed_tree_heur : heur_id;
+    sv.prune = cfg.fixed_tree_heur != CBDFS_HEUR_NONE ? cfg.fixed_tree_heur : heur_id;
     if (cfg.time_limit_s > 0)
         sv.deadline = t0 + std::chrono::microseconds((int64_t)(cfg.time_limit_s * 1e6));
     // take every free host slot (at least one; waits for one if all are busy)
@@ -894,7 +894,7 @@ void cbdfs_search_defaults(cbdfs_search_cfg *cfg) {
     cfg->batch = 4096;
     cfg->timeout_us = 4000;
     cfg->complete_final = 1;
-    cfg->fixed_tree_heur = -1;
+    cfg->fixed_tree_heur = CBDFS_HEUR_NONE;
     cfg->bts_n0 = 10000;
     cfg->bts_c1 = 2;
     cfg->bts_c2 = 8;

@@ -27,6 +27,12 @@ def ctx(P):
     P.cbdfs_destroy(c)
 
 
+def solve(P, ctx, *a, **kw):
+    """cbdfs_solve with a time limit, so that a wrong tree cannot run on for long."""
+    kw.setdefault("time_limit_s", 60.0)
+    return P.cbdfs_solve(ctx, *a, **kw)
+
+
 def _iters(r):
     return [list(map(int, t)) for t in r["iters"]]
 
@@ -35,7 +41,7 @@ def _iters(r):
                                                           (3, 5, 4, 18), (8, 32, 2, 1024)])
 def test_c0_ida_md_counts_match_oracle(P, ctx, threads, work_num, d_init, batch):
     for row in GOLD["instances"]:
-        r = P.cbdfs_solve(ctx, P.DOM_STP3, row["state"], P.ALGO_IDA, P.HEUR_MD, threads=threads,
+        r = solve(P, ctx, P.DOM_STP3, row["state"], P.ALGO_IDA, P.HEUR_MD, threads=threads,
                           work_num=work_num, d_init=d_init, batch=batch, timeout_us=200)
         assert r["cost"] == row["cost"]
         assert _iters(r) == row["iters"]
@@ -56,11 +62,11 @@ def test_c0_network_heuristic_and_fixed_tree(P, ctx, orc):
 
     for row in GOLD["instances"][:8]:
         want = orc.ida_star(orc.DOM_STP3, row["state"], orc.Heur(fn=h_nn))
-        r = P.cbdfs_solve(ctx, P.DOM_STP3, row["state"], P.ALGO_IDA, hid, threads=4, work_num=8,
+        r = solve(P, ctx, P.DOM_STP3, row["state"], P.ALGO_IDA, hid, threads=4, work_num=8,
                           batch=256, timeout_us=200)
         assert r["cost"] == want["cost"]
         assert _iters(r) == [list(t) for t in want["iters"]]
-        f = P.cbdfs_solve(ctx, P.DOM_STP3, row["state"], P.ALGO_IDA, hid, threads=4, work_num=8,
+        f = solve(P, ctx, P.DOM_STP3, row["state"], P.ALGO_IDA, hid, threads=4, work_num=8,
                           batch=256, timeout_us=200, fixed_tree_heur=P.HEUR_MD)
         assert _iters(f) == row["iters"]
         # the network ran on every batch (the initial tree is evaluated once and cached)
@@ -74,7 +80,7 @@ def test_c0_pdb_heuristic(P, ctx, orc):
     pdb = orc.PDB(3, pats, tabs)
     for row in GOLD["instances"][:10]:
         want = orc.ida_star(orc.DOM_STP3, row["state"], orc.Heur(orc.H_PDB, pdb=pdb))
-        r = P.cbdfs_solve(ctx, P.DOM_STP3, row["state"], P.ALGO_IDA, hid, threads=2, work_num=4,
+        r = solve(P, ctx, P.DOM_STP3, row["state"], P.ALGO_IDA, hid, threads=2, work_num=4,
                           batch=128, timeout_us=200)
         assert r["cost"] == want["cost"] == row["cost"]
         assert _iters(r) == [list(t) for t in want["iters"]]
@@ -84,7 +90,7 @@ def test_15_puzzle_md_counts(P, ctx, orc):
     for i in range(6):
         s = orc.stp_apply_walk(4, W.stp_walk(4, 36, W.seed_for(W.TAG_C1, 5000 + i)))
         want = orc.ida_star(orc.DOM_STP4, s, orc.Heur(orc.H_MD))
-        r = P.cbdfs_solve(ctx, P.DOM_STP4, s, P.ALGO_IDA, P.HEUR_MD, threads=8, work_num=16,
+        r = solve(P, ctx, P.DOM_STP4, s, P.ALGO_IDA, P.HEUR_MD, threads=8, work_num=16,
                           batch=2048, timeout_us=300)
         assert r["cost"] == want["cost"]
         assert _iters(r) == [list(t) for t in want["iters"]]
@@ -94,7 +100,7 @@ def test_rc_zero_heuristic_counts(P, ctx, orc):
     for i in range(3):
         s = orc.rc_apply_seq(W.rc_scramble(4, W.seed_for(W.TAG_C2, 100 + i)))
         want = orc.ida_star(orc.DOM_RC3, s, orc.Heur(orc.H_ZERO))
-        r = P.cbdfs_solve(ctx, P.DOM_RC3, s, P.ALGO_IDA, P.HEUR_ZERO, threads=4, work_num=16,
+        r = solve(P, ctx, P.DOM_RC3, s, P.ALGO_IDA, P.HEUR_ZERO, threads=4, work_num=16,
                           batch=4096, timeout_us=300)
         assert r["cost"] == want["cost"]
         assert _iters(r) == [list(t) for t in want["iters"]]
@@ -107,7 +113,7 @@ def test_rc_classifier_fixed_tree(P, ctx, orc):
     hid = P.cbdfs_net_load(ctx, P.DOM_RC3, Ws, bs, PREC["bf16"], P.HEAD_CLASSIFIER, 0)
     s = orc.rc_apply_seq(W.rc_scramble(4, W.seed_for(W.TAG_C2, 7)))
     want = orc.ida_star(orc.DOM_RC3, s, orc.Heur(orc.H_ZERO))
-    r = P.cbdfs_solve(ctx, P.DOM_RC3, s, P.ALGO_IDA, hid, threads=8, work_num=16, batch=4096,
+    r = solve(P, ctx, P.DOM_RC3, s, P.ALGO_IDA, hid, threads=8, work_num=16, batch=4096,
                       timeout_us=300, fixed_tree_heur=P.HEUR_ZERO)
     assert r["cost"] == want["cost"] and _iters(r) == [list(t) for t in want["iters"]]
     assert r["batches"] > 0 and r["evaluated"] >= r["expanded"]
@@ -117,7 +123,7 @@ def test_rc_classifier_fixed_tree(P, ctx, orc):
 def test_bts_matches_oracle_schedule(P, ctx, orc, n0):
     for row in GOLD["instances"][:10]:
         want = orc.bts(orc.DOM_STP3, row["state"], orc.Heur(orc.H_MD), n0=n0)
-        r = P.cbdfs_solve(ctx, P.DOM_STP3, row["state"], P.ALGO_BTS, P.HEUR_MD, threads=4,
+        r = solve(P, ctx, P.DOM_STP3, row["state"], P.ALGO_BTS, P.HEUR_MD, threads=4,
                           work_num=8, batch=256, timeout_us=200, bts_n0=n0)
         assert r["cost"] == want["cost"] == row["cost"]
         got = [(b, lim, e, g, c) for (b, e, g), lim, c in zip(r["iters"], r["iter_limit"], r["iter_cut"])]
@@ -130,16 +136,16 @@ def test_bts_matches_oracle_schedule(P, ctx, orc, n0):
 
 def test_solve_errors(P, ctx):
     with pytest.raises(P.CbdfsError):
-        P.cbdfs_solve(ctx, P.DOM_RC3, W.rc_goal(), P.ALGO_IDA, P.HEUR_MD)
+        solve(P, ctx, P.DOM_RC3, W.rc_goal(), P.ALGO_IDA, P.HEUR_MD)
     with pytest.raises(P.CbdfsError):
-        P.cbdfs_solve(ctx, P.DOM_STP3, W.stp_goal(3), P.ALGO_IDA, P.HEUR_MD, threads=0)
-    r = P.cbdfs_solve(ctx, P.DOM_STP3, W.stp_goal(3), P.ALGO_IDA, P.HEUR_MD)
+        solve(P, ctx, P.DOM_STP3, W.stp_goal(3), P.ALGO_IDA, P.HEUR_MD, threads=0)
+    r = solve(P, ctx, P.DOM_STP3, W.stp_goal(3), P.ALGO_IDA, P.HEUR_MD)
     assert r["cost"] == 0 and r["iters"] == [(0, 0, 0)]
 
 
 def test_node_limit_stops(P, ctx, orc):
     s = orc.stp_apply_walk(4, W.stp_walk(4, 200, W.seed_for(W.TAG_C1, 0)))
     with pytest.raises(P.CbdfsError) as e:
-        P.cbdfs_solve(ctx, P.DOM_STP4, s, P.ALGO_IDA, P.HEUR_MD, threads=4, work_num=8,
+        solve(P, ctx, P.DOM_STP4, s, P.ALGO_IDA, P.HEUR_MD, threads=4, work_num=8,
                       batch=1024, node_limit=20000)
     assert e.value.status == P.CBDFS_ECANCELED
