@@ -169,6 +169,27 @@ int heur_eval_device(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_
                      const uint8_t *d_g, uint32_t bound, uint32_t n, uint8_t *d_h,
                      uint32_t *d_mask, uint32_t *d_minf, float *d_y, void *stream);
 
+/* Like heur_eval_device, for callers that cannot allocate device memory when they evaluate
+ * a batch (a real-time or latency-budgeted caller that must not enter the allocator, or a
+ * process whose device memory another framework's allocator owns).  The paper has no
+ * counterpart; this is a library-usage variant.
+ *   - The call allocates nothing: the layers' activation scratch is a file-scope device
+ *     array of 2 x 16 MiB that every device holding the library keeps until the process
+ *     exits.  The network (or PDB) must already be loaded on the context.
+ *   - Limit: the padded batch (n rounded up to 128) times the widest hidden layer times 2
+ *     bytes (4 for FP32 networks) must fit 16 MiB, e.g. 8192 states of a 1024-wide BF16
+ *     network; a larger n fails with CBDFS_EINVAL and says the largest n that fits.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before any
+ *     stream capture.
+ *   - Every call shares the array, which keeps the previous call's contents; nothing in it
+ *     needs to start at zero (each call writes every activation row it reads).  Calls that
+ *     overlap on the GPU (other streams, other threads) race on the array: order them.
+ * Errors: EINVAL (arguments, size limit), EDEVICE. */
+int heur_eval_device_static(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_states,
+                            const uint8_t *d_g, uint32_t bound, uint32_t n, uint8_t *d_h,
+                            uint32_t *d_mask, uint32_t *d_minf, void *stream);
+
 /* Like heur_eval_device, and then waits: stage_ms[i] receives the device time of the i-th
  * kernel of the pipeline (network: layer 1 .. layer L-1, then the head; PDB / built-in: the
  * one kernel), measured with CUDA events recorded between the launches on `stream`.

@@ -107,6 +107,8 @@ _lib.heur_submit_batch.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ct
 _lib.heur_eval_device.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint32,
                                   ctypes.c_uint32, _vp, _vp, _vp, _vp, _vp]
 _lib.cbdfs_device_status.argtypes = [_vp]
+_lib.heur_eval_device_static.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint32,
+                                         ctypes.c_uint32, _vp, _vp, _vp, _vp]
 _lib.cbdfs_eval_profile.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint32,
                                     ctypes.c_uint32, _vp, _vp, _vp, _vp,
                                     ctypes.POINTER(ctypes.c_float), ctypes.c_int,
@@ -124,6 +126,7 @@ _lib.cbdfs_cancel.restype = None
 # every symbol include/cbdfs.h declares
 EXPORTED = ["cbdfs_create", "cbdfs_destroy", "cbdfs_last_error", "cbdfs_mem_used", "cbdfs_net_load",
             "cbdfs_pdb_load", "pdb_build", "heur_submit_batch", "heur_eval_device",
+            "heur_eval_device_static",
             "cbdfs_device_status", "cbdfs_eval_profile", "cbdfs_apply_moves", "cbdfs_manhattan", "cbdfs_solve",
             "cbdfs_search_defaults", "cbdfs_cancel"]
 
@@ -227,6 +230,15 @@ def heur_eval_device(ctx, heur_id, domain, d_states, d_g, bound, n, d_h, d_mask,
     s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
     _check(_lib.heur_eval_device(ctx, heur_id, domain, _ptr(d_states), _ptr(d_g), bound, n,
                                  _ptr(d_h), _ptr(d_mask), _ptr(d_minf), _ptr(d_y), s))
+
+
+def heur_eval_device_static(ctx, heur_id, domain, d_states, d_g, bound, n, d_h, d_mask, d_minf,
+                            stream=None):
+    """heur_eval_device without any device allocation in the call: the activation scratch is
+    the library's file-scope device array (see include/cbdfs.h for its limit)."""
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(_lib.heur_eval_device_static(ctx, heur_id, domain, _ptr(d_states), _ptr(d_g), bound, n,
+                                        _ptr(d_h), _ptr(d_mask), _ptr(d_minf), s))
 
 
 def cbdfs_eval_profile(ctx, heur_id, domain, d_states, d_g, bound, n, d_h, d_mask, d_minf,
