@@ -472,14 +472,24 @@ def quantise_weights(Ws, prec: str):
     raise ValueError(prec)
 
 
-def mlp_forward(Ws, bs, X, return_hidden=False):
-    """z_l = a_{l-1} W_l^T + b_l with ReLU on every layer but the last, in float64."""
+def mlp_forward(Ws, bs, X, return_hidden=False, act_scales=None):
+    """z_l = a_{l-1} W_l^T + b_l with ReLU on every layer but the last, in float64.
+
+    act_scales (optional): emulate E4M3 storage of the activations that feed a following
+    hidden layer: hidden layer l's output (l < L-2) becomes s_l * E4M3(float32(a) *
+    float32(1/s_l)); the last hidden layer's output, which feeds the float32 last layer,
+    is not rounded."""
     a = np.asarray(X, dtype=np.float64)
     hidden = []
+    L = len(Ws)
     for l, (W, b) in enumerate(zip(Ws, bs)):
         z = a @ np.asarray(W, np.float64).T + np.asarray(b, np.float64)
-        if l < len(Ws) - 1:
+        if l < L - 1:
             a = np.maximum(z, 0.0)
+            if act_scales is not None and l < L - 2:
+                inv = np.float32(1.0) / np.float32(act_scales[l])
+                q = e4m3_round(a.astype(np.float32) * inv)
+                a = q.astype(np.float64) * float(np.float32(act_scales[l]))
             hidden.append(a)
         else:
             a = z

@@ -36,6 +36,51 @@ int pdb_gather(int domain, const PdbParams &P, const uint64_t *states, uint32_t 
 int pdb_build_device(Ctx *c, int side, const int *tiles, int k, uint8_t *table, cudaStream_t st);
 uint64_t npk(int n, int k);
 
+constexpr int kChainBN = 256;
+constexpr int kChainMaxC = 32;
+struct ChainMaps {
+    CUtensorMap w[kMaxLayers];
+    CUtensorMap a[kMaxLayers];
+};
+struct ChainParams {
+    int nh;
+    int dims[kMaxLayers + 1];
+    int kdim[kMaxLayers];
+    int nt[kMaxLayers];
+    int tile_start[kMaxLayers + 1];
+    int mblocks;
+    uint32_t n;
+    const uint64_t *states;
+    void *act[2];
+    const float *bias[kMaxLayers];
+    float acc_scale[kMaxLayers], out_qscale[kMaxLayers];
+    int *counters;
+    float *partial;
+    int rows_pad;
+    int C;
+    int head_kind, max_with_md;
+    const float *w_last, *b_last;
+    const uint8_t *g;
+    uint32_t bound;
+    uint8_t *h;
+    uint32_t *mask, *minf;
+    float *y;
+    int *err;
+};
+int chain_launch(int domain, bool fp8, const ChainMaps &maps, const ChainParams &P, int grid, cudaStream_t st);
+
+// the fused chain runs networks whose hidden widths are multiples of 256 and whose last
+// layer has at most 32 outputs
+static bool chain_ok(const NetGPU &net) {
+    if (net.prec == CBDFS_PREC_FP32 || net.dims[net.L] > kChainMaxC) return false;
+    for (int l = 1; l < net.L; ++l)
+        if (net.dims[l] % kChainBN) return false;
+    return true;
+}
+static size_t chain_partial_floats(const NetGPU &net) {
+    return (size_t)(net.dims[net.L - 1] / kChainBN) * net.dims[net.L];
+}
+
 // ------------------------------------------------------------------------------------
 // errors
 // ------------------------------------------------------------------------------------
@@ -189,6 +234,28 @@ int ensure_act(Ctx *c, size_t width) {
     return CBDFS_OK;
 }
 
+// chain scratch of every slot: tile counters, and head partials of `floats` per row
+int ensure_chain(Ctx *c, size_t floats) {
+    const size_t cbytes = sizeof(int) * (kMaxLayers + 1) * (c->max_batch_pad / kBM);
+    for (auto &s : c->slots)
+        if (!s.counters) {
+            int rc = dev_alloc(c, (void **)&s.counters, cbytes);
+            if (rc) return rc;
+        }
+    if (floats <= c->partial_floats) return CBDFS_OK;
+    const size_t pbytes = sizeof(float) * floats * c->max_batch_pad;
+    for (auto &s : c->slots) {
+        dev_free(c, s.partial, s.partial_bytes);
+        s.partial = nullptr;
+        s.partial_bytes = 0;
+        int rc = dev_alloc(c, (void **)&s.partial, pbytes);
+        if (rc) return rc;
+        s.partial_bytes = pbytes;
+    }
+    c->partial_floats = floats;
+    return CBDFS_OK;
+}
+
 const CUtensorMap *act_map(Slot &s, Ctx *c, int buf, int K, int elem_bytes) {
     const long long key = ((long long)buf << 40) | ((long long)elem_bytes << 32) | K;
     auto it = s.tm_act.find(key);
@@ -213,6 +280,63 @@ static int mark(Slot &s, cudaStream_t st) {
     CUDA_TRY(cudaEventRecord(e, st));
     s.prof->push_back(e);
     return CBDFS_OK;
+}
+
+// the whole network in one persistent launch (mlp_chain.cu)
+static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint64_t *d_states,
+                     const uint8_t *d_g, uint32_t bound, uint32_t n, uint8_t *d_h, uint32_t *d_mask,
+                     uint32_t *d_minf, float *d_y, cudaStream_t st) {
+    const bool fp8 = net.prec == CBDFS_PREC_FP8;
+    const int eb = fp8 ? 1 : 2;
+    const int L = net.L, nh = L - 1;
+    ChainMaps maps;
+    ChainParams P{};
+    P.nh = nh;
+    for (int l = 0; l <= L; ++l) P.dims[l] = net.dims[l];
+    const uint32_t rows_pad = (n + kBM - 1) / kBM * kBM;
+    P.mblocks = rows_pad / kBM;
+    P.rows_pad = rows_pad;
+    P.n = n;
+    int max_tiles = 0;
+    P.tile_start[0] = 0;
+    for (int l = 0; l < nh; ++l) {
+        maps.w[l] = net.tm_w[l];
+        if (l > 0) {
+            const CUtensorMap *m = act_map(s, c, (l - 1) & 1, net.dims[l], eb);
+            if (!m) return CBDFS_EDEVICE;
+            maps.a[l] = *m;
+        } else {
+            maps.a[0] = net.tm_w[0];  // unused
+        }
+        P.kdim[l] = l == 0 ? net.k1pad : net.dims[l];
+        P.nt[l] = net.dims[l + 1] / kChainBN;
+        P.tile_start[l + 1] = P.tile_start[l] + P.nt[l] * P.mblocks;
+        max_tiles = std::max(max_tiles, P.nt[l] * P.mblocks);
+        P.bias[l] = net.b32[l];
+        P.acc_scale[l] = fp8 ? net.w_scale[l] * (l == 0 ? 1.f : net.a_scale[l - 1]) : 1.f;
+        P.out_qscale[l] = fp8 ? 1.f / net.a_scale[l] : 1.f;
+    }
+    P.states = d_states;
+    P.act[0] = s.act[0];
+    P.act[1] = s.act[1];
+    P.counters = s.counters;
+    P.partial = s.partial;
+    P.C = net.dims[L];
+    P.head_kind = net.head;
+    P.max_with_md = net.max_with_md;
+    P.w_last = net.w32[L - 1];
+    P.b_last = net.b32[L - 1];
+    P.g = d_g;
+    P.bound = bound;
+    P.h = d_h;
+    P.mask = d_mask;
+    P.minf = d_minf;
+    P.y = d_y;
+    P.err = c->d_err;
+    CUDA_TRY(cudaMemsetAsync(s.counters, 0, sizeof(int) * (nh + 1) * P.mblocks, st));
+    const int grid = std::min(c->num_sms, max_tiles);
+    int rc = chain_launch(domain, fp8, maps, P, grid, st);
+    return rc ? rc : mark(s, st);
 }
 
 int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states, const uint8_t *d_g,
@@ -261,6 +385,8 @@ int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
         return rc ? rc : mark(s, st);
     }
     const bool fp8 = net.prec == CBDFS_PREC_FP8;
+    if (s.counters && s.partial && chain_ok(net) && chain_partial_floats(net) <= c->partial_floats)
+        return run_chain(c, s, net, domain, d_states, d_g, bound, n, d_h, d_mask, d_minf, d_y, st);
     int cur = 0;
     for (int l = 0; l < L - 1; ++l) {
         const bool first = l == 0;
@@ -311,6 +437,8 @@ void cbdfs_destroy(cbdfs_ctx *ctx) {
         dev_free(c, s.d_h, c->max_batch_pad);
         dev_free(c, s.d_mask, c->max_batch_pad / 8);
         dev_free(c, s.d_minf, 4);
+        dev_free(c, s.counters, sizeof(int) * (kMaxLayers + 1) * (c->max_batch_pad / kBM));
+        dev_free(c, s.partial, s.partial_bytes);
         if (s.stream) cudaStreamDestroy(s.stream);
         if (s.done) cudaEventDestroy(s.done);
     }
@@ -338,6 +466,8 @@ int cbdfs_create(const cbdfs_config *cfg, cbdfs_ctx **out) {
     CUDA_TRY(cudaSetDevice(cfg->device));
     Ctx *c = new Ctx();
     c->device = cfg->device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, cfg->device);
+    if (c->num_sms <= 0) c->num_sms = 1;
     c->mem_budget = cfg->mem_budget;
     c->max_batch = cfg->max_batch ? cfg->max_batch : 65536;
     c->max_batch_pad = (c->max_batch + kBM - 1) / kBM * kBM;
@@ -450,6 +580,7 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
         }
     }
     if ((size_t)d->dims[L] * 4 * 4 > 48 * 1024) return fail(CBDFS_EINVAL, "output width too large");
+    if (chain_ok(N) && (rc = ensure_chain(c, chain_partial_floats(N)))) return rc;
     c->nets.push_back(std::move(net));
     c->heur_kind.push_back(0);
     c->heur_index.push_back((int)c->nets.size() - 1);

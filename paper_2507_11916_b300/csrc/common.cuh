@@ -41,6 +41,7 @@ enum DevErr : int {
     DEVERR_STAGE_EMPTY = 2,  // producer waited for the MMA to free a stage
     DEVERR_ACCUM = 3,        // epilogue waited for the accumulator
     DEVERR_ENCODE = 4,
+    DEVERR_DEPENDENCY = 5,   // a chain tile waited for the previous layer's row block
 };
 
 // ------------------------------------------------------------------------------------
@@ -86,6 +87,10 @@ struct Slot {
     cudaEvent_t done = nullptr;
     bool busy = false;
     std::vector<cudaEvent_t> *prof = nullptr;  // when set, an event follows every launch
+    // fused-chain scratch (null: the per-layer kernels are used)
+    int *counters = nullptr;           // tile counts per (layer, row block) + head counts
+    float *partial = nullptr;          // head partials [n-tiles][rows][C]
+    size_t partial_bytes = 0;
 };
 
 struct Ctx {
@@ -104,6 +109,8 @@ struct Ctx {
     std::mutex device_call_mu;         // heur_eval_device scratch (slot 0)
     std::atomic<int> cancel{0};
     size_t max_width = 0;
+    size_t partial_floats = 0;         // per-row head partials the chain scratch holds
+    int num_sms = 0;
 };
 
 // allocation through the context's budget
@@ -174,12 +181,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 }
 // Bounded wait: gives up after kWaitNs (or 2^30 polls), records `code` in *err and
 // returns false.  Never traps.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code) {
+// A wait also gives up at once when the error flag is already set (another wait failed).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code,
+                                          unsigned long long limit_ns = kWaitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t i = 1; i < (1u << 30); ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 63) == 0 && globaltimer() - t0 > kWaitNs) break;
+        if ((i & 63) == 0) {
+            if (*reinterpret_cast<volatile int *>(err) != 0) return false;
+            if (globaltimer() - t0 > limit_ns) break;
+        }
     }
     atomicExch(err, code);
     return false;

@@ -1,0 +1,503 @@
+// mlp_chain.cu -- the whole network heuristic in one persistent launch.
+//
+// Every hidden layer is cut into 128-state x 256-output tiles; the tiles of all layers form
+// one sequence, layer by layer and, inside a layer, row block by row block.  Each CTA (one
+// per SM, a cooperative launch, so all are resident) takes tiles i, i+G, i+2G, ... .  A tile
+// of layer l+1 for row block m starts as soon as every tile of layer l for that row block is
+// stored: the epilogue counts finished tiles per (layer, row block) with a release atomic and
+// the producer waits for the count with a bounded acquire poll.  Dependencies only point to
+// earlier tiles of the sequence, and all CTAs are resident, so the earliest unfinished tile
+// can always proceed.  Activations of a row block stay in L2 between layers.
+//
+// Per CTA (192 threads):
+//   warp 0      producer: for layer 0 the whole warp writes the one-hot A k-block (decoded
+//               from the packed states) into the stage in the 128-byte swizzled layout; for
+//               later layers TMA loads the activation k-block; TMA loads the weight k-block
+//   warp 1      owns 512 TMEM columns (two 256-column FP32 accumulators); one lane issues
+//               tcgen05.mma and commits stages back to the producer and finished
+//               accumulators to the epilogue, so one tile's epilogue overlaps the next main loop
+//   warps 2..5  epilogue: bias + ReLU + BF16 (or scaled E4M3) store of the activation tile,
+//               or, for the last hidden layer, the FP32 last layer as per-tile partial dot
+//               products; the CTA that stores the last partial of a row block adds the
+//               partials in tile order (deterministic), applies the integer-h rule (rint or
+//               argmax, max with Manhattan distance, goal = 0) and the bound test (mask bits
+//               by ballot, least f above the bound by warp minimum + atomicMin).
+// Every wait is bounded (2 s of %globaltimer) and reports through the error flag.
+#include <cuda_fp8.h>
+
+#include "common.cuh"
+
+namespace cbdfs {
+
+constexpr int kChainBN = 256;
+constexpr int kChainStages = 4;
+constexpr int kChainThreads = 192;
+constexpr int kMaxHeadC = 32;
+
+struct ChainMaps {
+    CUtensorMap w[kMaxLayers];  // weights of hidden layer l, [N][K] K-major
+    CUtensorMap a[kMaxLayers];  // activations read by hidden layer l >= 1
+};
+
+struct ChainParams {
+    int nh;                        // hidden layers (tensor-core layers) = L-1
+    int dims[kMaxLayers + 1];
+    int kdim[kMaxLayers];          // K of hidden layer l (layer 0: padded one-hot width)
+    int nt[kMaxLayers];            // n-tiles of hidden layer l
+    int tile_start[kMaxLayers + 1];
+    int mblocks;
+    uint32_t n;
+    const uint64_t *states;
+    void *act[2];
+    const float *bias[kMaxLayers];
+    float acc_scale[kMaxLayers], out_qscale[kMaxLayers];
+    int *counters;                 // [nh][mblocks] tile counts, then [mblocks] head counts
+    float *partial;                // [nt_last][rows_pad][C]
+    int rows_pad;
+    int C;                         // outputs of the last layer (fused head)
+    int head_kind, max_with_md;
+    const float *w_last, *b_last;  // [C][dims[nh]], [C]
+    const uint8_t *g;
+    uint32_t bound;
+    uint8_t *h;
+    uint32_t *mask, *minf;
+    float *y;
+    int *err;
+};
+
+namespace {
+
+using namespace dev;
+
+constexpr int kStageA = kBM * 128;
+constexpr int kStageB = kChainBN * 128;
+
+__device__ __forceinline__ uint32_t ld_acquire(const int *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void epi_bar() {  // the 128 epilogue threads
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+
+// bounded wait until *p >= want (acquire)
+__device__ __forceinline__ bool wait_count(const int *p, int want, int *err) {
+    if ((int)ld_acquire(p) >= want) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t i = 1; i < (1u << 28); ++i) {
+        if ((int)ld_acquire(p) >= want) return true;
+        __nanosleep(64);
+        if ((i & 63) == 0) {
+            if (*reinterpret_cast<volatile int *>(err) != 0) return false;
+            if (globaltimer() - t0 > kWaitNs) break;
+        }
+    }
+    atomicExch(err, DEVERR_DEPENDENCY);
+    return false;
+}
+
+struct Tile {
+    int l, m, n;
+};
+__device__ __forceinline__ Tile tile_of(const ChainParams &P, int t) {
+    int l = 0;
+    while (l + 1 < P.nh && t >= P.tile_start[l + 1]) ++l;
+    const int local = t - P.tile_start[l];
+    return Tile{l, local / P.nt[l], local % P.nt[l]};
+}
+
+// one-hot k-block of 128 rows into a stage (128B-swizzled K-major), by the 32 producer lanes
+template <int DOMAIN, bool FP8>
+__device__ __forceinline__ void onehot_kblock(uint8_t *A, const ChainParams &P, int m, int kb,
+                                              const uint64_t (&st)[4][2], int lane) {
+    constexpr int KBLK = FP8 ? 128 : 64;
+    const int k0 = kb * KBLK;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int r = lane + 32 * q;
+        uint8_t *row = A + r * 128;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) reinterpret_cast<uint4 *>(row)[c] = make_uint4(0, 0, 0, 0);
+        if ((uint32_t)(m * kBM + r) >= P.n) continue;
+        auto put = [&](int j) {
+            const int w = j - k0;
+            if (w < 0 || w >= KBLK) return;
+            if (FP8) {
+                row[(((w >> 4) ^ (r & 7)) << 4) | (w & 15)] = 0x38;
+            } else {
+                *reinterpret_cast<uint16_t *>(row + ((((w >> 3) ^ (r & 7)) << 4) | ((w & 7) << 1))) = 0x3F80;
+            }
+        };
+        if (DOMAIN == CBDFS_DOM_RC3) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) put(c * 24 + (int)((st[q][0] >> (5 * c)) & 31u));
+#pragma unroll
+            for (int e = 0; e < 12; ++e) put(192 + e * 24 + (int)((st[q][1] >> (5 * e)) & 31u));
+        } else {
+            constexpr int N = DOMAIN == CBDFS_DOM_STP3 ? 9 : 16;
+#pragma unroll
+            for (int p = 0; p < N; ++p) put((int)((st[q][0] >> (4 * p)) & 15u) * N + p);
+        }
+    }
+}
+
+template <int DOMAIN, int CMAX>
+__device__ __forceinline__ void finish_row(const ChainParams &P, uint32_t row_g, const float (&yv)[CMAX],
+                                           bool valid, int lane, int wq, int m) {
+    uint32_t f = 0xFFFFFFFFu;
+    bool pass = false;
+    if (valid) {
+        int hv;
+        if (P.head_kind == CBDFS_HEAD_REGRESSION) {
+            hv = (int)fminf(fmaxf(rintf(yv[0]), 0.f), 255.f);
+        } else {
+            int best = 0;
+            float bv = yv[0];
+#pragma unroll
+            for (int c = 1; c < CMAX; ++c)
+                if (c < P.C && yv[c] > bv) { bv = yv[c]; best = c; }
+            hv = best;
+        }
+        bool goal;
+        if (DOMAIN == CBDFS_DOM_RC3) {
+            const ulonglong2 w = reinterpret_cast<const ulonglong2 *>(P.states)[row_g];
+            goal = rc_is_goal(w.x, w.y);
+        } else {
+            constexpr int SIDE = DOMAIN == CBDFS_DOM_STP3 ? 3 : 4;
+            const uint64_t s = P.states[row_g];
+            if (P.max_with_md) hv = max(hv, manhattan<SIDE>(s));
+            goal = stp_is_goal<SIDE>(s);
+        }
+        hv = goal ? 0 : min(hv, 255);
+        P.h[row_g] = (uint8_t)hv;
+        f = (uint32_t)P.g[row_g] + (uint32_t)hv;
+        pass = f <= P.bound;
+        if (P.y)
+#pragma unroll
+            for (int c = 0; c < CMAX; ++c)
+                if (c < P.C) P.y[(size_t)row_g * P.C + c] = yv[c];
+    }
+    const uint32_t bits = __ballot_sync(0xFFFFFFFFu, pass);
+    const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, pass ? 0xFFFFFFFFu : f);
+    const uint32_t word = (uint32_t)m * 4 + wq;
+    if (lane == 0 && word < (P.n + 31) / 32) {
+        P.mask[word] = bits;
+        if (mn != 0xFFFFFFFFu) atomicMin(P.minf, mn);
+    }
+}
+
+template <int DOMAIN, bool FP8, int CMAX>
+__global__ void __launch_bounds__(kChainThreads, 1)
+k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainParams P) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *A = smem;
+    uint8_t *B = smem + kChainStages * kStageA;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(B + kChainStages * kStageB);
+    uint64_t *full = bars, *empty = bars + kChainStages;
+    uint64_t *acc_full = bars + 2 * kChainStages, *acc_empty = acc_full + 2;
+    uint64_t *drain = acc_empty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    int *flag = reinterpret_cast<int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int total = P.tile_start[P.nh];
+    const int last_l = P.nh - 1;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kChainStages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&acc_full[b]), 1);
+            mbar_init(smem_u32(&acc_empty[b]), 4);
+        }
+        mbar_init(smem_u32(drain), 1);
+        fence_mbar_init();
+    }
+    if (warp == 0 && lane == 0) {
+        for (int l = 0; l < P.nh; ++l) {
+            tma_prefetch_map(&maps.w[l]);
+            if (l) tma_prefetch_map(&maps.a[l]);
+        }
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    constexpr int KBLK = FP8 ? 128 : 64;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------- producer
+        uint32_t it = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+            const Tile T = tile_of(P, t);
+            const int KB = P.kdim[T.l] / KBLK;
+            uint64_t st[4][2];
+            if (T.l == 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t r = T.m * kBM + lane + 32 * q;
+                    st[q][0] = st[q][1] = 0;
+                    if (r < P.n) {
+                        if (DOMAIN == CBDFS_DOM_RC3) {
+                            const ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2 *>(P.states) + r);
+                            st[q][0] = w.x;
+                            st[q][1] = w.y;
+                        } else {
+                            st[q][0] = __ldg(P.states + r);
+                        }
+                    }
+                }
+            } else {
+                if (lane == 0)
+                    ok = wait_count(P.counters + (T.l - 1) * P.mblocks + T.m, P.nt[T.l - 1], P.err);
+                ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+                if (!ok) break;
+                fence_proxy_async_global();
+            }
+            for (int kb = 0; kb < KB; ++kb, ++it) {
+                const int s = it % kChainStages;
+                const uint32_t u = it / kChainStages;
+                if (it >= kChainStages) {
+                    bool w = true;
+                    if (lane == 0) w = mbar_wait(smem_u32(&empty[s]), (u - 1) & 1, P.err, DEVERR_STAGE_EMPTY);
+                    w = __shfl_sync(0xFFFFFFFFu, w, 0);
+                    if (!w) { ok = false; break; }
+                }
+                if (T.l == 0) {
+                    onehot_kblock<DOMAIN, FP8>(A + s * kStageA, P, T.m, kb, st, lane);
+                    fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) {
+                        mbar_arrive_expect_tx(smem_u32(&full[s]), kStageB);
+                        tma_load_2d(smem_u32(B + s * kStageB), &maps.w[0], smem_u32(&full[s]), kb * KBLK,
+                                    T.n * kChainBN);
+                    }
+                } else if (lane == 0) {
+                    mbar_arrive_expect_tx(smem_u32(&full[s]), kStageA + kStageB);
+                    tma_load_2d(smem_u32(A + s * kStageA), &maps.a[T.l], smem_u32(&full[s]), kb * KBLK,
+                                T.m * kBM);
+                    tma_load_2d(smem_u32(B + s * kStageB), &maps.w[T.l], smem_u32(&full[s]), kb * KBLK,
+                                T.n * kChainBN);
+                }
+                __syncwarp();
+            }
+        }
+        // every TMA load this CTA issued has landed before the CTA can exit (bounded)
+        if (lane == 0) {
+            const uint32_t first = it > kChainStages ? it - kChainStages : 0;
+            for (uint32_t j = first; j < it; ++j)
+                mbar_wait(smem_u32(&full[j % kChainStages]), (j / kChainStages) & 1, P.err,
+                          DEVERR_TMA_FULL, 100000000ull);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = FP8 ? make_idesc(kBM, kChainBN, 0, 0) : make_idesc(kBM, kChainBN, 1, 1);
+            uint32_t it = 0, i = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
+                const Tile T = tile_of(P, t);
+                const int KB = P.kdim[T.l] / KBLK;
+                const uint32_t b = i & 1, u = i >> 1;
+                if (i >= 2 && !mbar_wait(smem_u32(&acc_empty[b]), (u - 1) & 1, P.err, DEVERR_ACCUM)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + b * kChainBN;
+                for (int kb = 0; kb < KB; ++kb, ++it) {
+                    const int s = it % kChainStages;
+                    if (!mbar_wait(smem_u32(&full[s]), (it / kChainStages) & 1, P.err, DEVERR_TMA_FULL)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t ad = sw128_desc(smem_u32(A + s * kStageA));
+                    const uint64_t bd = sw128_desc(smem_u32(B + s * kStageB));
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (FP8) umma_fp8(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                        else umma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                    }
+                    umma_commit(smem_u32(&empty[s]));
+                }
+                if (ok) umma_commit(smem_u32(&acc_full[b]));
+            }
+            // all MMAs this thread issued have completed before TMEM is released (bounded)
+            umma_commit(smem_u32(drain));
+            mbar_wait(smem_u32(drain), 0, P.err, DEVERR_ACCUM, 100000000ull);
+        }
+    } else {
+        // ------------------------------------------------------------- epilogue
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        const int ep_tid = threadIdx.x - 64;
+        uint32_t i = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+            const Tile T = tile_of(P, t);
+            const uint32_t b = i & 1, u = i >> 1;
+            // after a failed wait the warps skip the work but keep every barrier, so that
+            // the four epilogue warps stay in step
+            const bool good = mbar_wait(smem_u32(&acc_full[b]), u & 1, P.err, DEVERR_ACCUM);
+            tc_fence_after();
+            const uint32_t taddr = tmem + b * kChainBN + ((uint32_t)(q * 32) << 16);
+            const uint32_t rg = T.m * kBM + row;
+            const int N = P.dims[T.l + 1];
+            const int n0 = T.n * kChainBN;
+            const float *bias = P.bias[T.l] + n0;
+            const float sc = P.acc_scale[T.l];
+            if (T.l < last_l) {
+                void *out = P.act[T.l & 1];
+                const bool out8 = FP8;  // every stored activation is read by the next layer's TMA
+                const float oq = P.out_qscale[T.l];
+#pragma unroll 1
+                for (int c = 0; c < kChainBN / 32 && good; ++c) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + c * 32, r);
+                    tmem_ld_wait();
+                    float v[32];
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        const float4 bb = __ldg(reinterpret_cast<const float4 *>(bias + c * 32 + j));
+                        v[j + 0] = fmaxf(fmaf(__uint_as_float(r[j + 0]), sc, bb.x), 0.f);
+                        v[j + 1] = fmaxf(fmaf(__uint_as_float(r[j + 1]), sc, bb.y), 0.f);
+                        v[j + 2] = fmaxf(fmaf(__uint_as_float(r[j + 2]), sc, bb.z), 0.f);
+                        v[j + 3] = fmaxf(fmaf(__uint_as_float(r[j + 3]), sc, bb.w), 0.f);
+                    }
+                    if (out8) {
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            __nv_fp8x4_e4m3 q4(make_float4(v[4 * j] * oq, v[4 * j + 1] * oq, v[4 * j + 2] * oq,
+                                                           v[4 * j + 3] * oq));
+                            pk[j] = *reinterpret_cast<uint32_t *>(&q4);
+                        }
+                        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(out) + (size_t)rg * N + n0 + c * 32);
+                        dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    } else {
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                            pk[j] = *reinterpret_cast<uint32_t *>(&h2);
+                        }
+                        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + (size_t)rg * N + n0 + c * 32);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) dst[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
+                // publish: the stores must be visible to other CTAs' TMA loads
+                fence_proxy_async_global();
+                __threadfence();
+                epi_bar();
+                if (ep_tid == 0 && good) atomicAdd(P.counters + T.l * P.mblocks + T.m, 1);
+            } else {
+                // last hidden layer: partial dot products with the FP32 last layer
+                float acc[CMAX];
+#pragma unroll
+                for (int c = 0; c < CMAX; ++c) acc[c] = 0.f;
+                const float *wl = P.w_last + n0;
+                const int K = P.dims[T.l + 1];
+#pragma unroll 1
+                for (int c = 0; c < kChainBN / 32 && good; ++c) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + c * 32, r);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float v = fmaxf(fmaf(__uint_as_float(r[j]), sc, __ldg(bias + c * 32 + j)), 0.f);
+#pragma unroll
+                        for (int o = 0; o < CMAX; ++o)
+                            if (o < P.C) acc[o] = fmaf(v, __ldg(wl + (size_t)o * K + c * 32 + j), acc[o]);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
+                float *pp = P.partial + ((size_t)T.n * P.rows_pad + rg) * P.C;
+#pragma unroll
+                for (int o = 0; o < CMAX; ++o)
+                    if (o < P.C) pp[o] = acc[o];
+                __threadfence();
+                epi_bar();
+                if (ep_tid == 0) {
+                    const int old = good ? atomicAdd(P.counters + P.nh * P.mblocks + T.m, 1) : -1;
+                    *flag = old == P.nt[T.l] - 1;
+                }
+                epi_bar();
+                if (*flag) {
+                    __threadfence();
+                    float yv[CMAX];
+#pragma unroll
+                    for (int o = 0; o < CMAX; ++o) {
+                        if (o >= P.C) break;
+                        float s = __ldg(P.b_last + o);
+                        for (int nt = 0; nt < P.nt[T.l]; ++nt)
+                            s += __ldcg(P.partial + ((size_t)nt * P.rows_pad + rg) * P.C + o);
+                        yv[o] = s;
+                    }
+                    finish_row<DOMAIN, CMAX>(P, rg, yv, rg < P.n, lane, q, T.m);
+                }
+                epi_bar();
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+}  // namespace
+
+size_t chain_smem_bytes() { return 1024 + kChainStages * (kStageA + kStageB) + 256; }
+
+// Launch the chain for one batch.  P.counters must be zeroed (on stream st) beforehand.
+template <int D, bool F>
+static int launch_t(const ChainMaps &maps, const ChainParams &P, int grid, cudaStream_t st) {
+    const size_t smem = chain_smem_bytes();
+    void (*kern)(const ChainMaps, const ChainParams) =
+        P.C == 1 ? k_chain<D, F, 1> : k_chain<D, F, kMaxHeadC>;
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kChainThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, maps, P));
+    return CBDFS_OK;
+}
+
+int chain_launch(int domain, bool fp8, const ChainMaps &maps, const ChainParams &P, int grid, cudaStream_t st) {
+    if (P.C < 1 || P.C > kMaxHeadC) return fail(CBDFS_EINVAL, "fused head width %d", P.C);
+    if (fp8) {
+        if (domain == CBDFS_DOM_STP3) return launch_t<CBDFS_DOM_STP3, true>(maps, P, grid, st);
+        if (domain == CBDFS_DOM_STP4) return launch_t<CBDFS_DOM_STP4, true>(maps, P, grid, st);
+        return launch_t<CBDFS_DOM_RC3, true>(maps, P, grid, st);
+    }
+    if (domain == CBDFS_DOM_STP3) return launch_t<CBDFS_DOM_STP3, false>(maps, P, grid, st);
+    if (domain == CBDFS_DOM_STP4) return launch_t<CBDFS_DOM_STP4, false>(maps, P, grid, st);
+    return launch_t<CBDFS_DOM_RC3, false>(maps, P, grid, st);
+}
+
+}  // namespace cbdfs

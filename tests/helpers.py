@@ -9,11 +9,13 @@ RTOL = {"fp32": 1e-4, "bf16": 2e-2, "fp8": 6e-2}
 PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
 
 
-def oracle_net(orc, dom, Ws, bs, prec, states, head="regression", max_with_md=False):
+def oracle_net(orc, dom, Ws, bs, prec, states, head="regression", max_with_md=False,
+               act_scales=None):
     """Float64 outputs and integer h of the oracle, with the hidden layers' weights rounded
-    to `prec` (the last layer stays float32, as the library keeps it)."""
+    to `prec` (the last layer stays float32, as the library keeps it).  With act_scales the
+    E4M3 storage of the activations between tensor-core layers is emulated too."""
     Wq = orc.quantise_weights(Ws[:-1], prec) + [np.asarray(Ws[-1], np.float32)]
-    y = orc.mlp_forward(Wq, bs, orc.one_hot(dom, states))
+    y = orc.mlp_forward(Wq, bs, orc.one_hot(dom, states), act_scales=act_scales)
     goal = orc.is_goal_states(dom, states)
     md = orc.md_states(dom, states) if max_with_md else None
     # A rounding or argmax decision counts as a margin case when the boundary lies within
@@ -52,3 +54,16 @@ def stp_states(side, n, seed):
 
 def rc_states(n, seed):
     return W.random_rc_states(n, seed)
+
+
+def fp8_act_scales(orc, dom, Ws, bs, states, margin=1.0):
+    """Static per-layer activation scales for the FP8 form: the largest float64 activation of
+    each hidden layer over calibration states (on the E4M3-rounded weights), divided by 448."""
+    Wq = orc.quantise_weights(Ws[:-1], "fp8") + [np.asarray(Ws[-1], np.float32)]
+    _, hidden = orc.mlp_forward(Wq, bs, orc.one_hot(dom, states), return_hidden=True)
+    return np.array([max(float(a.max()), 1e-6) * margin / 448.0 for a in hidden], np.float32)
+
+
+def normwise(y_gpu, y64):
+    y64 = np.asarray(y64, np.float64)
+    return float(np.linalg.norm(np.asarray(y_gpu, np.float64) - y64) / np.linalg.norm(y64))

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from helpers import PREC, check_h, check_logits, oracle_net
+from helpers import PREC, check_h, check_logits, fp8_act_scales, normwise, oracle_net
 
 pytestmark = pytest.mark.gpu
 
@@ -204,4 +204,72 @@ def test_device_entry_matches_host_entry(P, ctx):
         assert np.array_equal(dh.cpu().numpy(), h)
         assert np.array_equal(dm.cpu().numpy().view(np.uint32), mask)
         assert int(dmin.cpu().numpy().view(np.uint32)[0]) == minf
+    assert P.cbdfs_device_status(ctx) == 0
+
+
+# FP8 (E4M3 weights with a per-tensor scale, E4M3 activations with static per-layer scales):
+# per-logit parity is checked against the oracle's emulation of that storage (float64
+# arithmetic on the E4M3 values); against plain float64 on the same weights the error is the
+# format's own and is bounded normwise.
+
+@pytest.mark.parametrize("n", [1, 129, 1000])
+def test_c1_fp8(P, ctx, orc, n):
+    Ws, bs = W.net_weights(**W.NET_C1)
+    sc = fp8_act_scales(orc, 1, Ws, bs, W.random_stp_states(4, 4096, 11))
+    hid = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, PREC["fp8"], P.HEAD_REGRESSION, 1, act_scales=sc)
+    s = W.random_stp_states(4, n, 70 + n)
+    g = _g(n, n + 4)
+    h, mask, minf, y = P.heur_submit_batch(ctx, hid, P.DOM_STP4, s, g, 60, want_y=True)
+    ye, he, margin = oracle_net(orc, 1, Ws, bs, "fp8", s, "regression", True, act_scales=sc)
+    check_logits(y, ye, "fp8")
+    check_h(h, he, margin)
+    y64, _, _ = oracle_net(orc, 1, Ws, bs, "fp8", s, "regression", True)
+    if n > 1:
+        assert normwise(y, y64) <= 6e-2
+    _check_bound(orc, h, g, 60, mask, minf)
+
+
+@pytest.mark.parametrize("n", [129, 1000])
+def test_c2_fp8(P, ctx, orc, n):
+    Ws, bs = W.net_weights(**W.NET_C2)
+    sc = fp8_act_scales(orc, 2, Ws, bs, W.random_rc_states(4096, 12))
+    hid = P.cbdfs_net_load(ctx, P.DOM_RC3, Ws, bs, PREC["fp8"], P.HEAD_CLASSIFIER, 0, act_scales=sc)
+    s = W.random_rc_states(n, 80 + n)
+    g = _g(n, n + 5, 20)
+    h, mask, minf, y = P.heur_submit_batch(ctx, hid, P.DOM_RC3, s.reshape(-1), g, 25, want_y=True,
+                                           n_out=21)
+    ye, he, margin = oracle_net(orc, 2, Ws, bs, "fp8", s, "classifier", False, act_scales=sc)
+    check_logits(y, ye, "fp8")
+    nm = check_h(h, he, margin)
+    y64, _, _ = oracle_net(orc, 2, Ws, bs, "fp8", s, "classifier", False)
+    err = normwise(y, y64)
+    assert err <= 6e-2
+    _check_bound(orc, h, g, 25, mask, minf)
+    print(f"fp8 margin mismatches: {nm} of {n}; normwise error vs float64 {err:.4f}")
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_fused_chain_matches_per_layer_kernels(P, ctx, orc, prec):
+    """The persistent chain (device-buffer entry) and the per-layer kernels (the static-scratch
+    entry) evaluate the same network: outputs agree to the precision, integers exactly."""
+    import torch
+    Ws, bs = W.net_weights(**W.NET_C1)
+    sc = fp8_act_scales(orc, 1, Ws, bs, W.random_stp_states(4, 4096, 11)) if prec == "fp8" else None
+    hid = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, PREC[prec], P.HEAD_REGRESSION, 1, act_scales=sc)
+    dev = torch.device("cuda:0")
+    n = 5000
+    s = W.random_stp_states(4, n, 4321)
+    g = _g(n, 17)
+    ds = torch.from_numpy(s.view(np.int64)).to(dev)
+    dg = torch.from_numpy(g).to(dev)
+    outs = []
+    for fn in (P.heur_eval_device, P.heur_eval_device_static):
+        dh = torch.empty(n, dtype=torch.uint8, device=dev)
+        dm = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
+        dmin = torch.empty(1, dtype=torch.int32, device=dev)
+        fn(ctx, hid, P.DOM_STP4, ds, dg, 55, n, dh, dm, dmin, stream=torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        outs.append((dh.cpu().numpy(), dm.cpu().numpy(), int(dmin.cpu()[0])))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1]) and outs[0][2] == outs[1][2]
     assert P.cbdfs_device_status(ctx) == 0

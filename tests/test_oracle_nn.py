@@ -163,3 +163,26 @@ def test_fp8_quantised_weights_within_grid(orc):
     # relative error of E4M3 rounding is at most 2^-4 for normal values
     big = np.abs(Ws[0]) > 2 ** -6 * s
     assert (np.abs(q - Ws[0])[big] <= 2 ** -4 * np.abs(Ws[0])[big] + 1e-12).all()
+
+
+def test_e4m3_activation_emulation(orc):
+    # Activations that are exactly representable in E4M3 at the given scale are unchanged
+    # by the emulation; others move by at most 2^-4 of their value (round to nearest).
+    W1 = np.zeros((4, 16))
+    W1[0, 0], W1[1, 1], W1[2, 2], W1[3, 3] = 2.0, 3.0, 0.5, 448.0
+    Ws = [W1, np.eye(4), np.ones((1, 4))]
+    bs = [np.zeros(4), np.zeros(4), np.zeros(1)]
+    X = np.eye(16)[:4]
+    plain = orc.mlp_forward(Ws, bs, X)
+    emu = orc.mlp_forward(Ws, bs, X, act_scales=[1.0, 1.0])
+    assert np.array_equal(plain, emu)
+    W1[0, 0] = 2.3  # 2.3 is between E4M3 neighbours 2.25 and 2.5
+    emu = orc.mlp_forward(Ws, bs, X, act_scales=[1.0, 1.0])
+    assert emu[0, 0] == 2.25
+    rng = np.random.default_rng(1)
+    Ws2, bs2 = W.net_weights([16, 32, 32, 1], "kaiming", 5)
+    X2 = rng.random((50, 16))
+    _, hp = orc.mlp_forward(Ws2, bs2, X2, return_hidden=True)
+    _, he = orc.mlp_forward(Ws2, bs2, X2, return_hidden=True, act_scales=[0.01, 0.01])
+    big = hp[0] > 2 ** -6 * 0.01
+    assert (np.abs(he[0] - hp[0])[big] <= 2 ** -4 * hp[0][big] + 1e-12).all()
