@@ -93,24 +93,24 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def kernel_traffic(stage_name):
-    """dram bytes per launch from the committed ncu summary, if the kernel source is the one
-    the counters were taken on; else None."""
-    path = os.path.join(ROOT, "profiles", "tc_layer_c1_bf16_b8192.md")
+def kernel_traffic(key):
+    """DRAM bytes per launch of the fused chain kernel from the committed ncu summary, if the
+    kernel source is the one the counters were taken on; else None."""
+    path = os.path.join(ROOT, "profiles", "chain_c1_bf16_b8192.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     h = hashlib.sha256()
-    for f in ("mlp_tc.cu", "common.cuh"):
+    for f in ("mlp_chain.cu", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2507_11916_b300", "csrc", f), "rb").read())
     want = {}
     for line in txt.splitlines():
-        if ":" in line and line.strip().startswith(("source_sha256", f"{stage_name}_dram_bytes")):
+        if ":" in line and line.strip().startswith(("source_sha256", f"{key}_dram_bytes")):
             k, v = line.split(":", 1)
             want[k.strip()] = v.strip()
     if want.get("source_sha256") != h.hexdigest()[:16]:
         return None
-    v = want.get(f"{stage_name}_dram_bytes")
+    v = want.get(f"{key}_dram_bytes")
     return float(v) if v else None
 
 
@@ -304,18 +304,30 @@ def run_ours(args):
         stage.append(P.cbdfs_eval_profile(ctx, hid, P.DOM_STP4, ds, dg, BOUND, B, dh, dm, dmin,
                                           stream=stream))
     stage_ms = np.mean(np.array(stage), axis=0)
-    names = ["layer1_onehot_256x1024", "layer2_1024x1024", "layer3_1024x512", "head_512x1"]
-    flops = [2 * B * 256 * 1024, 2 * B * 1024 * 1024, 2 * B * 1024 * 512, 2 * B * 512]
-    top = int(np.argmax(stage_ms[:3]))
+    dims = W.NET_C1["dims"]
+    layer_flops = [2 * B * dims[l] * dims[l + 1] for l in range(len(dims) - 1)]
+    if len(stage_ms) == 1:
+        # the fused chain: one launch runs every layer and the head
+        names = ["k_chain (256-1024-1024-512-1, one launch)"]
+        flops = [sum(layer_flops)]
+        traffic_key = "chain"
+    else:
+        names = ["layer1_onehot_256x1024", "layer2_1024x1024", "layer3_1024x512", "head_512x1"]
+        flops = layer_flops
+        traffic_key = None
+    top = int(np.argmax(stage_ms))
     pk = peaks()
     achieved = flops[top] / (stage_ms[top] / 1e3) / 1e12
-    roof = {"kernel": f"k_tc_layer ({names[top]})", "bound": "tensor", "achieved": achieved,
+    roof = {"kernel": names[top], "bound": "tensor", "achieved": achieved,
             "peak": pk["bf16"], "unit": "TFLOP/s", "frac": achieved / pk["bf16"],
             "peak_source": f"{pk['src']} bf16 dense (burst)",
-            "traffic": kernel_traffic(names[top]),
-            "algorithmic_flops_per_launch": flops[top], "launch_ms": float(stage_ms[top]),
+            "traffic": kernel_traffic(traffic_key) if traffic_key else None,
+            "algorithmic_flops_per_launch": flops[top],
+            "algorithmic_flops_onehot_as_gather": flops[top] - layer_flops[0] + 2 * B * 16 * dims[1],
+            "launch_ms": float(stage_ms[top]),
             "stages_ms": {n: float(t) for n, t in zip(names, stage_ms)},
             "step_share": float(stage_ms[top] / stage_ms.sum())}
+    launches_per_step = len(stage_ms)
 
     # end to end through the public host-buffer call (copies in and out every step)
     pin_s = torch.from_numpy(states.view(np.int64)).pin_memory()
@@ -338,7 +350,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": dict(CONFIG, parallelism=f"replicas x{world}"),
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "e2e": {"value": e2e, "unit": "states/s", "h2d_bytes_per_step": B * 8 + B,
                 "d2h_bytes_per_step": B + (B + 31) // 32 * 4 + 4},
         "roofline": roof, "clocks": clk,

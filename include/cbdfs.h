@@ -200,6 +200,18 @@ int cbdfs_eval_profile(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *
                        uint32_t *d_mask, uint32_t *d_minf, void *stream, float *stage_ms, int cap,
                        int *n_stages);
 
+/* Like cbdfs_eval_profile, for the fused network kernel: records its tile timeline.  d_trace
+ * (device, caller-owned) holds ctas_max x tiles_per_cta x 8 uint64 %globaltimer stamps (ns):
+ * for the i-th tile a CTA processes, [0] producer start, [1] its layer dependency satisfied,
+ * [2] its last load issued, [3] first MMA issue, [4] last MMA committed, [5] epilogue start,
+ * [6] epilogue end, [7] unused; 0 = not reached.  *ctas receives the grid size (at most the
+ * SM count).  Networks not run by the fused kernel record nothing (*ctas = 0).  Waits for
+ * completion.  Errors: those of heur_eval_device, EDEVICE. */
+int cbdfs_eval_trace(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_states,
+                     const uint8_t *d_g, uint32_t bound, uint32_t n, uint8_t *d_h,
+                     uint32_t *d_mask, uint32_t *d_minf, void *stream, uint64_t *d_trace,
+                     int tiles_per_cta, int *ctas);
+
 /* Reads and clears the device-side error flag (0 = none; otherwise a code naming the
  * wait that ran out).  Synchronises the context's device. */
 int cbdfs_device_status(cbdfs_ctx *ctx);

@@ -107,6 +107,9 @@ _lib.heur_submit_batch.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ct
 _lib.heur_eval_device.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint32,
                                   ctypes.c_uint32, _vp, _vp, _vp, _vp, _vp]
 _lib.cbdfs_device_status.argtypes = [_vp]
+_lib.cbdfs_eval_trace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint32,
+                                  ctypes.c_uint32, _vp, _vp, _vp, _vp, _vp, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_int)]
 _lib.heur_eval_device_static.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint32,
                                          ctypes.c_uint32, _vp, _vp, _vp, _vp]
 _lib.cbdfs_eval_profile.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint32,
@@ -127,7 +130,7 @@ _lib.cbdfs_cancel.restype = None
 EXPORTED = ["cbdfs_create", "cbdfs_destroy", "cbdfs_last_error", "cbdfs_mem_used", "cbdfs_net_load",
             "cbdfs_pdb_load", "pdb_build", "heur_submit_batch", "heur_eval_device",
             "heur_eval_device_static",
-            "cbdfs_device_status", "cbdfs_eval_profile", "cbdfs_apply_moves", "cbdfs_manhattan", "cbdfs_solve",
+            "cbdfs_device_status", "cbdfs_eval_profile", "cbdfs_eval_trace", "cbdfs_apply_moves", "cbdfs_manhattan", "cbdfs_solve",
             "cbdfs_search_defaults", "cbdfs_cancel"]
 
 
@@ -250,6 +253,18 @@ def cbdfs_eval_profile(ctx, heur_id, domain, d_states, d_g, bound, n, d_h, d_mas
     _check(_lib.cbdfs_eval_profile(ctx, heur_id, domain, _ptr(d_states), _ptr(d_g), bound, n,
                                    _ptr(d_h), _ptr(d_mask), _ptr(d_minf), s, ms, 16, ctypes.byref(k)))
     return list(ms[:k.value])
+
+
+def cbdfs_eval_trace(ctx, heur_id, domain, d_states, d_g, bound, n, d_h, d_mask, d_minf,
+                     d_trace, tiles_per_cta, stream=None) -> int:
+    """Runs the pipeline once recording the fused kernel's tile timeline into d_trace (a CUDA
+    uint64/int64 tensor of at least SMs x tiles_per_cta x 8); returns the CTA count."""
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    k = ctypes.c_int()
+    _check(_lib.cbdfs_eval_trace(ctx, heur_id, domain, _ptr(d_states), _ptr(d_g), bound, n,
+                                 _ptr(d_h), _ptr(d_mask), _ptr(d_minf), s, _ptr(d_trace),
+                                 tiles_per_cta, ctypes.byref(k)))
+    return k.value
 
 
 def cbdfs_device_status(ctx) -> int:

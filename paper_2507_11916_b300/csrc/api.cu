@@ -41,6 +41,7 @@ constexpr int kChainMaxC = 32;
 struct ChainMaps {
     CUtensorMap w[kMaxLayers];
     CUtensorMap a[kMaxLayers];
+    CUtensorMap o[kMaxLayers];
 };
 struct ChainParams {
     int nh;
@@ -51,6 +52,7 @@ struct ChainParams {
     int mblocks;
     uint32_t n;
     const uint64_t *states;
+    void *onehot;
     void *act[2];
     const float *bias[kMaxLayers];
     float acc_scale[kMaxLayers], out_qscale[kMaxLayers];
@@ -66,6 +68,8 @@ struct ChainParams {
     uint32_t *mask, *minf;
     float *y;
     int *err;
+    unsigned long long *trace;
+    int trace_tiles;
 };
 int chain_launch(int domain, bool fp8, const ChainMaps &maps, const ChainParams &P, int grid, cudaStream_t st);
 
@@ -146,7 +150,8 @@ static EncodeTiledFn encode_fn() {
 }
 
 int make_tmap_2d(CUtensorMap *map, void *base, CUtensorMapDataType dt, int elem_bytes,
-                 uint64_t inner, uint64_t outer, uint32_t box_inner, uint32_t box_outer) {
+                 uint64_t inner, uint64_t outer, uint32_t box_inner, uint32_t box_outer,
+                 CUtensorMapSwizzle swizzle) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return fail(CBDFS_EDEVICE, "cuTensorMapEncodeTiled unavailable");
     cuuint64_t dims[2] = {inner, outer};
@@ -154,8 +159,7 @@ int make_tmap_2d(CUtensorMap *map, void *base, CUtensorMapDataType dt, int elem_
     cuuint32_t box[2] = {box_inner, box_outer};
     cuuint32_t es[2] = {1, 1};
     CUresult r = fn(map, dt, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(CBDFS_EDEVICE, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return CBDFS_OK;
 }
@@ -236,10 +240,11 @@ int ensure_act(Ctx *c, size_t width) {
 
 // chain scratch of every slot: tile counters, and head partials of `floats` per row
 int ensure_chain(Ctx *c, size_t floats) {
-    const size_t cbytes = sizeof(int) * (kMaxLayers + 1) * (c->max_batch_pad / kBM);
+    const size_t cbytes = sizeof(int) * (kMaxLayers + 2) * (c->max_batch_pad / kBM);
     for (auto &s : c->slots)
         if (!s.counters) {
             int rc = dev_alloc(c, (void **)&s.counters, cbytes);
+            if (!rc) rc = dev_alloc(c, &s.onehot, (size_t)c->max_batch_pad * 1024);
             if (rc) return rc;
         }
     if (floats <= c->partial_floats) return CBDFS_OK;
@@ -262,6 +267,35 @@ const CUtensorMap *act_map(Slot &s, Ctx *c, int buf, int K, int elem_bytes) {
     if (it != s.tm_act.end()) return &it->second;
     CUtensorMap m;
     if (make_tmap_2d(&m, s.act[buf],
+                     elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                     elem_bytes, (uint64_t)K, c->max_batch_pad, 128 / elem_bytes, kBM))
+        return nullptr;
+    return &s.tm_act.emplace(key, m).first->second;
+}
+
+// TMA store maps over the activation buffers: 32-element x 32-row boxes, swizzled so that
+// one row per lane lands in shared memory without bank conflicts (64 B rows: 64-byte
+// swizzle; 32 B rows of E4M3: 32-byte swizzle)
+const CUtensorMap *act_store_map(Slot &s, Ctx *c, int buf, int K, int elem_bytes) {
+    const long long key = (1LL << 50) | ((long long)buf << 40) | ((long long)elem_bytes << 32) | K;
+    auto it = s.tm_act.find(key);
+    if (it != s.tm_act.end()) return &it->second;
+    CUtensorMap m;
+    if (make_tmap_2d(&m, s.act[buf],
+                     elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                     elem_bytes, (uint64_t)K, c->max_batch_pad, 32, 32,
+                     elem_bytes == 1 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B))
+        return nullptr;
+    return &s.tm_act.emplace(key, m).first->second;
+}
+
+// TMA load map over the one-hot rows (row stride = the padded one-hot width)
+const CUtensorMap *onehot_map(Slot &s, Ctx *c, int K, int elem_bytes) {
+    const long long key = (2LL << 50) | ((long long)elem_bytes << 32) | K;
+    auto it = s.tm_act.find(key);
+    if (it != s.tm_act.end()) return &it->second;
+    CUtensorMap m;
+    if (make_tmap_2d(&m, s.onehot,
                      elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                      elem_bytes, (uint64_t)K, c->max_batch_pad, 128 / elem_bytes, kBM))
         return nullptr;
@@ -306,7 +340,16 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
             if (!m) return CBDFS_EDEVICE;
             maps.a[l] = *m;
         } else {
-            maps.a[0] = net.tm_w[0];  // unused
+            const CUtensorMap *m = onehot_map(s, c, net.k1pad, eb);
+            if (!m) return CBDFS_EDEVICE;
+            maps.a[0] = *m;
+        }
+        if (l < nh - 1) {  // stored activations: 32 x 32 boxes, written by TMA stores
+            const CUtensorMap *m = act_store_map(s, c, l & 1, net.dims[l + 1], eb);
+            if (!m) return CBDFS_EDEVICE;
+            maps.o[l] = *m;
+        } else {
+            maps.o[l] = net.tm_w[0];  // unused
         }
         P.kdim[l] = l == 0 ? net.k1pad : net.dims[l];
         P.nt[l] = net.dims[l + 1] / kChainBN;
@@ -317,6 +360,7 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
         P.out_qscale[l] = fp8 ? 1.f / net.a_scale[l] : 1.f;
     }
     P.states = d_states;
+    P.onehot = s.onehot;
     P.act[0] = s.act[0];
     P.act[1] = s.act[1];
     P.counters = s.counters;
@@ -333,8 +377,14 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     P.minf = d_minf;
     P.y = d_y;
     P.err = c->d_err;
-    CUDA_TRY(cudaMemsetAsync(s.counters, 0, sizeof(int) * (nh + 1) * P.mblocks, st));
     const int grid = std::min(c->num_sms, max_tiles);
+    if (s.trace) {
+        P.trace = s.trace;
+        P.trace_tiles = s.trace_tiles;
+        *s.trace_grid = grid;
+        CUDA_TRY(cudaMemsetAsync(s.trace, 0, sizeof(unsigned long long) * grid * s.trace_tiles * 8, st));
+    }
+    CUDA_TRY(cudaMemsetAsync(s.counters, 0, sizeof(int) * (nh + 2) * P.mblocks, st));
     int rc = chain_launch(domain, fp8, maps, P, grid, st);
     return rc ? rc : mark(s, st);
 }
@@ -437,7 +487,8 @@ void cbdfs_destroy(cbdfs_ctx *ctx) {
         dev_free(c, s.d_h, c->max_batch_pad);
         dev_free(c, s.d_mask, c->max_batch_pad / 8);
         dev_free(c, s.d_minf, 4);
-        dev_free(c, s.counters, sizeof(int) * (kMaxLayers + 1) * (c->max_batch_pad / kBM));
+        dev_free(c, s.counters, sizeof(int) * (kMaxLayers + 2) * (c->max_batch_pad / kBM));
+        dev_free(c, s.onehot, (size_t)c->max_batch_pad * 1024);
         dev_free(c, s.partial, s.partial_bytes);
         if (s.stream) cudaStreamDestroy(s.stream);
         if (s.done) cudaEventDestroy(s.done);
@@ -779,6 +830,31 @@ int cbdfs_eval_profile(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *
         if (*n_stages < cap) stage_ms[(*n_stages)++] = ms;
     }
     for (auto e : evs) cudaEventDestroy(e);
+    return rc;
+}
+
+int cbdfs_eval_trace(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_states, const uint8_t *d_g,
+                     uint32_t bound, uint32_t n, uint8_t *d_h, uint32_t *d_mask, uint32_t *d_minf,
+                     void *stream, uint64_t *d_trace, int tiles_per_cta, int *ctas) {
+    if (!ctx || !d_trace || !ctas || tiles_per_cta < 1 || !d_minf || (n && (!d_states || !d_g || !d_h || !d_mask)))
+        return fail(CBDFS_EINVAL, "null argument");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    int rc = check_eval_args(c, heur_id, domain, n);
+    if (rc) return rc;
+    CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lk(c->device_call_mu);
+    Slot &s = c->slots[0];
+    CUDA_TRY(cudaStreamWaitEvent(st, s.done, 0));
+    *ctas = 0;
+    s.trace = reinterpret_cast<unsigned long long *>(d_trace);
+    s.trace_tiles = tiles_per_cta;
+    s.trace_grid = ctas;
+    rc = run_eval(c, s, heur_id, domain, d_states, d_g, bound, n, d_h, d_mask, d_minf, nullptr, st);
+    s.trace = nullptr;
+    s.trace_grid = nullptr;
+    if (!rc && cudaEventRecord(s.done, st) != cudaSuccess) rc = fail(CBDFS_EDEVICE, "event record");
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(CBDFS_EDEVICE, "trace sync");
     return rc;
 }
 

@@ -90,7 +90,12 @@ struct Slot {
     // fused-chain scratch (null: the per-layer kernels are used)
     int *counters = nullptr;           // tile counts per (layer, row block) + head counts
     float *partial = nullptr;          // head partials [n-tiles][rows][C]
+    void *onehot = nullptr;            // one-hot input rows [max_batch_pad][1 KB]
     size_t partial_bytes = 0;
+    // when set, the fused chain stamps its tile timeline here (see cbdfs_eval_trace)
+    unsigned long long *trace = nullptr;
+    int trace_tiles = 0;
+    int *trace_grid = nullptr;
 };
 
 struct Ctx {
@@ -119,7 +124,8 @@ void dev_free(Ctx *c, void *p, size_t bytes);
 
 // TMA map creation (driver entry point fetched once)
 int make_tmap_2d(CUtensorMap *map, void *base, CUtensorMapDataType dt, int elem_bytes,
-                 uint64_t inner, uint64_t outer, uint32_t box_inner, uint32_t box_outer);
+                 uint64_t inner, uint64_t outer, uint32_t box_inner, uint32_t box_outer,
+                 CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_128B);
 
 // the evaluation pipeline on a stream with a slot's scratch (device pointers)
 int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
@@ -206,6 +212,21 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
         : "memory");
 }
+// shared -> global tensor store (bulk group of the issuing thread)
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                     (uint64_t)map),
+                 "r"(src), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// wait until at most N of this thread's bulk groups still read shared memory
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+// wait until all of this thread's bulk groups are complete (writes performed)
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void tma_prefetch_map(const CUtensorMap *map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
 }

@@ -37,6 +37,7 @@ constexpr int kMaxHeadC = 32;
 struct ChainMaps {
     CUtensorMap w[kMaxLayers];  // weights of hidden layer l, [N][K] K-major
     CUtensorMap a[kMaxLayers];  // activations read by hidden layer l >= 1
+    CUtensorMap o[kMaxLayers];  // activations written by hidden layer l (32 x 32 store boxes)
 };
 
 struct ChainParams {
@@ -48,10 +49,13 @@ struct ChainParams {
     int mblocks;
     uint32_t n;
     const uint64_t *states;
+    void *onehot;                  // [rows_pad][kdim[0]] one-hot input, written by the pre-pass
     void *act[2];
     const float *bias[kMaxLayers];
     float acc_scale[kMaxLayers], out_qscale[kMaxLayers];
-    int *counters;                 // [nh][mblocks] tile counts, then [mblocks] head counts
+    int *counters;                 // [mblocks] one-hot rows ready (4 = all warps), then
+                                   // [nh][mblocks] stored warp-tiles (4 per tile), then
+                                   // [mblocks] head partial counts
     float *partial;                // [nt_last][rows_pad][C]
     int rows_pad;
     int C;                         // outputs of the last layer (fused head)
@@ -63,6 +67,8 @@ struct ChainParams {
     uint32_t *mask, *minf;
     float *y;
     int *err;
+    unsigned long long *trace;     // optional: [grid][trace_tiles][8] %globaltimer stamps
+    int trace_tiles;
 };
 
 namespace {
@@ -71,6 +77,9 @@ using namespace dev;
 
 constexpr int kStageA = kBM * 128;
 constexpr int kStageB = kChainBN * 128;
+constexpr int kStagingWarp = 2 * 32 * 64;   // two 32-row x 64-byte boxes per epilogue warp
+constexpr int kStaging = 4 * kStagingWarp;
+constexpr int kBiasSmem = 2 * kChainBN * 4;  // the tile's biases, double-buffered
 
 __device__ __forceinline__ uint32_t ld_acquire(const int *p) {
     uint32_t v;
@@ -100,6 +109,11 @@ __device__ __forceinline__ bool wait_count(const int *p, int want, int *err) {
     return false;
 }
 
+__device__ __forceinline__ void stamp(const ChainParams &P, uint32_t i, int k) {
+    if (P.trace && (int)i < P.trace_tiles)
+        P.trace[((size_t)blockIdx.x * P.trace_tiles + i) * 8 + k] = globaltimer();
+}
+
 struct Tile {
     int l, m, n;
 };
@@ -110,38 +124,75 @@ __device__ __forceinline__ Tile tile_of(const ChainParams &P, int t) {
     return Tile{l, local / P.nt[l], local % P.nt[l]};
 }
 
-// one-hot k-block of 128 rows into a stage (128B-swizzled K-major), by the 32 producer lanes
+// One row of the one-hot input, written by one warp as coalesced 16-byte chunks: lane i
+// writes chunks i, i+32, ...  Chunk k holds elements [k*E, k*E+E) (E = 8 BF16 or 16 E4M3).
 template <int DOMAIN, bool FP8>
-__device__ __forceinline__ void onehot_kblock(uint8_t *A, const ChainParams &P, int m, int kb,
-                                              const uint64_t (&st)[4][2], int lane) {
-    constexpr int KBLK = FP8 ? 128 : 64;
-    const int k0 = kb * KBLK;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int r = lane + 32 * q;
-        uint8_t *row = A + r * 128;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) reinterpret_cast<uint4 *>(row)[c] = make_uint4(0, 0, 0, 0);
-        if ((uint32_t)(m * kBM + r) >= P.n) continue;
-        auto put = [&](int j) {
-            const int w = j - k0;
-            if (w < 0 || w >= KBLK) return;
-            if (FP8) {
-                row[(((w >> 4) ^ (r & 7)) << 4) | (w & 15)] = 0x38;
-            } else {
-                *reinterpret_cast<uint16_t *>(row + ((((w >> 3) ^ (r & 7)) << 4) | ((w & 7) << 1))) = 0x3F80;
-            }
+__device__ __forceinline__ void onehot_row(const ChainParams &P, uint32_t row, int lane, uint64_t w0,
+                                           uint64_t w1) {
+    constexpr int E = FP8 ? 16 : 8;
+    const int nchunk = P.kdim[0] / E;
+    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(P.onehot) + (size_t)row * P.kdim[0] * (FP8 ? 1 : 2));
+    const bool live = row < P.n;
+    for (int k = lane; k < nchunk; k += 32) {
+        // four scalar words (a runtime-indexed array would live in local memory)
+        uint32_t v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+        auto set = [&](int e) {  // element e of the chunk is 1
+            const uint32_t bits = FP8 ? (0x38u << (8 * (e & 3))) : (0x3F80u << (16 * (e & 1)));
+            const int wi = FP8 ? (e >> 2) : (e >> 1);
+            v0 |= wi == 0 ? bits : 0u;
+            v1 |= wi == 1 ? bits : 0u;
+            v2 |= wi == 2 ? bits : 0u;
+            v3 |= wi == 3 ? bits : 0u;
         };
-        if (DOMAIN == CBDFS_DOM_RC3) {
+        if (live) {
+            if (DOMAIN == CBDFS_DOM_STP4 && !FP8) {
+                // chunk k: tile k/2, cells (k%2)*8 .. +7
+                const uint32_t t = k >> 1;
+                int cell = 0;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) put(c * 24 + (int)((st[q][0] >> (5 * c)) & 31u));
+                for (int p = 0; p < 16; ++p) cell = (((w0 >> (4 * p)) & 15u) == t) ? p : cell;
+                const int e = cell - (k & 1) * 8;
+                if (e >= 0 && e < 8) set(e);
+            } else if (DOMAIN == CBDFS_DOM_STP4 && FP8) {
+                // chunk k: tile k, cells 0..15
+                int cell = 0;
 #pragma unroll
-            for (int e = 0; e < 12; ++e) put(192 + e * 24 + (int)((st[q][1] >> (5 * e)) & 31u));
-        } else {
-            constexpr int N = DOMAIN == CBDFS_DOM_STP3 ? 9 : 16;
+                for (int p = 0; p < 16; ++p) cell = (((w0 >> (4 * p)) & 15u) == (uint32_t)k) ? p : cell;
+                set(cell);
+            } else if (DOMAIN == CBDFS_DOM_RC3 && !FP8) {
+                // chunks 0..23: corner k/3; chunks 24..59: edge (k-24)/3; each cubie spans 3 chunks
+                if (k < 60) {
+                    const int cub = k < 24 ? k / 3 : (k - 24) / 3;
+                    const int sub = k < 24 ? k % 3 : (k - 24) % 3;
+                    const int f = (int)(((k < 24 ? w0 : w1) >> (5 * cub)) & 31u);
+                    const int e = f - sub * 8;
+                    if (e >= 0 && e < 8) set(e);
+                }
+            } else {
+                // general form: test every one-hot index against the chunk
+                const int lo = k * E;
+                if (DOMAIN == CBDFS_DOM_RC3) {
 #pragma unroll
-            for (int p = 0; p < N; ++p) put((int)((st[q][0] >> (4 * p)) & 15u) * N + p);
+                    for (int c = 0; c < 8; ++c) {
+                        const int j = c * 24 + (int)((w0 >> (5 * c)) & 31u) - lo;
+                        if (j >= 0 && j < E) set(j);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 12; ++c) {
+                        const int j = 192 + c * 24 + (int)((w1 >> (5 * c)) & 31u) - lo;
+                        if (j >= 0 && j < E) set(j);
+                    }
+                } else {
+                    constexpr int N = DOMAIN == CBDFS_DOM_STP3 ? 9 : 16;
+#pragma unroll
+                    for (int p = 0; p < N; ++p) {
+                        const int j = (int)((w0 >> (4 * p)) & 15u) * N + p - lo;
+                        if (j >= 0 && j < E) set(j);
+                    }
+                }
+            }
         }
+        dst[k] = make_uint4(v0, v1, v2, v3);
     }
 }
 
@@ -197,7 +248,9 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *A = smem;
     uint8_t *B = smem + kChainStages * kStageA;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(B + kChainStages * kStageB);
+    uint8_t *stg = B + kChainStages * kStageB;  // epilogue staging: 4 warps x 2 x 2 KB
+    float *bsm = reinterpret_cast<float *>(stg + kStaging);  // [2][256] tile biases
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stg + kStaging + kBiasSmem);
     uint64_t *full = bars, *empty = bars + kChainStages;
     uint64_t *acc_full = bars + 2 * kChainStages, *acc_empty = acc_full + 2;
     uint64_t *drain = acc_empty + 2;
@@ -223,7 +276,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
     if (warp == 0 && lane == 0) {
         for (int l = 0; l < P.nh; ++l) {
             tma_prefetch_map(&maps.w[l]);
-            if (l) tma_prefetch_map(&maps.a[l]);
+            tma_prefetch_map(&maps.a[l]);
         }
     }
     if (warp == 1) {
@@ -238,34 +291,21 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
 
     if (warp == 0) {
         // ------------------------------------------------------------- producer
-        uint32_t it = 0;
+        uint32_t it = 0, pi = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++pi) {
             const Tile T = tile_of(P, t);
             const int KB = P.kdim[T.l] / KBLK;
-            uint64_t st[4][2];
-            if (T.l == 0) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint32_t r = T.m * kBM + lane + 32 * q;
-                    st[q][0] = st[q][1] = 0;
-                    if (r < P.n) {
-                        if (DOMAIN == CBDFS_DOM_RC3) {
-                            const ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2 *>(P.states) + r);
-                            st[q][0] = w.x;
-                            st[q][1] = w.y;
-                        } else {
-                            st[q][0] = __ldg(P.states + r);
-                        }
-                    }
-                }
-            } else {
-                if (lane == 0)
-                    ok = wait_count(P.counters + (T.l - 1) * P.mblocks + T.m, P.nt[T.l - 1], P.err);
-                ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
-                if (!ok) break;
-                fence_proxy_async_global();
-            }
+            if (lane == 0) stamp(P, pi, 0);
+            // layer 0 reads the one-hot rows (16 units of 8 rows), layer l the stored tiles of
+            // layer l-1 (4 warps per tile)
+            const int *cnt = T.l == 0 ? P.counters + T.m : P.counters + T.l * P.mblocks + T.m;
+            const int want = T.l == 0 ? kBM / 8 : 4 * P.nt[T.l - 1];
+            if (lane == 0) ok = wait_count(cnt, want, P.err);
+            ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+            if (!ok) break;
+            fence_proxy_async_global();
+            if (lane == 0) stamp(P, pi, 1);
             for (int kb = 0; kb < KB; ++kb, ++it) {
                 const int s = it % kChainStages;
                 const uint32_t u = it / kChainStages;
@@ -275,16 +315,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                     w = __shfl_sync(0xFFFFFFFFu, w, 0);
                     if (!w) { ok = false; break; }
                 }
-                if (T.l == 0) {
-                    onehot_kblock<DOMAIN, FP8>(A + s * kStageA, P, T.m, kb, st, lane);
-                    fence_proxy_async();
-                    __syncwarp();
-                    if (lane == 0) {
-                        mbar_arrive_expect_tx(smem_u32(&full[s]), kStageB);
-                        tma_load_2d(smem_u32(B + s * kStageB), &maps.w[0], smem_u32(&full[s]), kb * KBLK,
-                                    T.n * kChainBN);
-                    }
-                } else if (lane == 0) {
+                if (lane == 0) {
                     mbar_arrive_expect_tx(smem_u32(&full[s]), kStageA + kStageB);
                     tma_load_2d(smem_u32(A + s * kStageA), &maps.a[T.l], smem_u32(&full[s]), kb * KBLK,
                                 T.m * kBM);
@@ -293,6 +324,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                 }
                 __syncwarp();
             }
+            if (lane == 0) stamp(P, pi, 2);
         }
         // every TMA load this CTA issued has landed before the CTA can exit (bounded)
         if (lane == 0) {
@@ -313,6 +345,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                 const uint32_t b = i & 1, u = i >> 1;
                 if (i >= 2 && !mbar_wait(smem_u32(&acc_empty[b]), (u - 1) & 1, P.err, DEVERR_ACCUM)) break;
                 tc_fence_after();
+                stamp(P, i, 3);
                 const uint32_t d = tmem + b * kChainBN;
                 for (int kb = 0; kb < KB; ++kb, ++it) {
                     const int s = it % kChainStages;
@@ -331,6 +364,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                     umma_commit(smem_u32(&empty[s]));
                 }
                 if (ok) umma_commit(smem_u32(&acc_full[b]));
+                stamp(P, i, 4);
             }
             // all MMAs this thread issued have completed before TMEM is released (bounded)
             umma_commit(smem_u32(drain));
@@ -341,87 +375,166 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
         const int q = warp & 3;
         const int row = q * 32 + lane;
         const int ep_tid = threadIdx.x - 64;
+        // one-hot pre-pass, spread over every epilogue warp of the grid in units of 8 rows:
+        // unit v = rows [8v, 8v+8) goes to warp v mod (4 * grid); each row block counts its
+        // 16 units
+        {
+            const int units = P.mblocks * (kBM / 8);
+            const int gw = blockIdx.x * 4 + q, nw = gridDim.x * 4;
+            for (int v = gw; v < units; v += nw) {
+                const uint32_t my = v * 8 + (lane & 7);
+                uint64_t s0 = 0, s1 = 0;
+                if (lane < 8 && my < P.n) {
+                    if (DOMAIN == CBDFS_DOM_RC3) {
+                        const ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2 *>(P.states) + my);
+                        s0 = w.x;
+                        s1 = w.y;
+                    } else {
+                        s0 = __ldg(P.states + my);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+                    onehot_row<DOMAIN, FP8>(P, v * 8 + r, lane, __shfl_sync(0xFFFFFFFFu, s0, r),
+                                            DOMAIN == CBDFS_DOM_RC3 ? __shfl_sync(0xFFFFFFFFu, s1, r) : 0ull);
+                fence_proxy_async_global();
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) atomicAdd(P.counters + v / (kBM / 8), 1);
+            }
+        }
         uint32_t i = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
             const Tile T = tile_of(P, t);
             const uint32_t b = i & 1, u = i >> 1;
+            // the tile's biases into shared memory while the MMAs run (buffer i & 1 was last
+            // read two tiles ago, before everyone passed the previous tile's barrier)
+            float *bt = bsm + (i & 1) * kChainBN;
+            bt[2 * ep_tid] = __ldg(P.bias[T.l] + T.n * kChainBN + 2 * ep_tid);
+            bt[2 * ep_tid + 1] = __ldg(P.bias[T.l] + T.n * kChainBN + 2 * ep_tid + 1);
+            epi_bar();
             // after a failed wait the warps skip the work but keep every barrier, so that
             // the four epilogue warps stay in step
             const bool good = mbar_wait(smem_u32(&acc_full[b]), u & 1, P.err, DEVERR_ACCUM);
             tc_fence_after();
+            if (ep_tid == 0) stamp(P, i, 5);
             const uint32_t taddr = tmem + b * kChainBN + ((uint32_t)(q * 32) << 16);
             const uint32_t rg = T.m * kBM + row;
-            const int N = P.dims[T.l + 1];
             const int n0 = T.n * kChainBN;
-            const float *bias = P.bias[T.l] + n0;
+            const float *bias = bt;  // shared memory
             const float sc = P.acc_scale[T.l];
             if (T.l < last_l) {
-                void *out = P.act[T.l & 1];
                 const bool out8 = FP8;  // every stored activation is read by the next layer's TMA
                 const float oq = P.out_qscale[T.l];
+                uint8_t *wstg = stg + q * kStagingWarp;
 #pragma unroll 1
-                for (int c = 0; c < kChainBN / 32 && good; ++c) {
-                    uint32_t r[32];
-                    tmem_ld32(taddr + c * 32, r);
+                for (int c2 = 0; c2 < kChainBN / 32 && good; c2 += 2) {
+                    uint32_t ra[2][32];
+                    tmem_ld32(taddr + c2 * 32, ra[0]);
+                    tmem_ld32(taddr + (c2 + 1) * 32, ra[1]);
                     tmem_ld_wait();
-                    float v[32];
 #pragma unroll
-                    for (int j = 0; j < 32; j += 4) {
-                        const float4 bb = __ldg(reinterpret_cast<const float4 *>(bias + c * 32 + j));
-                        v[j + 0] = fmaxf(fmaf(__uint_as_float(r[j + 0]), sc, bb.x), 0.f);
-                        v[j + 1] = fmaxf(fmaf(__uint_as_float(r[j + 1]), sc, bb.y), 0.f);
-                        v[j + 2] = fmaxf(fmaf(__uint_as_float(r[j + 2]), sc, bb.z), 0.f);
-                        v[j + 3] = fmaxf(fmaf(__uint_as_float(r[j + 3]), sc, bb.w), 0.f);
+                    for (int hb = 0; hb < 2; ++hb) {
+                        const int c = c2 + hb;
+                        float v[32];
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4) {
+                            const float4 bb = *reinterpret_cast<const float4 *>(bias + c * 32 + j);
+                            v[j + 0] = fmaxf(fmaf(__uint_as_float(ra[hb][j + 0]), sc, bb.x), 0.f);
+                            v[j + 1] = fmaxf(fmaf(__uint_as_float(ra[hb][j + 1]), sc, bb.y), 0.f);
+                            v[j + 2] = fmaxf(fmaf(__uint_as_float(ra[hb][j + 2]), sc, bb.z), 0.f);
+                            v[j + 3] = fmaxf(fmaf(__uint_as_float(ra[hb][j + 3]), sc, bb.w), 0.f);
+                        }
+                        uint8_t *sb = wstg + hb * (32 * 64);
+                        // both boxes of the previous pair must have been read out
+                        if (hb == 0 && c >= 2) {
+                            if (lane == 0) bulk_wait_read<0>();
+                            __syncwarp();
+                        }
+                        if (out8) {
+                            uint32_t pk[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                __nv_fp8x4_e4m3 q4(make_float4(v[4 * j] * oq, v[4 * j + 1] * oq, v[4 * j + 2] * oq,
+                                                               v[4 * j + 3] * oq));
+                                pk[j] = *reinterpret_cast<uint32_t *>(&q4);
+                            }
+                            // 32-byte row, 32-byte swizzle: chunk k of row r at k ^ ((r >> 2) & 1)
+                            uint8_t *rowp = sb + lane * 32;
+                            const int sw = (lane >> 2) & 1;
+                            *reinterpret_cast<uint4 *>(rowp + ((0 ^ sw) << 4)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                            *reinterpret_cast<uint4 *>(rowp + ((1 ^ sw) << 4)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                        } else {
+                            uint32_t pk[16];
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                                pk[j] = *reinterpret_cast<uint32_t *>(&h2);
+                            }
+                            // 64-byte row, 64-byte swizzle: chunk k of row r at k ^ ((r >> 1) & 3)
+                            uint8_t *rowp = sb + lane * 64;
+                            const int sw = (lane >> 1) & 3;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                *reinterpret_cast<uint4 *>(rowp + ((k ^ sw) << 4)) =
+                                    make_uint4(pk[4 * k], pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
+                        }
                     }
-                    if (out8) {
-                        uint32_t pk[8];
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            __nv_fp8x4_e4m3 q4(make_float4(v[4 * j] * oq, v[4 * j + 1] * oq, v[4 * j + 2] * oq,
-                                                           v[4 * j + 3] * oq));
-                            pk[j] = *reinterpret_cast<uint32_t *>(&q4);
-                        }
-                        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(out) + (size_t)rg * N + n0 + c * 32);
-                        dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                        dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-                    } else {
-                        uint32_t pk[16];
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                            pk[j] = *reinterpret_cast<uint32_t *>(&h2);
-                        }
-                        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + (size_t)rg * N + n0 + c * 32);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) dst[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                    fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_2d(&maps.o[T.l], smem_u32(wstg), n0 + c2 * 32, T.m * kBM + q * 32);
+                        tma_store_2d(&maps.o[T.l], smem_u32(wstg + 32 * 64), n0 + (c2 + 1) * 32,
+                                     T.m * kBM + q * 32);
+                        bulk_commit();
                     }
                 }
+                if (ep_tid == 0) stamp(P, i, 7);
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
-                // publish: the stores must be visible to other CTAs' TMA loads
-                fence_proxy_async_global();
-                __threadfence();
-                epi_bar();
-                if (ep_tid == 0 && good) atomicAdd(P.counters + T.l * P.mblocks + T.m, 1);
+                if (lane == 0) {
+                    mbar_arrive(smem_u32(&acc_empty[b]));
+                    // publish this warp's 32 rows: stores complete, then the count (4 per tile)
+                    bulk_wait_all();
+                    fence_proxy_async_global();
+                    __threadfence();
+                    if (good) atomicAdd(P.counters + (1 + T.l) * P.mblocks + T.m, 1);
+                }
+                __syncwarp();
             } else {
                 // last hidden layer: partial dot products with the FP32 last layer
                 float acc[CMAX];
 #pragma unroll
                 for (int c = 0; c < CMAX; ++c) acc[c] = 0.f;
-                const float *wl = P.w_last + n0;
                 const int K = P.dims[T.l + 1];
+                float *wsm = reinterpret_cast<float *>(stg);  // [C][128] slice of the last layer
 #pragma unroll 1
-                for (int c = 0; c < kChainBN / 32 && good; ++c) {
-                    uint32_t r[32];
-                    tmem_ld32(taddr + c * 32, r);
-                    tmem_ld_wait();
+                for (int half = 0; half < 2; ++half) {
+                    epi_bar();  // the previous slice has been read
+#pragma unroll 8
+                    for (int idx = ep_tid; idx < P.C * 128; idx += 128)
+                        wsm[idx] = __ldg(P.w_last + (size_t)(idx >> 7) * K + n0 + half * 128 + (idx & 127));
+                    epi_bar();
+#pragma unroll 1
+                    for (int c = half * 4; c < half * 4 + 4 && good; ++c) {
+                        uint32_t r[32];
+                        tmem_ld32(taddr + c * 32, r);
+                        tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float v = fmaxf(fmaf(__uint_as_float(r[j]), sc, __ldg(bias + c * 32 + j)), 0.f);
+                        for (int j = 0; j < 32; j += 4) {
+                            float v[4];
 #pragma unroll
-                        for (int o = 0; o < CMAX; ++o)
-                            if (o < P.C) acc[o] = fmaf(v, __ldg(wl + (size_t)o * K + c * 32 + j), acc[o]);
+                            for (int jj = 0; jj < 4; ++jj)
+                                v[jj] = fmaxf(fmaf(__uint_as_float(r[j + jj]), sc, bias[c * 32 + j + jj]), 0.f);
+                            const float *wj = wsm + (c - half * 4) * 32 + j;
+#pragma unroll
+                            for (int o = 0; o < CMAX; ++o) {
+                                if (o < P.C) {  // predicated: the loop stays unrolled, acc in registers
+                                    const float4 w4 = *reinterpret_cast<const float4 *>(wj + o * 128);
+                                    acc[o] = fmaf(v[0], w4.x, fmaf(v[1], w4.y, fmaf(v[2], w4.z, fmaf(v[3], w4.w, acc[o]))));
+                                }
+                            }
+                        }
                     }
                 }
                 tc_fence_before();
@@ -434,25 +547,28 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                 __threadfence();
                 epi_bar();
                 if (ep_tid == 0) {
-                    const int old = good ? atomicAdd(P.counters + P.nh * P.mblocks + T.m, 1) : -1;
+                    const int old = good ? atomicAdd(P.counters + (1 + P.nh) * P.mblocks + T.m, 1) : -1;
                     *flag = old == P.nt[T.l] - 1;
                 }
                 epi_bar();
                 if (*flag) {
                     __threadfence();
+                    // y = b + partial[0] + partial[1] + ... in tile order (deterministic); all of a
+                    // tile's C loads are issued together
                     float yv[CMAX];
 #pragma unroll
-                    for (int o = 0; o < CMAX; ++o) {
-                        if (o >= P.C) break;
-                        float s = __ldg(P.b_last + o);
-                        for (int nt = 0; nt < P.nt[T.l]; ++nt)
-                            s += __ldcg(P.partial + ((size_t)nt * P.rows_pad + rg) * P.C + o);
-                        yv[o] = s;
+                    for (int o = 0; o < CMAX; ++o) yv[o] = o < P.C ? __ldg(P.b_last + o) : 0.f;
+                    for (int nt = 0; nt < P.nt[T.l]; ++nt) {
+                        const float *pp = P.partial + ((size_t)nt * P.rows_pad + rg) * P.C;
+#pragma unroll
+                        for (int o = 0; o < CMAX; ++o)
+                            if (o < P.C) yv[o] += __ldcg(pp + o);
                     }
                     finish_row<DOMAIN, CMAX>(P, rg, yv, rg < P.n, lane, q, T.m);
                 }
                 epi_bar();
             }
+            if (ep_tid == 0) stamp(P, i, 6);
         }
     }
     tc_fence_before();
@@ -465,14 +581,14 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
 
 }  // namespace
 
-size_t chain_smem_bytes() { return 1024 + kChainStages * (kStageA + kStageB) + 256; }
+size_t chain_smem_bytes() { return 1024 + kChainStages * (kStageA + kStageB) + kStaging + kBiasSmem + 256; }
 
 // Launch the chain for one batch.  P.counters must be zeroed (on stream st) beforehand.
 template <int D, bool F>
 static int launch_t(const ChainMaps &maps, const ChainParams &P, int grid, cudaStream_t st) {
     const size_t smem = chain_smem_bytes();
     void (*kern)(const ChainMaps, const ChainParams) =
-        P.C == 1 ? k_chain<D, F, 1> : k_chain<D, F, kMaxHeadC>;
+        P.C == 1 ? k_chain<D, F, 1> : P.C <= 24 ? k_chain<D, F, 24> : k_chain<D, F, kMaxHeadC>;
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
