@@ -217,6 +217,58 @@ int cbdfs_eval_trace(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_
 int cbdfs_device_status(cbdfs_ctx *ctx);
 
 /* ---------------------------------------------------------------------------------------
+ * Learning the network heuristic (paper: Experimental Setup -- the heuristics are trained
+ * from PDB values).  BF16 networks only.  One step on a batch: BF16 tensor-core forward
+ * (activations kept), FP32 last layer and loss, backward with BF16 tensor-core GEMMs and
+ * FP32 accumulation (dW = dZ^T A, dA = dZ W, ReLU masks), FP32 Adam on FP32 master weights
+ * (bias-corrected), then the BF16 weights the heuristic evaluates are rewritten in place.
+ * The masters start from the FP32 weights given to cbdfs_net_load.
+ * ------------------------------------------------------------------------------------- */
+typedef enum { CBDFS_LOSS_CE = 0, CBDFS_LOSS_MSE = 1 } cbdfs_loss;
+
+typedef struct {
+    float lr, beta1, beta2, eps;    /* Adam (1e-3, 0.9, 0.999, 1e-8) */
+    uint32_t batch;                 /* states per step (<= max_batch) */
+    int epochs;                     /* passes over the set */
+    uint64_t seed;                  /* epoch e visits the states in the Fisher-Yates order drawn
+                                       from splitmix64(seed + (e+1)*0x9E3779B97F4A7C15) */
+    int loss;                       /* cbdfs_loss: cross-entropy over classes = labels, or
+                                       0.5*(y - label)^2 on one output */
+    int64_t max_steps;              /* stop after this many steps (0: no limit) */
+} cbdfs_train_cfg;
+
+typedef struct {
+    int64_t steps, samples;
+    double seconds;
+    float first_loss, last_loss;    /* mean batch loss of the first and last step */
+} cbdfs_train_report;
+
+/* Train network heur_id on n (state, label) pairs (host buffers, copied).  Labels are class
+ * indices (< outputs) for cross-entropy, target values for MSE.
+ * Errors: EINVAL (not a BF16 network, label range, sizes), ENOMEM, EDEVICE, ETIMEDOUT. */
+int net_train(cbdfs_ctx *ctx, int heur_id, const uint64_t *states, const uint8_t *labels,
+              uint64_t n, const cbdfs_train_cfg *cfg, cbdfs_train_report *rep);
+
+/* Loss and gradients of the mean loss over one batch of n states at the current weights,
+ * without updating (host buffers; gw_out[l] is dims[l+1] x dims[l], gb_out[l] dims[l+1];
+ * NULL entries are skipped).  n <= max_batch. */
+int cbdfs_train_grad(cbdfs_ctx *ctx, int heur_id, const uint64_t *states, const uint8_t *labels,
+                     uint32_t n, int loss, float *loss_out, float *const *gw_out,
+                     float *const *gb_out);
+
+/* The network's FP32 weights (the training masters once trained), host buffers as in
+ * cbdfs_net_desc. */
+int cbdfs_net_read(cbdfs_ctx *ctx, int heur_id, float *const *w_out, float *const *b_out);
+
+/* n sliding-tile states from random walks of the blank from the goal, walk i = first..:
+ * its splitmix64 stream starts at mix((tag << 32) | (i mod 2^32)); the walk's length is
+ * 1 + (draw mod max_len); each move is drawn (draw mod #choices) among the legal blank
+ * moves (up, left, right, down order) except the reverse of the previous one.  Host output.
+ * Errors: EINVAL, ENOMEM, EDEVICE. */
+int cbdfs_gen_walk_states(cbdfs_ctx *ctx, int domain, uint32_t tag, uint64_t first, uint64_t n,
+                          int max_len, uint64_t *states_out);
+
+/* ---------------------------------------------------------------------------------------
  * Domain helpers (product-side domain code; the search uses the same routines).
  * ------------------------------------------------------------------------------------- */
 

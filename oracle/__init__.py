@@ -566,10 +566,17 @@ def bound_test(g, h, bound):
 # training (float64)
 # ---------------------------------------------------------------------------------------
 
-def train_forward_backward(Ws, bs, X, labels, loss="ce"):
+def train_forward_backward(Ws, bs, X, labels, loss="ce", bf16_storage=False):
     """Loss and gradients of the mean loss over the batch.
     loss='ce': softmax cross-entropy against integer labels;
-    loss='mse': 0.5*(y - label)^2 on a single output."""
+    loss='mse': 0.5*(y - label)^2 on a single output.
+
+    bf16_storage: emulate a step that stores the hidden activations and the hidden layers'
+    dZ in bfloat16 (each rounded from its float32 value); the last layer, the loss and its
+    dZ stay unrounded.  The ReLU masks then come from the stored activations."""
+    def rnd(x):
+        return bf16_round(np.asarray(x, np.float32)).astype(np.float64) if bf16_storage else x
+
     Ws = [np.asarray(W, np.float64) for W in Ws]
     bs = [np.asarray(b, np.float64) for b in bs]
     acts = [np.asarray(X, np.float64)]
@@ -577,7 +584,7 @@ def train_forward_backward(Ws, bs, X, labels, loss="ce"):
     for l, (W, b) in enumerate(zip(Ws, bs)):
         z = acts[-1] @ W.T + b
         zs.append(z)
-        acts.append(np.maximum(z, 0.0) if l < len(Ws) - 1 else z)
+        acts.append(rnd(np.maximum(z, 0.0)) if l < len(Ws) - 1 else z)
     out = acts[-1]
     B = out.shape[0]
     labels = np.asarray(labels)
@@ -602,7 +609,7 @@ def train_forward_backward(Ws, bs, X, labels, loss="ce"):
         gb[l] = dz.sum(axis=0)
         if l > 0:
             da = dz @ Ws[l]
-            dz = da * (zs[l - 1] > 0)
+            dz = rnd(da * (acts[l] > 0))
     return L, gW, gb
 
 

@@ -35,6 +35,7 @@ CBDFS_EDEVICE, CBDFS_ECANCELED, CBDFS_ENOTFOUND = -4, -5, -6
 DOM_STP3, DOM_STP4, DOM_RC3 = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 HEAD_REGRESSION, HEAD_CLASSIFIER = 0, 1
+LOSS_CE, LOSS_MSE = 0, 1
 ALGO_IDA, ALGO_BTS = 0, 1
 HEUR_ZERO, HEUR_MD, HEUR_NONE = -1, -2, -100
 MAX_ITERS = 256
@@ -77,6 +78,17 @@ class SearchCfg(ctypes.Structure):
                 ("node_limit", ctypes.c_uint64), ("time_limit_s", ctypes.c_double)]
 
 
+class TrainCfg(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("batch", ctypes.c_uint32), ("epochs", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("loss", ctypes.c_int), ("max_steps", ctypes.c_int64)]
+
+
+class TrainReport(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("samples", ctypes.c_int64), ("seconds", ctypes.c_double),
+                ("first_loss", ctypes.c_float), ("last_loss", ctypes.c_float)]
+
+
 class Result(ctypes.Structure):
     _fields_ = [("cost", ctypes.c_int), ("path_len", ctypes.c_int), ("path", ctypes.c_int * 256),
                 ("n_iters", ctypes.c_int),
@@ -116,6 +128,14 @@ _lib.cbdfs_eval_profile.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, c
                                     ctypes.c_uint32, _vp, _vp, _vp, _vp,
                                     ctypes.POINTER(ctypes.c_float), ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_int)]
+_FPP = ctypes.POINTER(ctypes.POINTER(ctypes.c_float))
+_lib.net_train.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_uint64, ctypes.POINTER(TrainCfg),
+                           ctypes.POINTER(TrainReport)]
+_lib.cbdfs_train_grad.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_uint32, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_float), _FPP, _FPP]
+_lib.cbdfs_net_read.argtypes = [_vp, ctypes.c_int, _FPP, _FPP]
+_lib.cbdfs_gen_walk_states.argtypes = [_vp, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64,
+                                       ctypes.c_uint64, ctypes.c_int, _vp]
 _lib.cbdfs_apply_moves.argtypes = [ctypes.c_int, _u64p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                    _u64p]
 _lib.cbdfs_manhattan.argtypes = [ctypes.c_int, ctypes.c_uint64]
@@ -130,7 +150,8 @@ _lib.cbdfs_cancel.restype = None
 EXPORTED = ["cbdfs_create", "cbdfs_destroy", "cbdfs_last_error", "cbdfs_mem_used", "cbdfs_net_load",
             "cbdfs_pdb_load", "pdb_build", "heur_submit_batch", "heur_eval_device",
             "heur_eval_device_static",
-            "cbdfs_device_status", "cbdfs_eval_profile", "cbdfs_eval_trace", "cbdfs_apply_moves", "cbdfs_manhattan", "cbdfs_solve",
+            "cbdfs_device_status", "cbdfs_eval_profile", "cbdfs_eval_trace", "net_train",
+            "cbdfs_train_grad", "cbdfs_net_read", "cbdfs_gen_walk_states", "cbdfs_apply_moves", "cbdfs_manhattan", "cbdfs_solve",
             "cbdfs_search_defaults", "cbdfs_cancel"]
 
 
@@ -272,6 +293,51 @@ def cbdfs_device_status(ctx) -> int:
     if r < 0:
         _check(r)
     return r
+
+
+def _float_ptrs(arrays):
+    FP = ctypes.POINTER(ctypes.c_float)
+    return (FP * len(arrays))(*(a.ctypes.data_as(FP) for a in arrays))
+
+
+def _net_shapes(ctx_dims):
+    return [(ctx_dims[l + 1], ctx_dims[l]) for l in range(len(ctx_dims) - 1)]
+
+
+def net_train(ctx, heur_id, states, labels, batch=8192, epochs=1, lr=1e-3, beta1=0.9, beta2=0.999,
+              eps=1e-8, seed=0, loss=LOSS_CE, max_steps=0) -> dict:
+    states = np.ascontiguousarray(states, dtype=np.uint64)
+    labels = np.ascontiguousarray(labels, dtype=np.uint8)
+    cfg = TrainCfg(lr, beta1, beta2, eps, batch, epochs, seed, loss, max_steps)
+    rep = TrainReport()
+    _check(_lib.net_train(ctx, heur_id, _ptr(states), _ptr(labels), len(labels), ctypes.byref(cfg),
+                          ctypes.byref(rep)))
+    return {name: getattr(rep, name) for name, _ in TrainReport._fields_}
+
+
+def cbdfs_train_grad(ctx, heur_id, states, labels, dims, loss=LOSS_CE):
+    """(loss, [dW_l], [db_l]) of the mean loss over the batch at the current weights."""
+    states = np.ascontiguousarray(states, dtype=np.uint64)
+    labels = np.ascontiguousarray(labels, dtype=np.uint8)
+    gw = [np.zeros((o, i), np.float32) for o, i in _net_shapes(dims)]
+    gb = [np.zeros(o, np.float32) for o, _ in _net_shapes(dims)]
+    out = ctypes.c_float()
+    _check(_lib.cbdfs_train_grad(ctx, heur_id, _ptr(states), _ptr(labels), len(labels), loss,
+                                 ctypes.byref(out), _float_ptrs(gw), _float_ptrs(gb)))
+    return out.value, gw, gb
+
+
+def cbdfs_net_read(ctx, heur_id, dims):
+    Ws = [np.zeros((o, i), np.float32) for o, i in _net_shapes(dims)]
+    bs = [np.zeros(o, np.float32) for o, _ in _net_shapes(dims)]
+    _check(_lib.cbdfs_net_read(ctx, heur_id, _float_ptrs(Ws), _float_ptrs(bs)))
+    return Ws, bs
+
+
+def cbdfs_gen_walk_states(ctx, domain, tag, first, n, max_len) -> np.ndarray:
+    out = np.empty(n, dtype=np.uint64)
+    _check(_lib.cbdfs_gen_walk_states(ctx, domain, tag, first, n, max_len, _ptr(out)))
+    return out
 
 
 def cbdfs_apply_moves(domain, start, moves):

@@ -494,6 +494,8 @@ void cbdfs_destroy(cbdfs_ctx *ctx) {
         if (s.done) cudaEventDestroy(s.done);
     }
     for (auto &n : c->nets) {
+        train_free(c, n->train);
+        n->train = nullptr;
         for (int l = 0; l < kMaxLayers; ++l) {
             if (n->w_lp[l]) cudaFree(n->w_lp[l]);
             if (n->w32[l]) cudaFree(n->w32[l]);
@@ -582,6 +584,10 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
             return fail(CBDFS_EDEVICE, "weight upload");
         return CBDFS_OK;
     };
+    for (int l = 0; l < L; ++l) {
+        N.host_w[l].assign(d->weights[l], d->weights[l] + (size_t)d->dims[l + 1] * d->dims[l]);
+        N.host_b[l].assign(d->biases[l], d->biases[l] + d->dims[l + 1]);
+    }
     // FP32 copies: biases always; weights of the last layer always; all layers for FP32
     for (int l = 0; l < L; ++l) {
         const int O = d->dims[l + 1], I = d->dims[l];

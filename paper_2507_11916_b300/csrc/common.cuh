@@ -50,6 +50,9 @@ enum DevErr : int {
 constexpr int kMaxLayers = 8;
 constexpr int kBM = 128;  // rows (states) per tensor-core tile
 
+struct TrainState;  // train.cu
+void train_free(struct Ctx *c, TrainState *T);
+
 struct NetGPU {
     int domain = 0, L = 0, prec = 0, head = 0, max_with_md = 0;
     int dims[kMaxLayers + 1] = {};
@@ -64,6 +67,9 @@ struct NetGPU {
     float *w32[kMaxLayers] = {};
     float *b32[kMaxLayers] = {};
     size_t bytes = 0;
+    // FP32 weights as loaded (host), the training masters' starting point
+    std::vector<float> host_w[kMaxLayers], host_b[kMaxLayers];
+    TrainState *train = nullptr;
 };
 
 struct PdbGPU {

@@ -1,0 +1,797 @@
+// train.cu -- learning the network heuristic on the GPU (the paper trains its heuristics
+// from PDB values: Experimental Setup; Background, Heuristics) with BF16 tensor-core GEMMs,
+// FP32 accumulation, an FP32 last layer and loss, and FP32 Adam on master weights.
+//
+// One step on a batch of B states (B padded to 128):
+//   forward   layer 0..L-2: tcgen05 layers (one-hot A built from the packed states), ReLU,
+//             activations A_l kept in BF16; last layer FP32: logits = A_{L-2} W_L^T + b_L
+//   loss      cross-entropy over the classes (labels = class index) or MSE (one output);
+//             dZ_L = dLoss/dlogits (mean over the batch)
+//   backward  last layer FP32: dW_L = dZ_L^T A_{L-2}, db_L = colsum(dZ_L),
+//             dZ_{L-2} = (dZ_L W_L) * [A_{L-2} > 0] (BF16)
+//             hidden l: dW_l = dZ_l^T A_{l-1} as a tcgen05 GEMM over the batch (both operands
+//             transposed to K-major by a tiled transpose; A_{-1} is the transposed one-hot),
+//             db_l = colsum(dZ_l), dZ_{l-1} = (dZ_l W_l) * [A_{l-1} > 0] as a tcgen05 GEMM
+//             with the mask fused in the epilogue (W_l^T kept in BF16 beside W_l)
+//   update    Adam (bias-corrected) on the FP32 masters; BF16 copies W_l (K-padded, the
+//             inference layout) and W_l^T rewritten by the same kernel
+// Every reduction has a fixed order, so a step is deterministic.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <random>
+
+#include "common.cuh"
+
+namespace cbdfs {
+
+int tc_layer(bool first, int domain, bool fp8, bool out_fp8, int bn, const CUtensorMap &tmA,
+             const CUtensorMap &tmB, const uint64_t *states, uint32_t n, uint32_t rows_pad, int K,
+             int N, const float *bias, void *out, float acc_scale, float out_qscale, int *err,
+             cudaStream_t st);
+uint64_t npk(int n, int k);
+
+namespace {
+
+using namespace dev;
+
+constexpr int kThreads = 192;
+constexpr int kStageA = kBM * 128;
+
+// ---------------------------------------------------------------------------------------
+// TN GEMM on tcgen05: C[M][N] = A[M][K] B[N][K]^T, both BF16 K-major, FP32 accumulate.
+// EPI 1: C FP32.  EPI 2: C BF16 = acc * (mask[m][n] > 0) (mask BF16 [M][N]).
+// ---------------------------------------------------------------------------------------
+template <int BN, int EPI>
+__global__ void __launch_bounds__(kThreads, 1)
+k_gemm_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int K, int N,
+          void *__restrict__ out, const __nv_bfloat16 *__restrict__ mask, int stages, int *err) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    constexpr int kStageB = BN * 128;
+    const int KB = K / 64;
+    uint8_t *A = smem;
+    uint8_t *B = smem + stages * kStageA;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(B + stages * kStageB);
+    uint64_t *full = bars, *empty = bars + stages, *accum = bars + 2 * stages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * kBM;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        mbar_init(smem_u32(accum), 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), BN);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_d = *tmem_slot;
+    uint32_t issued = 0;
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kb = 0; kb < KB; ++kb) {
+                const int s = kb % stages, u = kb / stages;
+                if (kb >= stages && !mbar_wait(smem_u32(&empty[s]), (u - 1) & 1, err, DEVERR_STAGE_EMPTY)) break;
+                mbar_arrive_expect_tx(smem_u32(&full[s]), kStageA + kStageB);
+                tma_load_2d(smem_u32(A + s * kStageA), &tmA, smem_u32(&full[s]), kb * 64, m0);
+                tma_load_2d(smem_u32(B + s * kStageB), &tmB, smem_u32(&full[s]), kb * 64, n0);
+                ++issued;
+            }
+            // bounded drain of this thread's loads before the CTA can exit
+            for (uint32_t j = issued > (uint32_t)stages ? issued - stages : 0; j < issued; ++j)
+                mbar_wait(smem_u32(&full[j % stages]), (j / stages) & 1, err, DEVERR_TMA_FULL, 100000000ull);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = make_idesc(kBM, BN, 1, 1);
+            bool ok = true;
+            for (int kb = 0; kb < KB; ++kb) {
+                const int s = kb % stages, u = kb / stages;
+                if (!mbar_wait(smem_u32(&full[s]), u & 1, err, DEVERR_TMA_FULL)) { ok = false; break; }
+                tc_fence_after();
+                const uint64_t ad = sw128_desc(smem_u32(A + s * kStageA)), bd = sw128_desc(smem_u32(B + s * kStageB));
+#pragma unroll
+                for (int k = 0; k < 4; ++k) umma_bf16(tmem_d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                umma_commit(smem_u32(&empty[s]));
+            }
+            umma_commit(smem_u32(accum));
+            if (!ok) atomicExch(err, DEVERR_TMA_FULL);
+        }
+    } else {
+        const int q = warp & 3;
+        const uint32_t m = m0 + q * 32 + lane;
+        const bool good = mbar_wait(smem_u32(accum), 0, err, DEVERR_ACCUM);
+        tc_fence_after();
+#pragma unroll 1
+        for (int c = 0; c < BN / 32 && good; ++c) {
+            uint32_t r[32];
+            tmem_ld32(tmem_d + ((uint32_t)(q * 32) << 16) + c * 32, r);
+            tmem_ld_wait();
+            const size_t base = (size_t)m * N + n0 + c * 32;
+            if (EPI == 1) {
+                float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(out) + base);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                         __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+            } else {
+                const uint4 *mk = reinterpret_cast<const uint4 *>(mask + base);
+                uint32_t pk[16];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint4 mm = __ldg(mk + j);
+                    const __nv_bfloat162 *mh = reinterpret_cast<const __nv_bfloat162 *>(&mm);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const float2 a = __bfloat1622float2(mh[t]);
+                        const int e = 8 * j + 2 * t;
+                        const float v0 = a.x > 0.f ? __uint_as_float(r[e]) : 0.f;
+                        const float v1 = a.y > 0.f ? __uint_as_float(r[e + 1]) : 0.f;
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+                        pk[4 * j + t] = *reinterpret_cast<uint32_t *>(&h2);
+                    }
+                }
+                uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + base);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dst[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_d, BN);
+    }
+}
+
+template <int BN, int EPI>
+int gemm_tn(const CUtensorMap &tmA, const CUtensorMap &tmB, int M, int N, int K, void *out,
+            const __nv_bfloat16 *mask, int *err, cudaStream_t st) {
+    constexpr int kStageB = BN * 128;
+    const int stages = 4;
+    const size_t smem = 1024 + 256 + (size_t)stages * (kStageA + kStageB);
+    auto kern = k_gemm_tn<BN, EPI>;
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<dim3(N / BN, M / kBM), kThreads, smem, st>>>(tmA, tmB, K, N, out, mask, stages, err);
+    CUDA_TRY(cudaGetLastError());
+    return CBDFS_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------------------
+
+// BF16 transpose: in [R][C] -> out [C][R], 32 x 32 tiles through shared memory
+__global__ void k_transpose(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ out, int R, int C) {
+    __shared__ __nv_bfloat16 t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) t[i][threadIdx.x] = in[(size_t)(r0 + i) * C + c0 + threadIdx.x];
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) out[(size_t)(c0 + i) * R + r0 + threadIdx.x] = t[threadIdx.x][i];
+}
+
+// transposed one-hot X^T [K1pad][Bp] (BF16) of the packed states; rows >= n are zero
+template <int DOMAIN>
+__global__ void k_onehot_t(const uint64_t *__restrict__ states, uint32_t n, int Bp, __nv_bfloat16 *__restrict__ xt) {
+    const uint32_t m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= (uint32_t)Bp) return;
+    if (m >= n) return;  // the buffer was zeroed
+    const __nv_bfloat16 one = __float2bfloat16(1.f);
+    if (DOMAIN == CBDFS_DOM_RC3) {
+        const uint64_t w0 = states[2 * m], w1 = states[2 * m + 1];
+        for (int c = 0; c < 8; ++c) xt[(size_t)(c * 24 + ((w0 >> (5 * c)) & 31u)) * Bp + m] = one;
+        for (int e = 0; e < 12; ++e) xt[(size_t)(192 + e * 24 + ((w1 >> (5 * e)) & 31u)) * Bp + m] = one;
+    } else {
+        constexpr int N = DOMAIN == CBDFS_DOM_STP3 ? 9 : 16;
+        const uint64_t s = states[m];
+        for (int p = 0; p < N; ++p) xt[(size_t)(((s >> (4 * p)) & 15u) * N + p) * Bp + m] = one;
+    }
+}
+
+// logits[m][c] = sum_k A[m][k] W[c][k] + b[c] (A BF16, W FP32), one warp per row
+__global__ void k_logits(const __nv_bfloat16 *__restrict__ A, int K, int C, const float *__restrict__ W,
+                         const float *__restrict__ b, int n, float *__restrict__ logits) {
+    const int m = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (m >= n) return;
+    const __nv_bfloat16 *a = A + (size_t)m * K;
+    for (int c = 0; c < C; ++c) {
+        float part = 0.f;
+        for (int k = lane; k < K; k += 32) part = fmaf(__bfloat162float(a[k]), __ldg(W + (size_t)c * K + k), part);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+        if (lane == 0) logits[(size_t)m * C + c] = part + __ldg(b + c);
+    }
+}
+
+// loss and dZ = dLoss/dlogits (mean over n rows).  loss 0: softmax cross-entropy against
+// the class index; loss 1: 0.5 (y - label)^2 on one output.  Per-row losses to row_loss.
+__global__ void k_loss(const float *__restrict__ logits, const uint8_t *__restrict__ labels, int n, int C,
+                       int loss, float *__restrict__ dz, float *__restrict__ row_loss) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const float *z = logits + (size_t)m * C;
+    const float inv_n = 1.f / (float)n;
+    if (loss == 1) {
+        const float r = z[0] - (float)labels[m];
+        row_loss[m] = 0.5f * r * r;
+        dz[(size_t)m * C] = r * inv_n;
+        return;
+    }
+    float mx = z[0];
+    for (int c = 1; c < C; ++c) mx = fmaxf(mx, z[c]);
+    float sum = 0.f;
+    for (int c = 0; c < C; ++c) sum += expf(z[c] - mx);
+    const int y = labels[m];
+    row_loss[m] = logf(sum) + mx - z[y];
+    for (int c = 0; c < C; ++c) {
+        const float p = expf(z[c] - mx) / sum;
+        dz[(size_t)m * C + c] = (p - (c == y ? 1.f : 0.f)) * inv_n;
+    }
+}
+
+// dZ_prev[m][k] = (sum_c dZ[m][c] W[c][k]) * [A[m][k] > 0], BF16 out; rows >= n zero
+__global__ void k_back_last(const float *__restrict__ dz, int C, const float *__restrict__ W, int K,
+                            const __nv_bfloat16 *__restrict__ A, int n, int Bp, __nv_bfloat16 *__restrict__ out) {
+    const int m = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K || m >= Bp) return;
+    float s = 0.f;
+    if (m < n) {
+        for (int c = 0; c < C; ++c) s = fmaf(dz[(size_t)m * C + c], __ldg(W + (size_t)c * K + k), s);
+        if (!(__bfloat162float(A[(size_t)m * K + k]) > 0.f)) s = 0.f;
+    }
+    out[(size_t)m * K + k] = __float2bfloat16(s);
+}
+
+// dW[c][k] = sum_m dZ[m][c] A[m][k] (FP32, fixed order over m)
+__global__ void k_dw_last(const float *__restrict__ dz, int C, const __nv_bfloat16 *__restrict__ A, int K, int n,
+                          float *__restrict__ dw) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x, c = blockIdx.y;
+    if (k >= K) return;
+    float s = 0.f;
+    for (int m = 0; m < n; ++m) s = fmaf(dz[(size_t)m * C + c], __bfloat162float(A[(size_t)m * K + k]), s);
+    dw[(size_t)c * K + k] = s;
+}
+
+// column sums: out[j] = sum_m X[m][j] over m < n (FP32 or BF16 X), fixed order
+template <typename T>
+__global__ void k_colsum(const T *__restrict__ X, int n, int J, float *__restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J) return;
+    float s = 0.f;
+    for (int m = 0; m < n; ++m) s += (float)X[(size_t)m * J + j];
+    out[j] = s;
+}
+
+// sum of per-row losses (one block, fixed order), divided by n
+__global__ void k_mean(const float *__restrict__ v, int n, float *__restrict__ out) {
+    __shared__ float part[256];
+    float s = 0.f;
+    for (int i = threadIdx.x; i < n; i += 256) s += v[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int i = 0; i < 256; ++i) t += part[i];
+        *out = t / (float)n;
+    }
+}
+
+// Adam on FP32 masters; optional BF16 copies: w_lp[o][Kp] (padded inference layout) and
+// wt[i][O] (transposed, for the backward GEMM)
+__global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ mo,
+                       float *__restrict__ ve, int O, int I, float lr, float b1, float b2, float eps,
+                       float c1, float c2, __nv_bfloat16 *__restrict__ w_lp, int Kp,
+                       __nv_bfloat16 *__restrict__ wt) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= O * I) return;
+    const float gg = g[idx];
+    const float m = b1 * mo[idx] + (1.f - b1) * gg;
+    const float v = b2 * ve[idx] + (1.f - b2) * gg * gg;
+    mo[idx] = m;
+    ve[idx] = v;
+    const float mh = m / c1, vh = v / c2;
+    const float nw = w[idx] - lr * mh / (sqrtf(vh) + eps);
+    w[idx] = nw;
+    const int o = idx / I, i = idx % I;
+    if (w_lp) w_lp[(size_t)o * Kp + i] = __float2bfloat16(nw);
+    if (wt) wt[(size_t)i * O + o] = __float2bfloat16(nw);
+}
+
+// wt[i][O] = BF16(w[o][i])
+__global__ void k_write_t(const float *__restrict__ w, int O, int I, __nv_bfloat16 *__restrict__ wt) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= O * I) return;
+    wt[(size_t)(idx % I) * O + idx / I] = __float2bfloat16(w[idx]);
+}
+
+__global__ void k_gather(const uint64_t *__restrict__ src, const uint8_t *__restrict__ lab, const uint32_t *__restrict__ idx,
+                         int words, uint32_t n, uint64_t *__restrict__ dst, uint8_t *__restrict__ dlab) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = idx[i];
+    for (int w = 0; w < words; ++w) dst[(size_t)i * words + w] = src[(size_t)j * words + w];
+    dlab[i] = lab[j];
+}
+
+// Random walks of the blank from the goal (label generation): walk i draws from the
+// splitmix64 stream seeded with seed_for(tag, i) = mix((tag << 32) | i); first its length
+// 1 + (draw mod max_len), then each move uniformly (draw mod #choices) among the legal
+// directions (up, left, right, down order) other than the reverse of the previous one.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+template <int SIDE>
+__global__ void k_walks(uint32_t tag, uint64_t first, uint32_t n, int max_len, uint64_t *__restrict__ out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t idx = first + i;
+    uint64_t st = mix64(((uint64_t)tag << 32) | (idx & 0xFFFFFFFFull));
+    auto next = [&]() {
+        st += 0x9E3779B97F4A7C15ull;
+        return mix64(st);
+    };
+    uint64_t s = 0;
+    for (int t = 0; t < SIDE * SIDE; ++t) s |= (uint64_t)t << (4 * t);
+    int r = 0, c = 0, prev = -1;
+    const int len = 1 + (int)(next() % (uint64_t)max_len);
+    for (int k = 0; k < len; ++k) {
+        int cand[4], nc = 0;
+        const int dr[4] = {-1, 0, 0, 1}, dcl[4] = {0, -1, 1, 0};
+        for (int d = 0; d < 4; ++d) {
+            if (prev >= 0 && d == 3 - prev) continue;
+            const int nr = r + dr[d], ncl = c + dcl[d];
+            if (nr >= 0 && nr < SIDE && ncl >= 0 && ncl < SIDE) cand[nc++] = d;
+        }
+        const int d = cand[next() % (uint64_t)nc];
+        const int b = r * SIDE + c, nr = r + dr[d], ncl = c + dcl[d], q = nr * SIDE + ncl;
+        const uint64_t tile = (s >> (4 * q)) & 15u;
+        s = (s & ~((uint64_t)15 << (4 * q))) | (tile << (4 * b));
+        r = nr;
+        c = ncl;
+        prev = d;
+    }
+    out[i] = s;
+}
+
+}  // namespace
+
+// =========================================================================================
+// host side
+// =========================================================================================
+
+struct TrainState {
+    int L = 0, B = 0, Bp = 0;
+    int dims[kMaxLayers + 1] = {};
+    float *w[kMaxLayers] = {}, *b[kMaxLayers] = {};        // FP32 masters
+    float *mw[kMaxLayers] = {}, *vw[kMaxLayers] = {}, *mb[kMaxLayers] = {}, *vb[kMaxLayers] = {};
+    float *gw[kMaxLayers] = {}, *gb[kMaxLayers] = {};      // gradients
+    __nv_bfloat16 *wt[kMaxLayers] = {};                    // W_l^T BF16 (hidden layers >= 1)
+    __nv_bfloat16 *act[kMaxLayers] = {};                   // A_l, l = 0..L-2, [Bp][dims[l+1]]
+    __nv_bfloat16 *dz[kMaxLayers] = {};                    // dZ_l BF16 [Bp][dims[l+1]]
+    __nv_bfloat16 *t_dz = nullptr, *t_a = nullptr;         // transposes (largest)
+    float *logits = nullptr, *dzl = nullptr, *row_loss = nullptr, *loss = nullptr;
+    uint64_t *states = nullptr;
+    uint8_t *labels = nullptr;
+    int64_t step = 0;
+    std::vector<std::pair<void *, size_t>> allocs;
+    std::map<long long, CUtensorMap> maps;
+};
+
+static int talloc(Ctx *c, TrainState &T, void **p, size_t bytes) {
+    int rc = dev_alloc(c, p, bytes);
+    if (rc) return rc;
+    T.allocs.emplace_back(*p, bytes);
+    return cudaMemset(*p, 0, bytes) == cudaSuccess ? CBDFS_OK : fail(CBDFS_EDEVICE, "memset");
+}
+
+static const CUtensorMap *bmap(TrainState &T, const void *base, int inner, int outer, int box_outer) {
+    long long key = (long long)(uintptr_t)base;
+    key = key * 1000003LL + inner;
+    key = key * 1000003LL + outer;
+    key = key * 1000003LL + box_outer;
+    auto it = T.maps.find(key);
+    if (it != T.maps.end()) return &it->second;
+    CUtensorMap m;
+    if (make_tmap_2d(&m, const_cast<void *>(base), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (uint64_t)inner,
+                     (uint64_t)outer, 64, box_outer))
+        return nullptr;
+    return &T.maps.emplace(key, m).first->second;
+}
+
+void train_free(Ctx *c, TrainState *T) {
+    if (!T) return;
+    for (auto &a : T->allocs) dev_free(c, a.first, a.second);
+    delete T;
+}
+
+// set up (or resize) the training state of a BF16 network for batches of up to B states
+static int train_setup(Ctx *c, NetGPU &net, int B, const float *const *host_w, const float *const *host_b) {
+    if (net.prec != CBDFS_PREC_BF16) return fail(CBDFS_EINVAL, "training needs a BF16 network");
+    if (!net.train || net.train->B < B) {
+        if (!net.train && (!host_w || !host_b)) return fail(CBDFS_EINVAL, "no master weights to train from");
+        TrainState *old = net.train;
+        TrainState *T = new TrainState();
+        T->L = net.L;
+        for (int l = 0; l <= net.L; ++l) T->dims[l] = net.dims[l];
+        T->B = B;
+        T->Bp = (B + kBM - 1) / kBM * kBM;
+        const int L = net.L, Bp = T->Bp;
+        int rc = CBDFS_OK;
+        size_t maxw = 0;
+        for (int l = 1; l < L; ++l) maxw = std::max(maxw, (size_t)net.dims[l]);
+        const size_t k1 = (size_t)net.k1pad;
+        for (int l = 0; l < L && !rc; ++l) {
+            const size_t O = net.dims[l + 1], I = l == 0 ? k1 : (size_t)net.dims[l];
+            rc = talloc(c, *T, (void **)&T->w[l], O * I * 4);
+            if (!rc) rc = talloc(c, *T, (void **)&T->b[l], O * 4);
+            if (!rc) rc = talloc(c, *T, (void **)&T->mw[l], O * I * 4);
+            if (!rc) rc = talloc(c, *T, (void **)&T->vw[l], O * I * 4);
+            if (!rc) rc = talloc(c, *T, (void **)&T->mb[l], O * 4);
+            if (!rc) rc = talloc(c, *T, (void **)&T->vb[l], O * 4);
+            if (!rc) rc = talloc(c, *T, (void **)&T->gw[l], O * I * 4);
+            if (!rc) rc = talloc(c, *T, (void **)&T->gb[l], O * 4);
+            if (!rc && l >= 1 && l < L - 1) rc = talloc(c, *T, (void **)&T->wt[l], O * I * 2);
+            if (!rc && l < L - 1) rc = talloc(c, *T, (void **)&T->act[l], (size_t)Bp * O * 2);
+            if (!rc && l < L - 1) rc = talloc(c, *T, (void **)&T->dz[l], (size_t)Bp * O * 2);
+        }
+        if (!rc) rc = talloc(c, *T, (void **)&T->t_dz, (size_t)Bp * maxw * 2);
+        if (!rc) rc = talloc(c, *T, (void **)&T->t_a, (size_t)Bp * std::max(maxw, k1) * 2);
+        const int C = net.dims[L];
+        if (!rc) rc = talloc(c, *T, (void **)&T->logits, (size_t)Bp * C * 4);
+        if (!rc) rc = talloc(c, *T, (void **)&T->dzl, (size_t)Bp * C * 4);
+        if (!rc) rc = talloc(c, *T, (void **)&T->row_loss, (size_t)Bp * 4);
+        if (!rc) rc = talloc(c, *T, (void **)&T->loss, 4);
+        if (!rc) rc = talloc(c, *T, (void **)&T->states, (size_t)Bp * 16);
+        if (!rc) rc = talloc(c, *T, (void **)&T->labels, (size_t)Bp);
+        if (rc) {
+            train_free(c, T);
+            return rc;
+        }
+        // masters: from the old state (resize) or from the host copies (layer 0 padded to
+        // the one-hot K block with zero columns, which stay zero: their gradient is zero)
+        for (int l = 0; l < L; ++l) {
+            const size_t O = net.dims[l + 1], I = l == 0 ? k1 : (size_t)net.dims[l];
+            if (old) {
+                CUDA_TRY(cudaMemcpy(T->w[l], old->w[l], O * I * 4, cudaMemcpyDeviceToDevice));
+                CUDA_TRY(cudaMemcpy(T->b[l], old->b[l], O * 4, cudaMemcpyDeviceToDevice));
+                CUDA_TRY(cudaMemcpy(T->mw[l], old->mw[l], O * I * 4, cudaMemcpyDeviceToDevice));
+                CUDA_TRY(cudaMemcpy(T->vw[l], old->vw[l], O * I * 4, cudaMemcpyDeviceToDevice));
+                CUDA_TRY(cudaMemcpy(T->mb[l], old->mb[l], O * 4, cudaMemcpyDeviceToDevice));
+                CUDA_TRY(cudaMemcpy(T->vb[l], old->vb[l], O * 4, cudaMemcpyDeviceToDevice));
+            } else {
+                const size_t Iu = net.dims[l];
+                CUDA_TRY(cudaMemcpy2D(T->w[l], I * 4, host_w[l], Iu * 4, Iu * 4, O, cudaMemcpyHostToDevice));
+                CUDA_TRY(cudaMemcpy(T->b[l], host_b[l], O * 4, cudaMemcpyHostToDevice));
+            }
+        }
+        if (old) {
+            T->step = old->step;
+            train_free(c, old);
+        }
+        net.train = T;
+        // W^T copies of the hidden layers >= 1
+        for (int l = 1; l < L - 1; ++l) {
+            const int O = net.dims[l + 1], I = net.dims[l];
+            k_write_t<<<(O * I + 255) / 256, 256>>>(T->w[l], O, I, T->wt[l]);
+        }
+        CUDA_TRY(cudaDeviceSynchronize());
+    }
+    return CBDFS_OK;
+}
+
+// forward + loss + backward on the batch already in T.states / T.labels (n rows)
+static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t st) {
+    TrainState &T = *net.train;
+    const int L = net.L, C = net.dims[L];
+    const int Bp = (n + kBM - 1) / kBM * kBM;
+    int rc;
+    // forward through the tensor-core layers
+    for (int l = 0; l < L - 1; ++l) {
+        const bool first = l == 0;
+        const int K = first ? net.k1pad : net.dims[l];
+        const CUtensorMap *tmA = first ? &net.tm_w[0] : bmap(T, T.act[l - 1], K, T.Bp, kBM);
+        if (!tmA) return CBDFS_EDEVICE;
+        rc = tc_layer(first, net.domain, false, false, net.bn[l], *tmA, net.tm_w[l], T.states, n, Bp, K,
+                      net.dims[l + 1], T.b[l], T.act[l], 1.f, 1.f, c->d_err, st);
+        if (rc) return rc;
+    }
+    const int KL = net.dims[L - 1];
+    k_logits<<<(n + 7) / 8, 256, 0, st>>>(T.act[L - 2], KL, C, T.w[L - 1], T.b[L - 1], n, T.logits);
+    k_loss<<<(n + 255) / 256, 256, 0, st>>>(T.logits, T.labels, n, C, loss_kind, T.dzl, T.row_loss);
+    k_mean<<<1, 256, 0, st>>>(T.row_loss, n, T.loss);
+    // last layer backward (FP32)
+    k_dw_last<<<dim3((KL + 255) / 256, C), 256, 0, st>>>(T.dzl, C, T.act[L - 2], KL, n, T.gw[L - 1]);
+    k_colsum<float><<<(C + 255) / 256, 256, 0, st>>>(T.dzl, n, C, T.gb[L - 1]);
+    k_back_last<<<dim3((KL + 255) / 256, Bp), 256, 0, st>>>(T.dzl, C, T.w[L - 1], KL, T.act[L - 2], n, Bp,
+                                                            T.dz[L - 2]);
+    // hidden layers, last to first
+    for (int l = L - 2; l >= 0; --l) {
+        const int O = net.dims[l + 1], I = l == 0 ? net.k1pad : net.dims[l];
+        // dW_l = dZ_l^T A_{l-1}: transpose both to K-major over the batch
+        k_transpose<<<dim3(O / 32, Bp / 32), dim3(32, 8), 0, st>>>(T.dz[l], T.t_dz, Bp, O);
+        if (l == 0) {
+            CUDA_TRY(cudaMemsetAsync(T.t_a, 0, (size_t)I * Bp * 2, st));
+            if (net.domain == CBDFS_DOM_STP3) k_onehot_t<CBDFS_DOM_STP3><<<(Bp + 255) / 256, 256, 0, st>>>(T.states, n, Bp, T.t_a);
+            else if (net.domain == CBDFS_DOM_STP4) k_onehot_t<CBDFS_DOM_STP4><<<(Bp + 255) / 256, 256, 0, st>>>(T.states, n, Bp, T.t_a);
+            else k_onehot_t<CBDFS_DOM_RC3><<<(Bp + 255) / 256, 256, 0, st>>>(T.states, n, Bp, T.t_a);
+        } else {
+            k_transpose<<<dim3(I / 32, Bp / 32), dim3(32, 8), 0, st>>>(T.act[l - 1], T.t_a, Bp, I);
+        }
+        // the output width is the (padded) input width; padding columns of the one-hot are
+        // zero, so their gradient is exactly zero
+        const CUtensorMap *ma = bmap(T, T.t_dz, Bp, O, kBM);
+        const CUtensorMap *mb = bmap(T, T.t_a, Bp, I, I % 256 == 0 ? 256 : 128);
+        if (!ma || !mb) return CBDFS_EDEVICE;
+        rc = (I % 256 == 0) ? gemm_tn<256, 1>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st)
+                            : gemm_tn<128, 1>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st);
+        if (rc) return rc;
+        k_colsum<__nv_bfloat16><<<(O + 255) / 256, 256, 0, st>>>(T.dz[l], n, O, T.gb[l]);
+        if (l > 0) {
+            // dZ_{l-1} = (dZ_l W_l) * [A_{l-1} > 0]
+            const CUtensorMap *mz = bmap(T, T.dz[l], O, T.Bp, kBM);
+            const CUtensorMap *mw = bmap(T, T.wt[l], O, I, I % 256 == 0 ? 256 : 128);
+            if (!mz || !mw) return CBDFS_EDEVICE;
+            rc = (I % 256 == 0) ? gemm_tn<256, 2>(*mz, *mw, Bp, I, O, T.dz[l - 1], T.act[l - 1], c->d_err, st)
+                                : gemm_tn<128, 2>(*mz, *mw, Bp, I, O, T.dz[l - 1], T.act[l - 1], c->d_err, st);
+            if (rc) return rc;
+        }
+    }
+    CUDA_TRY(cudaGetLastError());
+    return CBDFS_OK;
+}
+
+static int train_update(Ctx *c, NetGPU &net, const cbdfs_train_cfg &tc, cudaStream_t st) {
+    TrainState &T = *net.train;
+    T.step++;
+    const float c1 = 1.f - powf(tc.beta1, (float)T.step), c2 = 1.f - powf(tc.beta2, (float)T.step);
+    for (int l = 0; l < net.L; ++l) {
+        const int O = net.dims[l + 1], I = l == 0 ? net.k1pad : net.dims[l];
+        __nv_bfloat16 *wlp = l < net.L - 1 ? static_cast<__nv_bfloat16 *>(net.w_lp[l]) : nullptr;
+        const int Kp = I;
+        k_adam<<<(O * I + 255) / 256, 256, 0, st>>>(T.w[l], T.gw[l], T.mw[l], T.vw[l], O, I, tc.lr, tc.beta1,
+                                                    tc.beta2, tc.eps, c1, c2, wlp, Kp,
+                                                    (l >= 1 && l < net.L - 1) ? T.wt[l] : nullptr);
+        k_adam<<<(O + 255) / 256, 256, 0, st>>>(T.b[l], T.gb[l], T.mb[l], T.vb[l], O, 1, tc.lr, tc.beta1, tc.beta2,
+                                                tc.eps, c1, c2, nullptr, 0, nullptr);
+        if (l == net.L - 1) {  // the inference head reads the FP32 last layer
+            CUDA_TRY(cudaMemcpyAsync(net.w32[l], T.w[l], (size_t)O * I * 4, cudaMemcpyDeviceToDevice, st));
+        }
+        CUDA_TRY(cudaMemcpyAsync(net.b32[l], T.b[l], (size_t)O * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    CUDA_TRY(cudaGetLastError());
+    return CBDFS_OK;
+}
+
+}  // namespace cbdfs
+
+using namespace cbdfs;
+
+static int get_train_net(cbdfs_ctx *ctx, int net_id, NetGPU **out) {
+    if (!ctx) return fail(CBDFS_EINVAL, "null context");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (net_id < 0 || net_id >= (int)c->heur_kind.size() || c->heur_kind[net_id] != 0)
+        return fail(CBDFS_EINVAL, "heuristic %d is not a network", net_id);
+    *out = c->nets[c->heur_index[net_id]].get();
+    return CBDFS_OK;
+}
+
+static int upload_batch(Ctx *c, NetGPU &net, const uint64_t *states, const uint8_t *labels, uint32_t n, cudaStream_t st) {
+    TrainState &T = *net.train;
+    const int w = dom_words(net.domain);
+    CUDA_TRY(cudaMemcpyAsync(T.states, states, (size_t)n * 8 * w, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(T.labels, labels, n, cudaMemcpyHostToDevice, st));
+    return CBDFS_OK;
+}
+
+static int check_labels(const NetGPU &net, const uint8_t *labels, uint64_t n, int loss) {
+    if (loss == CBDFS_LOSS_CE) {
+        for (uint64_t i = 0; i < n; ++i)
+            if (labels[i] >= net.dims[net.L]) return fail(CBDFS_EINVAL, "label %d of state %llu outside the %d classes", labels[i], (unsigned long long)i, net.dims[net.L]);
+    } else if (net.dims[net.L] != 1) {
+        return fail(CBDFS_EINVAL, "the squared-error loss needs one output");
+    }
+    return CBDFS_OK;
+}
+
+extern "C" {
+
+int cbdfs_train_grad(cbdfs_ctx *ctx, int net_id, const uint64_t *states, const uint8_t *labels, uint32_t n,
+                     int loss, float *loss_out, float *const *gw_out, float *const *gb_out) {
+    NetGPU *net;
+    int rc = get_train_net(ctx, net_id, &net);
+    if (rc) return rc;
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!states || !labels || !loss_out || !gw_out || !gb_out || n == 0) return fail(CBDFS_EINVAL, "null argument");
+    if (loss != CBDFS_LOSS_CE && loss != CBDFS_LOSS_MSE) return fail(CBDFS_EINVAL, "loss %d", loss);
+    if ((rc = check_labels(*net, labels, n, loss))) return rc;
+    CUDA_TRY(cudaSetDevice(c->device));
+    std::lock_guard<std::mutex> lk(c->device_call_mu);
+    const float *const *hw = nullptr;
+    std::vector<const float *> hwv, hbv;
+    for (int l = 0; l < net->L; ++l) {
+        hwv.push_back(net->host_w[l].data());
+        hbv.push_back(net->host_b[l].data());
+    }
+    hw = hwv.data();
+    if ((rc = train_setup(c, *net, (int)n, hw, hbv.data()))) return rc;
+    cudaStream_t st = c->slots[0].stream;
+    if ((rc = upload_batch(c, *net, states, labels, n, st))) return rc;
+    if ((rc = train_fwd_bwd(c, *net, (int)n, loss, st))) return rc;
+    TrainState &T = *net->train;
+    CUDA_TRY(cudaMemcpyAsync(loss_out, T.loss, 4, cudaMemcpyDeviceToHost, st));
+    for (int l = 0; l < net->L; ++l) {
+        const size_t O = net->dims[l + 1], Iu = net->dims[l], I = l == 0 ? (size_t)net->k1pad : Iu;
+        if (gw_out[l])
+            CUDA_TRY(cudaMemcpy2DAsync(gw_out[l], Iu * 4, T.gw[l], I * 4, Iu * 4, O, cudaMemcpyDeviceToHost, st));
+        if (gb_out[l]) CUDA_TRY(cudaMemcpyAsync(gb_out[l], T.gb[l], O * 4, cudaMemcpyDeviceToHost, st));
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    int flag = 0;
+    CUDA_TRY(cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return fail(CBDFS_ETIMEDOUT, "a device wait ran out (code %d)", flag);
+    return CBDFS_OK;
+}
+
+int net_train(cbdfs_ctx *ctx, int net_id, const uint64_t *states, const uint8_t *labels, uint64_t n,
+              const cbdfs_train_cfg *cfg, cbdfs_train_report *rep) {
+    NetGPU *net;
+    int rc = get_train_net(ctx, net_id, &net);
+    if (rc) return rc;
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!states || !labels || !cfg || !rep || n == 0) return fail(CBDFS_EINVAL, "null argument");
+    cbdfs_train_cfg tc = *cfg;
+    if (tc.batch == 0 || tc.batch > c->max_batch) return fail(CBDFS_EINVAL, "batch %u outside 1..max_batch", tc.batch);
+    if (tc.epochs < 1) return fail(CBDFS_EINVAL, "epochs %d", tc.epochs);
+    if (tc.loss != CBDFS_LOSS_CE && tc.loss != CBDFS_LOSS_MSE) return fail(CBDFS_EINVAL, "loss %d", tc.loss);
+    if (n > 0xFFFFFFFFull) return fail(CBDFS_EINVAL, "too many states");
+    if ((rc = check_labels(*net, labels, n, tc.loss))) return rc;
+    memset(rep, 0, sizeof(*rep));
+    CUDA_TRY(cudaSetDevice(c->device));
+    std::lock_guard<std::mutex> lk(c->device_call_mu);
+    std::vector<const float *> hwv, hbv;
+    for (int l = 0; l < net->L; ++l) {
+        hwv.push_back(net->host_w[l].data());
+        hbv.push_back(net->host_b[l].data());
+    }
+    if ((rc = train_setup(c, *net, (int)tc.batch, hwv.data(), hbv.data()))) return rc;
+    TrainState &T = *net->train;
+    cudaStream_t st = c->slots[0].stream;
+    const int w = dom_words(net->domain);
+    // the whole training set on the device
+    uint64_t *d_states = nullptr;
+    uint8_t *d_labels = nullptr;
+    uint32_t *d_idx = nullptr;
+    if ((rc = dev_alloc(c, (void **)&d_states, n * 8 * w))) return rc;
+    if ((rc = dev_alloc(c, (void **)&d_labels, n))) { dev_free(c, d_states, n * 8 * w); return rc; }
+    if ((rc = dev_alloc(c, (void **)&d_idx, n * 4))) {
+        dev_free(c, d_states, n * 8 * w);
+        dev_free(c, d_labels, n);
+        return rc;
+    }
+    auto cleanup = [&]() {
+        dev_free(c, d_states, n * 8 * w);
+        dev_free(c, d_labels, n);
+        dev_free(c, d_idx, n * 4);
+    };
+    if (cudaMemcpy(d_states, states, n * 8 * w, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_labels, labels, n, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cleanup();
+        return fail(CBDFS_EDEVICE, "training set upload");
+    }
+    std::vector<uint32_t> perm(n);
+    const auto t0 = std::chrono::steady_clock::now();
+    const uint64_t per_epoch = (n + tc.batch - 1) / tc.batch;
+    float loss = 0.f;
+    int64_t steps = 0;
+    for (int ep = 0; ep < tc.epochs && !rc; ++ep) {
+        // epoch order: Fisher-Yates driven by splitmix64(seed + epoch), j = draw mod (i+1)
+        for (uint64_t i = 0; i < n; ++i) perm[i] = (uint32_t)i;
+        uint64_t sm = tc.seed + 0x9E3779B97F4A7C15ull * (uint64_t)(ep + 1);
+        for (uint64_t i = n - 1; i > 0; --i) {
+            sm += 0x9E3779B97F4A7C15ull;
+            uint64_t z = sm;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            std::swap(perm[i], perm[z % (i + 1)]);
+        }
+        if (cudaMemcpyAsync(d_idx, perm.data(), n * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            rc = fail(CBDFS_EDEVICE, "permutation upload");
+            break;
+        }
+        for (uint64_t k = 0; k < per_epoch && !rc; ++k) {
+            if (tc.max_steps > 0 && steps >= tc.max_steps) break;
+            const uint32_t off = (uint32_t)(k * tc.batch);
+            const uint32_t bn = (uint32_t)std::min<uint64_t>(tc.batch, n - off);
+            k_gather<<<(bn + 255) / 256, 256, 0, st>>>(d_states, d_labels, d_idx + off, w, bn, T.states, T.labels);
+            rc = train_fwd_bwd(c, *net, (int)bn, tc.loss, st);
+            if (!rc) rc = train_update(c, *net, tc, st);
+            if (!rc && (steps == 0 || (steps & 255) == 255)) {
+                if (cudaMemcpyAsync(&loss, T.loss, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                    cudaStreamSynchronize(st) != cudaSuccess) {
+                    rc = fail(CBDFS_EDEVICE, "training step");
+                    break;
+                }
+                if (steps == 0) rep->first_loss = loss;
+            }
+            ++steps;
+        }
+        if (tc.max_steps > 0 && steps >= tc.max_steps) break;
+    }
+    if (!rc) {
+        if (cudaMemcpyAsync(&loss, T.loss, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = fail(CBDFS_EDEVICE, "training: %s", cudaGetErrorString(cudaGetLastError()));
+        rep->last_loss = loss;
+    }
+    rep->steps = steps;
+    rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    rep->samples = 0;
+    for (int64_t i = 0; i < steps; ++i) rep->samples += std::min<uint64_t>(tc.batch, n);
+    cleanup();
+    if (!rc) {
+        int flag = 0;
+        if (cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && flag)
+            rc = fail(CBDFS_ETIMEDOUT, "a device wait ran out (code %d)", flag);
+    }
+    return rc;
+}
+
+int cbdfs_net_read(cbdfs_ctx *ctx, int net_id, float *const *w_out, float *const *b_out) {
+    NetGPU *net;
+    int rc = get_train_net(ctx, net_id, &net);
+    if (rc) return rc;
+    if (!w_out || !b_out) return fail(CBDFS_EINVAL, "null argument");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    CUDA_TRY(cudaSetDevice(c->device));
+    for (int l = 0; l < net->L; ++l) {
+        const size_t O = net->dims[l + 1], Iu = net->dims[l];
+        if (net->train) {
+            const size_t I = l == 0 ? (size_t)net->k1pad : Iu;
+            if (w_out[l]) CUDA_TRY(cudaMemcpy2D(w_out[l], Iu * 4, net->train->w[l], I * 4, Iu * 4, O, cudaMemcpyDeviceToHost));
+            if (b_out[l]) CUDA_TRY(cudaMemcpy(b_out[l], net->train->b[l], O * 4, cudaMemcpyDeviceToHost));
+        } else {
+            if (w_out[l]) memcpy(w_out[l], net->host_w[l].data(), O * Iu * 4);
+            if (b_out[l]) memcpy(b_out[l], net->host_b[l].data(), O * 4);
+        }
+    }
+    return CBDFS_OK;
+}
+
+int cbdfs_gen_walk_states(cbdfs_ctx *ctx, int domain, uint32_t tag, uint64_t first, uint64_t n, int max_len,
+                          uint64_t *states_out) {
+    if (!ctx || !states_out) return fail(CBDFS_EINVAL, "null argument");
+    if (domain != CBDFS_DOM_STP3 && domain != CBDFS_DOM_STP4) return fail(CBDFS_EINVAL, "walks are for sliding-tile domains");
+    if (max_len < 1) return fail(CBDFS_EINVAL, "max_len %d", max_len);
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = c->slots[0].stream;
+    const uint64_t chunk = 1ull << 22;
+    uint64_t *d = nullptr;
+    int rc = dev_alloc(c, (void **)&d, std::min(n, chunk) * 8);
+    if (rc) return rc;
+    for (uint64_t o = 0; o < n && !rc; o += chunk) {
+        const uint32_t m = (uint32_t)std::min(chunk, n - o);
+        if (domain == CBDFS_DOM_STP3) k_walks<3><<<(m + 255) / 256, 256, 0, st>>>(tag, first + o, m, max_len, d);
+        else k_walks<4><<<(m + 255) / 256, 256, 0, st>>>(tag, first + o, m, max_len, d);
+        if (cudaMemcpyAsync(states_out + o, d, (size_t)m * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = fail(CBDFS_EDEVICE, "walk generation");
+    }
+    dev_free(c, d, std::min(n, chunk) * 8);
+    return rc;
+}
+
+}  // extern "C"

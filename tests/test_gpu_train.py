@@ -1,0 +1,151 @@
+"""The learned heuristic: label walks, gradients of the BF16 training step against the
+float64 oracle, the Adam update, and what a network trained on additive-PDB labels gains in
+the search over Manhattan distance alone."""
+import numpy as np
+import pytest
+
+import workloads as W
+from helpers import PREC
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2507_11916_b300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def ctx(P):
+    c = P.cbdfs_create(0, max_batch=8192, n_slots=4)
+    yield c
+    P.cbdfs_destroy(c)
+
+
+def _normwise(a, b):
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_walk_states_match_oracle(P, ctx, orc):
+    tag, first, n = W.TAG_C3, 17, 3000
+    gpu = P.cbdfs_gen_walk_states(ctx, P.DOM_STP4, tag, first, n, 250)
+    for i in range(0, n, 61):
+        dirs = W.stp_walk_random_length(4, 250, W.seed_for(tag, first + i))
+        assert int(gpu[i]) == orc.stp_apply_walk(4, dirs)
+    gpu3 = P.cbdfs_gen_walk_states(ctx, P.DOM_STP3, 7, 0, 200, 30)
+    for i in range(0, 200, 13):
+        assert int(gpu3[i]) == orc.stp_apply_walk(3, W.stp_walk_random_length(3, 30, W.seed_for(7, i)))
+
+
+def _grad_case(P, ctx, orc, cfg, dom, head, loss, n, seed, label_hi):
+    Ws, bs = W.net_weights(**cfg)
+    hid = P.cbdfs_net_load(ctx, dom, Ws, bs, PREC["bf16"], head, 0)
+    s = W.random_stp_states(4, n, seed)
+    labels = (W.splitmix64_array(seed + 1, n) % np.uint64(label_hi)).astype(np.uint8)
+    L, gw, gb = P.cbdfs_train_grad(ctx, hid, s, labels, cfg["dims"], loss)
+    Wq = orc.quantise_weights(Ws[:-1], "bf16") + [Ws[-1]]
+    kind = "ce" if loss == P.LOSS_CE else "mse"
+    X = orc.one_hot(dom, s)
+    ref64 = orc.train_forward_backward(Wq, bs, X, labels, kind)
+    emu = orc.train_forward_backward(Wq, bs, X, labels, kind, bf16_storage=True)
+    return hid, s, labels, Ws, bs, L, gw, gb, ref64, emu
+
+
+# The training step stores hidden activations and hidden dZ in BF16.  Against the oracle's
+# emulation of exactly that storage the gradients agree to 1e-2 normwise (the remaining
+# difference is FP32 versus float64 accumulation); against plain float64 the BF16 storage
+# itself moves them (ReLU units within a rounding step of 0 change side), by up to 0.1.
+def _check_grads(L, gw, gb, ref64, emu):
+    L64, gW64, gb64 = ref64
+    Le, gWe, gbe = emu
+    assert abs(L - Le) <= 1e-3 * abs(Le)
+    for l in range(len(gw)):
+        ew, eb = _normwise(gw[l], gWe[l]), _normwise(gb[l], gbe[l])
+        fw = _normwise(gw[l], gW64[l])
+        print(f"layer {l}: dW vs emulation {ew:.2e}, db {eb:.2e}; dW vs float64 {fw:.2e}")
+        assert ew <= 1e-2 and eb <= 1e-2
+        assert fw <= 0.1
+
+
+@pytest.mark.parametrize("n", [300, 1024])
+def test_gradients_match_oracle_ce(P, ctx, orc, n):
+    _, _, _, _, _, L, gw, gb, ref64, emu = _grad_case(
+        P, ctx, orc, W.NET_C3, P.DOM_STP4, P.HEAD_CLASSIFIER, P.LOSS_CE, n, 900 + n, 81)
+    _check_grads(L, gw, gb, ref64, emu)
+
+
+def test_gradients_match_oracle_mse(P, ctx, orc):
+    _, _, _, _, _, L, gw, gb, ref64, emu = _grad_case(
+        P, ctx, orc, W.NET_C1, P.DOM_STP4, P.HEAD_REGRESSION, P.LOSS_MSE, 640, 4242, 60)
+    _check_grads(L, gw, gb, ref64, emu)
+
+
+def test_adam_step_matches_oracle(P, ctx, orc):
+    # the update is pinned given the gradients: one step of net_train on the whole set (one
+    # batch) equals the oracle's Adam applied to the library's own gradients
+    hid, s, labels, Ws, bs, L, gw, gb, _, _ = _grad_case(
+        P, ctx, orc, W.NET_C3, P.DOM_STP4, P.HEAD_CLASSIFIER, P.LOSS_CE, 512, 77, 81)
+    rep = P.net_train(ctx, hid, s, labels, batch=512, epochs=1, lr=1e-3, seed=5)
+    assert rep["steps"] == 1
+    Wn, bn = P.cbdfs_net_read(ctx, hid, W.NET_C3["dims"])
+    # net_train visits the set in a permuted order, so its FP32 sums differ from the
+    # natural-order gradient in the last bits; Adam's first step is about -lr*sign(g), so
+    # gradients within that noise of zero (|g| < 1e-7, a handful of elements) may step either
+    # way: those are held only to the step bound lr
+    for got_all, w0_all, g_all in ((Wn, Ws, gw), (bn, bs, gb)):
+        for l in range(len(Ws)):
+            w0, g, got = w0_all[l].astype(np.float64), g_all[l].astype(np.float64), got_all[l]
+            z = np.zeros_like(w0)
+            want, _, _ = orc.adam_step(w0, g, z, z, 1)
+            sig = np.abs(g) >= 1e-7
+            assert np.allclose(got[sig], want[sig], rtol=1e-5, atol=2e-6)
+            assert (np.abs(got[~sig] - w0[~sig]) <= 1e-3 * 1.001).all()
+            zero = g == 0  # no gradient, no step
+            assert np.array_equal(got[zero], w0[zero].astype(np.float32))
+            assert ((~sig) & ~zero).mean() < 1e-2  # the exempt set stays small
+
+
+def test_training_on_pdb_labels_gains_over_manhattan(P, ctx, orc):
+    # labels: the additive 6-6-3 PDB on states of random walks from the goal (lengths 1..250)
+    pats = [list(p) for p in orc.PATTERNS_663]
+    tabs = [P.pdb_build(ctx, P.DOM_STP4, t) for t in pats]
+    pdb = P.cbdfs_pdb_load(ctx, P.DOM_STP4, pats, tabs)
+    n = 409600
+    states = P.cbdfs_gen_walk_states(ctx, P.DOM_STP4, W.TAG_C3, 0, n, 250)
+    labels = np.concatenate([
+        P.heur_submit_batch(ctx, pdb, P.DOM_STP4, states[o:o + 8192], np.zeros(min(8192, n - o), np.uint8), 255)[0]
+        for o in range(0, n, 8192)])
+    assert labels.max() <= 80
+    Ws, bs = W.net_weights(**W.NET_C3)
+    hid = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, PREC["bf16"], P.HEAD_CLASSIFIER, 1)
+    rep = P.net_train(ctx, hid, states, labels, batch=8192, epochs=3, lr=1e-3, seed=3)
+    print("train report", rep)
+    assert rep["last_loss"] < 0.6 * rep["first_loss"]
+    # held-out states: predicted class (network alone) against the PDB value
+    held = P.cbdfs_gen_walk_states(ctx, P.DOM_STP4, W.TAG_C3, 10_000_000, 8192, 250)
+    plain = P.cbdfs_net_load(ctx, P.DOM_STP4, *P.cbdfs_net_read(ctx, hid, W.NET_C3["dims"]),
+                             PREC["bf16"], P.HEAD_CLASSIFIER, 0)
+    h_nn = P.heur_submit_batch(ctx, plain, P.DOM_STP4, held, np.zeros(8192, np.uint8), 255)[0]
+    h_pdb = P.heur_submit_batch(ctx, pdb, P.DOM_STP4, held, np.zeros(8192, np.uint8), 255)[0]
+    md = np.array([orc.stp_md(int(x), 4) for x in held])
+    err = np.abs(h_nn.astype(int) - h_pdb.astype(int))
+    print(f"held-out: mean |h_nn - h_pdb| {err.mean():.2f}, exact {np.mean(err == 0):.3f}, "
+          f"inadmissible vs PDB {np.mean(h_nn > h_pdb):.3f}, mean MD {md.mean():.1f}, "
+          f"mean PDB {h_pdb.mean():.1f}, mean NN {h_nn.mean():.1f}")
+    assert np.mean(np.abs(h_nn.astype(int) - h_pdb.astype(int))) < np.mean(h_pdb.astype(int) - md)
+    # the search: max(network, MD) expands fewer nodes than MD alone
+    tot_md = tot_nn = 0
+    for i in range(6):
+        s = orc.stp_apply_walk(4, W.stp_walk(4, 50, W.seed_for(W.TAG_C1, 7000 + i)))
+        a = P.cbdfs_solve(ctx, P.DOM_STP4, s, P.ALGO_IDA, P.HEUR_MD, threads=8, work_num=16,
+                          batch=2048, timeout_us=300, time_limit_s=60)
+        b = P.cbdfs_solve(ctx, P.DOM_STP4, s, P.ALGO_IDA, hid, threads=8, work_num=16,
+                          batch=2048, timeout_us=300, time_limit_s=60)
+        assert b["cost"] >= a["cost"]
+        tot_md += a["expanded"]
+        tot_nn += b["expanded"]
+        print(f"instance {i}: MD cost {a['cost']} expanded {a['expanded']}; "
+              f"network cost {b['cost']} expanded {b['expanded']}")
+    assert tot_nn < tot_md

@@ -186,3 +186,23 @@ def test_e4m3_activation_emulation(orc):
     _, he = orc.mlp_forward(Ws2, bs2, X2, return_hidden=True, act_scales=[0.01, 0.01])
     big = hp[0] > 2 ** -6 * 0.01
     assert (np.abs(he[0] - hp[0])[big] <= 2 ** -4 * hp[0][big] + 1e-12).all()
+
+
+def test_bf16_storage_emulation(orc):
+    # with every stored value exactly representable in bfloat16 the emulation changes nothing
+    Ws = [np.array([[1.0, 0.5], [0.25, -1.0]]), np.array([[2.0, -0.5], [1.0, 1.0]]),
+          np.array([[1.0, 1.0], [0.5, -1.0]])]
+    bs = [np.zeros(2), np.array([0.5, 0.0]), np.zeros(2)]
+    X = np.array([[1.0, 2.0], [3.0, 0.0]])
+    a = orc.train_forward_backward(Ws, bs, X, np.array([0, 1]), "ce")
+    b = orc.train_forward_backward(Ws, bs, X, np.array([0, 1]), "ce", bf16_storage=True)
+    assert a[0] == b[0]
+    # the first hidden layer's gradient only involves exact values here
+    assert np.array_equal(a[1][0], b[1][0]) or np.allclose(a[1][0], b[1][0], rtol=2 ** -8)
+    # and a random network moves by at most a few bfloat16 ulps per stored value
+    Ws2, bs2 = W.net_weights([16, 32, 32, 4], "kaiming", 4)
+    X2 = np.random.default_rng(0).random((20, 16))
+    lab = np.arange(20) % 4
+    g1 = orc.train_forward_backward(Ws2, bs2, X2, lab, "ce")
+    g2 = orc.train_forward_backward(Ws2, bs2, X2, lab, "ce", bf16_storage=True)
+    assert abs(g1[0] - g2[0]) < 1e-2 * abs(g1[0])

@@ -122,6 +122,27 @@ def stp_walk(side: int, length: int, seed: int) -> list[int]:
     return out
 
 
+def stp_walk_random_length(side: int, max_len: int, seed: int) -> list[int]:
+    """The labelled-state walks: one splitmix64 stream (SplitMix64(seed)) gives first the
+    length 1 + (draw mod max_len), then the moves exactly as stp_walk draws them."""
+    rng = SplitMix64(seed)
+    length = 1 + rng.below(max_len)
+    r = c = 0
+    prev = -1
+    out = []
+    for _ in range(length):
+        legal = []
+        for d, (dr, dc) in enumerate(((-1, 0), (0, -1), (0, 1), (1, 0))):
+            if prev >= 0 and d == 3 - prev:
+                continue
+            if 0 <= r + dr < side and 0 <= c + dc < side:
+                legal.append((d, dr, dc))
+        d, dr, dc = legal[rng.below(len(legal))]
+        r, c, prev = r + dr, c + dc, d
+        out.append(d)
+    return out
+
+
 def random_stp_states(side: int, n: int, seed: int) -> np.ndarray:
     """n uniformly random solvable sliding-tile states, packed (uint64)."""
     ncell = side * side
