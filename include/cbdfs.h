@@ -217,6 +217,50 @@ int cbdfs_eval_trace(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_
 int cbdfs_device_status(cbdfs_ctx *ctx);
 
 /* ---------------------------------------------------------------------------------------
+ * Serving: continuous batching of requests from many threads (paper: the batch-processing
+ * thread of SingleGPU Batch CB-DFS gathers states from the searching threads, evaluates
+ * them on the GPU and keeps more than one batch in flight).  A server thread takes queued
+ * requests of one heuristic, in arrival order, into one launch of up to bucket_max states
+ * as soon as an evaluation slot is free and the memory budget allows, replays the CUDA
+ * graph captured for (slot, heuristic, size bucket = next power of two), and lets launches
+ * on different slots overlap on the device.  Each request's h is exactly what it would get
+ * alone (rows are independent); its mask and least f above its own bound are formed at
+ * completion.  Caller buffers must stay valid until heur_request_wait returns.
+ * ------------------------------------------------------------------------------------- */
+typedef struct { uint64_t id; } cbdfs_ticket;
+
+typedef struct {
+    int max_inflight;       /* launches on the device at once (slots taken); 0 = all free slots */
+    uint32_t bucket_min;    /* smallest launch size (0 = 32) */
+    uint32_t bucket_max;    /* largest launch size and largest request (0 = 4096) */
+    size_t mem_budget;      /* device bytes in-flight launches may use; 0 = no limit */
+    int coalesce;           /* 1: merge queued requests of one heuristic into a launch */
+} cbdfs_server_cfg;
+
+typedef struct {
+    uint64_t requests, states, launches;
+    double p50_us, p99_us, mean_us;   /* request latency, submit to completion */
+    double states_per_s;              /* states completed / (last completion - first submit) */
+} cbdfs_server_stats;
+
+/* Start the server (at most one per context).  Errors: EINVAL (no free slot, buckets),
+ * ENOMEM, EDEVICE.  Load networks before starting: a later load may reallocate scratch. */
+int cbdfs_server_start(cbdfs_ctx *ctx, const cbdfs_server_cfg *cfg);
+/* Finish every queued request, then stop the server and release its slots. */
+int cbdfs_server_stop(cbdfs_ctx *ctx);
+/* Queue a request (arguments as heur_submit_batch, 1 <= n <= bucket_max); *t identifies it.
+ * Thread-safe.  Errors: EINVAL, ECANCELED (stopping). */
+int heur_request_submit(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *states,
+                        const uint8_t *g, uint32_t bound, uint32_t n, uint8_t *h_out,
+                        uint32_t *mask_out, uint32_t *minf_out, cbdfs_ticket *t);
+/* Wait up to timeout_us (0: just test) for a request; its results are then in the caller's
+ * buffers.  Returns OK, ETIMEDOUT (still running; wait again), EINVAL (unknown or already
+ * collected ticket), or the launch's error. */
+int heur_request_wait(cbdfs_ctx *ctx, cbdfs_ticket t, uint64_t timeout_us);
+/* Latency and throughput of the requests completed so far. */
+int cbdfs_server_get_stats(cbdfs_ctx *ctx, cbdfs_server_stats *out);
+
+/* ---------------------------------------------------------------------------------------
  * Learning the network heuristic (paper: Experimental Setup -- the heuristics are trained
  * from PDB values).  BF16 networks only.  One step on a batch: BF16 tensor-core forward
  * (activations kept), FP32 last layer and loss, backward with BF16 tensor-core GEMMs and

@@ -89,6 +89,22 @@ class TrainReport(ctypes.Structure):
                 ("first_loss", ctypes.c_float), ("last_loss", ctypes.c_float)]
 
 
+class Ticket(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64)]
+
+
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_int), ("bucket_min", ctypes.c_uint32),
+                ("bucket_max", ctypes.c_uint32), ("mem_budget", ctypes.c_size_t),
+                ("coalesce", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_uint64), ("states", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("states_per_s", ctypes.c_double)]
+
+
 class Result(ctypes.Structure):
     _fields_ = [("cost", ctypes.c_int), ("path_len", ctypes.c_int), ("path", ctypes.c_int * 256),
                 ("n_iters", ctypes.c_int),
@@ -136,6 +152,12 @@ _lib.cbdfs_train_grad.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_uint32, 
 _lib.cbdfs_net_read.argtypes = [_vp, ctypes.c_int, _FPP, _FPP]
 _lib.cbdfs_gen_walk_states.argtypes = [_vp, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64,
                                        ctypes.c_uint64, ctypes.c_int, _vp]
+_lib.cbdfs_server_start.argtypes = [_vp, ctypes.POINTER(ServerCfg)]
+_lib.cbdfs_server_stop.argtypes = [_vp]
+_lib.heur_request_submit.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint32,
+                                     ctypes.c_uint32, _vp, _vp, _vp, ctypes.POINTER(Ticket)]
+_lib.heur_request_wait.argtypes = [_vp, Ticket, ctypes.c_uint64]
+_lib.cbdfs_server_get_stats.argtypes = [_vp, ctypes.POINTER(ServerStats)]
 _lib.cbdfs_apply_moves.argtypes = [ctypes.c_int, _u64p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                    _u64p]
 _lib.cbdfs_manhattan.argtypes = [ctypes.c_int, ctypes.c_uint64]
@@ -151,7 +173,8 @@ EXPORTED = ["cbdfs_create", "cbdfs_destroy", "cbdfs_last_error", "cbdfs_mem_used
             "cbdfs_pdb_load", "pdb_build", "heur_submit_batch", "heur_eval_device",
             "heur_eval_device_static",
             "cbdfs_device_status", "cbdfs_eval_profile", "cbdfs_eval_trace", "net_train",
-            "cbdfs_train_grad", "cbdfs_net_read", "cbdfs_gen_walk_states", "cbdfs_apply_moves", "cbdfs_manhattan", "cbdfs_solve",
+            "cbdfs_train_grad", "cbdfs_net_read", "cbdfs_gen_walk_states", "cbdfs_server_start",
+            "cbdfs_server_stop", "heur_request_submit", "heur_request_wait", "cbdfs_server_get_stats", "cbdfs_apply_moves", "cbdfs_manhattan", "cbdfs_solve",
             "cbdfs_search_defaults", "cbdfs_cancel"]
 
 
@@ -338,6 +361,50 @@ def cbdfs_gen_walk_states(ctx, domain, tag, first, n, max_len) -> np.ndarray:
     out = np.empty(n, dtype=np.uint64)
     _check(_lib.cbdfs_gen_walk_states(ctx, domain, tag, first, n, max_len, _ptr(out)))
     return out
+
+
+def cbdfs_server_start(ctx, max_inflight=0, bucket_min=32, bucket_max=4096, mem_budget=0, coalesce=1):
+    _check(_lib.cbdfs_server_start(ctx, ctypes.byref(ServerCfg(max_inflight, bucket_min, bucket_max,
+                                                               mem_budget, coalesce))))
+
+
+def cbdfs_server_stop(ctx):
+    _check(_lib.cbdfs_server_stop(ctx))
+
+
+class Request:
+    """A queued request; its result arrays are owned here until wait() returns."""
+
+    def __init__(self, ctx, heur_id, domain, states, g, bound):
+        self.ctx = ctx
+        self.states = np.ascontiguousarray(states, dtype=np.uint64)
+        self.g = np.ascontiguousarray(g, dtype=np.uint8)
+        n = len(self.g)
+        self.h = np.empty(n, dtype=np.uint8)
+        self.mask = np.empty((n + 31) // 32, dtype=np.uint32)
+        self.minf = np.empty(1, dtype=np.uint32)
+        self.ticket = Ticket()
+        _check(_lib.heur_request_submit(ctx, heur_id, domain, _ptr(self.states), _ptr(self.g), bound, n,
+                                        _ptr(self.h), _ptr(self.mask), _ptr(self.minf),
+                                        ctypes.byref(self.ticket)))
+
+    def wait(self, timeout_us=60_000_000):
+        _check(_lib.heur_request_wait(self.ctx, self.ticket, timeout_us))
+        return self.h, self.mask, int(self.minf[0])
+
+
+def heur_request_submit(ctx, heur_id, domain, states, g, bound) -> Request:
+    return Request(ctx, heur_id, domain, states, g, bound)
+
+
+def heur_request_wait(ctx, req: Request, timeout_us=60_000_000):
+    return req.wait(timeout_us)
+
+
+def cbdfs_server_get_stats(ctx) -> dict:
+    st = ServerStats()
+    _check(_lib.cbdfs_server_get_stats(ctx, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in ServerStats._fields_}
 
 
 def cbdfs_apply_moves(domain, start, moves):

@@ -479,6 +479,7 @@ void cbdfs_destroy(cbdfs_ctx *ctx) {
     if (!ctx) return;
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     cudaSetDevice(c->device);
+    if (c->server) cbdfs_server_stop(ctx);
     cudaDeviceSynchronize();
     for (auto &s : c->slots) {
         for (int i = 0; i < 2; ++i) dev_free(c, s.act[i], c->act_bytes);

@@ -104,6 +104,9 @@ struct Slot {
     int *trace_grid = nullptr;
 };
 
+struct Server;  // serve.cpp
+void server_free(struct Ctx *c, Server *S);
+
 struct Ctx {
     int device = 0;
     size_t mem_budget = 0, mem_used = 0;
@@ -122,6 +125,7 @@ struct Ctx {
     size_t max_width = 0;
     size_t partial_floats = 0;         // per-row head partials the chain scratch holds
     int num_sms = 0;
+    Server *server = nullptr;
 };
 
 // allocation through the context's budget
