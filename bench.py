@@ -190,13 +190,14 @@ def run_reference(args):
         "e2e": {"value": v, "unit": "states/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
-def search_rates(P, ctx, hid_bf16, hid_fp32, seconds):
-    """IDA* nodes/s with the network heuristic (BF16 vs FP32) at equal solution cost."""
+def search_rates(P, ctx, hids, seconds):
+    """IDA* nodes/s with the network heuristic (h = max(rint(y), 0, MD)) in each precision at
+    equal solution cost, and the serial oracle's nodes/s with MD on the same starts."""
     out = {}
     starts = [P.cbdfs_apply_moves(P.DOM_STP4, W.stp_goal(4), W.stp_walk(4, 60, W.seed_for(W.TAG_C1, i)))
               for i in range(4)]
     threads = min(32, os.cpu_count() or 4)
-    for name, hid in (("bf16", hid_bf16), ("fp32", hid_fp32)):
+    for name, hid in hids.items():
         costs, exp, gen, secs, nb, ev = [], 0, 0, 0.0, 0, 0
         for s in starts:
             r = P.cbdfs_solve(ctx, P.DOM_STP4, s, P.ALGO_IDA, hid, partial_ok=True, threads=threads,
@@ -209,9 +210,142 @@ def search_rates(P, ctx, hid_bf16, hid_fp32, seconds):
             ev += r["evaluated"]
         out[name] = {"costs": costs, "expanded_per_s": exp / secs, "generated_per_s": gen / secs,
                      "avg_batch": ev / max(nb, 1), "seconds": secs, "threads": threads}
-    out["equal_cost"] = out["bf16"]["costs"] == out["fp32"]["costs"]
+    costs = [v["costs"] for v in out.values()]
+    out["equal_cost"] = all(c == costs[0] for c in costs)
     out["instances"] = "4 seeded 60-move 15-puzzle walks, h = max(rint(y), 0, MD)"
+    try:
+        import oracle
+        t0 = time.perf_counter()
+        n = 0
+        for s in starts[:2]:
+            r = oracle.ida_star(oracle.DOM_STP4, int(s), oracle.Heur(oracle.H_MD))
+            n += sum(it[1] for it in r["iters"])
+        out["oracle_md_expanded_per_s_1core"] = n / (time.perf_counter() - t0)
+    except Exception as e:  # the oracle is context only
+        out["oracle_md_expanded_per_s_1core"] = f"unavailable: {e}"
     return out
+
+
+def train_leg(P, args):
+    """The training configuration: 6-6-3 additive PDB built on the GPU, 10M walk states
+    labelled by it, the 81-class network trained 5 epochs (batch 8192, Adam 1e-3); then the
+    inadmissible fraction on held-out states and IDA* node counts against the PDB alone."""
+    import numpy as np
+    out = {}
+    ctx = P.cbdfs_create(0, max_batch=65536, n_slots=2)
+    try:
+        t0 = time.perf_counter()
+        pats = [[1, 2, 3, 5, 6, 7], [4, 8, 9, 12, 13, 14], [10, 11, 15]]
+        tabs = [P.pdb_build(ctx, P.DOM_STP4, t) for t in pats]
+        out["pdb_build_s"] = time.perf_counter() - t0
+        pdb = P.cbdfs_pdb_load(ctx, P.DOM_STP4, pats, tabs)
+        n = args.train_states
+        t0 = time.perf_counter()
+        states = P.cbdfs_gen_walk_states(ctx, P.DOM_STP4, W.TAG_C3, 0, n, 250)
+        labels = np.concatenate([P.heur_submit_batch(ctx, pdb, P.DOM_STP4, states[o:o + 65536],
+                                                     np.zeros(min(65536, n - o), np.uint8), 255)[0]
+                                 for o in range(0, n, 65536)])
+        out["label_s"] = time.perf_counter() - t0
+        Ws, bs = W.net_weights(**W.NET_C3)
+        hid = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, P.PREC_BF16, P.HEAD_CLASSIFIER, 1)
+        rep = P.net_train(ctx, hid, states, labels, batch=8192, epochs=args.train_epochs, lr=1e-3, seed=3)
+        dims = W.NET_C3["dims"]
+        fwd = 2 * sum(dims[l] * dims[l + 1] for l in range(len(dims) - 1))
+        out["train"] = dict(rep, samples_per_s=rep["samples"] / rep["seconds"],
+                            tflops=3 * fwd * rep["samples"] / rep["seconds"] / 1e12,
+                            states=n, epochs=args.train_epochs, batch=8192)
+        held = P.cbdfs_gen_walk_states(ctx, P.DOM_STP4, W.TAG_C3, 1 << 31, 65536, 250)
+        plain = P.cbdfs_net_load(ctx, P.DOM_STP4, *P.cbdfs_net_read(ctx, hid, dims), P.PREC_BF16,
+                                 P.HEAD_CLASSIFIER, 0)
+        z = np.zeros(65536, np.uint8)
+        h_nn = P.heur_submit_batch(ctx, plain, P.DOM_STP4, held, z, 255)[0].astype(int)
+        h_pdb = P.heur_submit_batch(ctx, pdb, P.DOM_STP4, held, z, 255)[0].astype(int)
+        out["held_out"] = {"states": 65536, "inadmissible_vs_pdb": float(np.mean(h_nn > h_pdb)),
+                           "exact": float(np.mean(h_nn == h_pdb)),
+                           "mean_abs_err": float(np.mean(np.abs(h_nn - h_pdb)))}
+        # IDA* on the 200-move starts: per completed bound, nodes with max(NN, MD) vs the PDB
+        cmp = []
+        threads = min(32, os.cpu_count() or 4)
+        for i in range(2):
+            s = P.cbdfs_apply_moves(P.DOM_STP4, W.stp_goal(4), W.stp_walk(4, 200, W.seed_for(W.TAG_C1, i)))
+            res = {}
+            for name, h in (("network", hid), ("pdb", pdb)):
+                r = P.cbdfs_solve(ctx, P.DOM_STP4, s, P.ALGO_IDA, h, partial_ok=True, threads=threads,
+                                  work_num=64, batch=8192, timeout_us=500, time_limit_s=args.search_seconds)
+                done = r["iters"] if r["status"] == 0 else r["iters"][:-1]
+                res[name] = {"cost": r["cost"] if r["status"] == 0 else None,
+                             "iters": {int(b): int(e) for b, e, _ in done}, "seconds": r["seconds"]}
+            common = sorted(set(res["network"]["iters"]) & set(res["pdb"]["iters"]))
+            cmp.append({"start": i, "network_cost": res["network"]["cost"], "pdb_cost": res["pdb"]["cost"],
+                        "bounds_compared": common,
+                        "expanded_network": sum(res["network"]["iters"][b] for b in common),
+                        "expanded_pdb": sum(res["pdb"]["iters"][b] for b in common)})
+        out["ida_vs_pdb"] = cmp
+    finally:
+        P.cbdfs_destroy(ctx)
+    return out
+
+
+def serve_leg(P, args):
+    """Mixed requests (15-puzzle 81-class network and cube network, BF16; sizes log-uniform in
+    32..4096) from many threads through the continuous-batching server."""
+    import concurrent.futures as cf
+    import numpy as np
+    ctx = P.cbdfs_create(0, max_batch=8192, n_slots=6)
+    try:
+        W3, b3 = W.net_weights(**W.NET_C3)
+        W2, b2 = W.net_weights(**W.NET_C2)
+        ids = [P.cbdfs_net_load(ctx, P.DOM_STP4, W3, b3, P.PREC_BF16, P.HEAD_CLASSIFIER, 1),
+               P.cbdfs_net_load(ctx, P.DOM_RC3, W2, b2, P.PREC_BF16, P.HEAD_CLASSIFIER, 0)]
+        rng = W.SplitMix64(0xC4)
+        reqs = []
+        for i in range(args.serve_requests):
+            size = int(round(32 * (4096 / 32) ** rng.uniform()))
+            kind = rng.below(2)
+            st = W.random_stp_states(4, size, i) if kind == 0 else W.random_rc_states(size, i).reshape(-1)
+            reqs.append((kind, st, np.zeros(size, np.uint8)))
+        P.cbdfs_server_start(ctx, max_inflight=5, bucket_max=4096, coalesce=1)
+        # warm the graphs, then the timed mix
+        for kind, st, g in reqs[:16]:
+            P.heur_request_submit(ctx, ids[kind], P.DOM_STP4 if kind == 0 else P.DOM_RC3, st, g, 60).wait()
+        P.cbdfs_server_stop(ctx)
+        P.cbdfs_server_start(ctx, max_inflight=5, bucket_max=4096, coalesce=1)
+
+        def run(k):
+            for j in range(k, len(reqs), args.serve_threads):
+                kind, st, g = reqs[j]
+                P.heur_request_submit(ctx, ids[kind], P.DOM_STP4 if kind == 0 else P.DOM_RC3, st, g, 60).wait()
+
+        t0 = time.perf_counter()
+        with cf.ThreadPoolExecutor(args.serve_threads) as ex:
+            list(ex.map(run, range(args.serve_threads)))
+        wall = time.perf_counter() - t0
+        stats = P.cbdfs_server_get_stats(ctx)
+        P.cbdfs_server_stop(ctx)
+        stats["wall_states_per_s"] = stats["states"] / wall
+        stats["threads"] = args.serve_threads
+        stats["workload"] = "15-puzzle 81-class and cube 21-class BF16 networks, request sizes log-uniform 32..4096"
+        return stats
+    finally:
+        P.cbdfs_destroy(ctx)
+
+
+def fp8_scales(P, ctx, Ws, bs):
+    """Static activation scales for E4M3 (an input of cbdfs_net_load): the largest activation
+    of each hidden layer over 4096 calibration states, from a float32 host forward of the
+    given weights, divided by 448.  Calibration only; nothing timed runs on the host."""
+    import numpy as np
+    X = np.zeros((4096, 256), np.float32)
+    st = W.random_stp_states(4, 4096, 4096)
+    for p in range(16):
+        t = ((st >> np.uint64(4 * p)) & np.uint64(15)).astype(np.int64)
+        X[np.arange(4096), t * 16 + p] = 1.0
+    a = X
+    sc = []
+    for l in range(len(Ws) - 1):
+        a = np.maximum(a @ Ws[l].T + bs[l], 0.0)
+        sc.append(max(float(a.max()), 1e-6) / 448.0)
+    return np.array(sc, np.float32)
 
 
 def run_ours(args):
@@ -232,6 +366,8 @@ def run_ours(args):
     Ws, bs = W.net_weights(**W.NET_C1)
     hid = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, P.PREC_BF16, P.HEAD_REGRESSION, 1)
     hid32 = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, P.PREC_FP32, P.HEAD_REGRESSION, 1)
+    act8 = fp8_scales(P, ctx, Ws, bs)
+    hid8 = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, P.PREC_FP8, P.HEAD_REGRESSION, 1, act_scales=act8)
     states = W.random_stp_states(4, B, W.seed_for(W.TAG_C1, 1_000_000 + rank))
     g = (W.splitmix64_array(W.seed_for(W.TAG_C1, 2_000_000 + rank), B) % np.uint64(60)).astype(np.uint8)
     ds = torch.from_numpy(states.view(np.int64)).to(dev)
@@ -358,9 +494,17 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate(args.cpu_seconds)
+    # FP8 form of the same workload (fused chain, E4M3)
+    gr8 = graph_of(hid8, 3)
+    ms8 = timed(gr8, K32)
+    line["fp8_states_per_s"] = B * K32 / (ms8 / 1e3)
     if rank == 0 and not args.no_search:
-        line["search"] = search_rates(P, ctx, hid, hid32, args.search_seconds)
+        line["search"] = search_rates(P, ctx, {"bf16": hid, "fp8": hid8, "fp32": hid32}, args.search_seconds)
     P.cbdfs_destroy(ctx)
+    if rank == 0 and not args.no_train:
+        line["train"] = train_leg(P, args)
+    if rank == 0 and not args.no_serve:
+        line["serve"] = serve_leg(P, args)
     if rank == 0:
         print(json.dumps(line))
     if dist:
@@ -375,8 +519,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
     ap.add_argument("--no-search", action="store_true", help="skip the IDA* nodes/s leg")
+    ap.add_argument("--no-train", action="store_true", help="skip the training leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--search-seconds", type=float, default=3.0)
+    ap.add_argument("--train-states", type=int, default=10_000_000)
+    ap.add_argument("--train-epochs", type=int, default=5)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-threads", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
