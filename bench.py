@@ -93,15 +93,15 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def kernel_traffic(key):
-    """DRAM bytes per launch of the fused chain kernel from the committed ncu summary, if the
-    kernel source is the one the counters were taken on; else None."""
-    path = os.path.join(ROOT, "profiles", "chain_c1_bf16_b8192.md")
+def kernel_traffic(key, summary="chain_c1_bf16_b8192.md", sources=("mlp_chain.cu", "common.cuh")):
+    """DRAM bytes per launch of a kernel from its committed ncu summary, if the kernel source
+    is the one the counters were taken on; else None."""
+    path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     h = hashlib.sha256()
-    for f in ("mlp_chain.cu", "common.cuh"):
+    for f in sources:
         h.update(open(os.path.join(ROOT, "paper_2507_11916_b300", "csrc", f), "rb").read())
     want = {}
     for line in txt.splitlines():
@@ -190,29 +190,55 @@ def run_reference(args):
         "e2e": {"value": v, "unit": "states/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
-def search_rates(P, ctx, hids, seconds):
-    """IDA* nodes/s with the network heuristic (h = max(rint(y), 0, MD)) in each precision at
-    equal solution cost, and the serial oracle's nodes/s with MD on the same starts."""
-    out = {}
-    starts = [P.cbdfs_apply_moves(P.DOM_STP4, W.stp_goal(4), W.stp_walk(4, 60, W.seed_for(W.TAG_C1, i)))
+def search_rates(P, ctx, hids, seconds, work_num=256):
+    """IDA* nodes/s with the network heuristic in each precision at equal solution cost.
+
+    fixed_tree: Manhattan distance prunes and the network is evaluated on every generated node
+    (the paper's fixed-tree evaluation), so every precision searches the same tree: equal
+    costs and equal per-iteration node counts by construction, nodes/s compares the
+    evaluation path.  network_pruned: h = max(rint(y), 0, MD) prunes (trees may differ where
+    the precision moves an h across an integer).  Also the serial oracle's nodes/s with MD."""
+    starts = [P.cbdfs_apply_moves(P.DOM_STP4, W.stp_goal(4), W.stp_walk(4, 50, W.seed_for(W.TAG_C1, i)))
               for i in range(4)]
     threads = min(32, os.cpu_count() or 4)
-    for name, hid in hids.items():
-        costs, exp, gen, secs, nb, ev = [], 0, 0, 0.0, 0, 0
+    out = {"instances": "4 seeded 50-move 15-puzzle walks", "threads": threads, "work_num": work_num,
+           "batch": 8192, "timeout_us": 500}
+
+    def run(hid, fixed):
+        costs, iters, exp, gen, secs, nb, ev = [], [], 0, 0, 0.0, 0, 0
         for s in starts:
             r = P.cbdfs_solve(ctx, P.DOM_STP4, s, P.ALGO_IDA, hid, partial_ok=True, threads=threads,
-                              work_num=64, batch=8192, timeout_us=500, time_limit_s=seconds)
-            costs.append(r["cost"] if r["status"] == 0 else None)
+                              work_num=work_num, batch=8192, timeout_us=500, time_limit_s=seconds,
+                              fixed_tree_heur=P.HEUR_MD if fixed else P.HEUR_NONE)
+            ok = r["status"] == 0
+            costs.append(r["cost"] if ok else None)
+            iters.append([tuple(it) for it in (r["iters"] if ok else r["iters"][:-1])])
             exp += r["expanded"]
             gen += r["generated"]
             secs += r["seconds"]
             nb += r["batches"]
             ev += r["evaluated"]
-        out[name] = {"costs": costs, "expanded_per_s": exp / secs, "generated_per_s": gen / secs,
-                     "avg_batch": ev / max(nb, 1), "seconds": secs, "threads": threads}
-    costs = [v["costs"] for v in out.values()]
-    out["equal_cost"] = all(c == costs[0] for c in costs)
-    out["instances"] = "4 seeded 60-move 15-puzzle walks, h = max(rint(y), 0, MD)"
+        return {"costs": costs, "expanded_per_s": exp / secs, "generated_per_s": gen / secs,
+                "avg_batch": ev / max(nb, 1), "seconds": secs}, iters
+
+    for mode in ("fixed_tree", "network_pruned"):
+        res, its = {}, {}
+        for name, hid in hids.items():
+            res[name], its[name] = run(hid, mode == "fixed_tree")
+        names = list(hids)
+        solved = [i for i in range(len(starts)) if all(res[n]["costs"][i] is not None for n in names)]
+        res["equal_cost"] = all(res[n]["costs"][i] == res[names[0]]["costs"][i] for n in names for i in solved)
+        res["instances_solved_by_all"] = len(solved)
+        if mode == "fixed_tree":
+            # per completed iteration (bound, expanded, generated) agree across precisions
+            res["equal_counts"] = all(
+                its[n][i][:m] == its[names[0]][i][:m]
+                for i in range(len(starts)) for n in names
+                for m in [min(len(its[n][i]), len(its[names[0]][i]))])
+        for n in names:
+            if n != "fp32" and res["fp32"]["expanded_per_s"] > 0:
+                res[f"{n}_over_fp32_nodes"] = res[n]["expanded_per_s"] / res["fp32"]["expanded_per_s"]
+        out[mode] = res
     try:
         import oracle
         t0 = time.perf_counter()
@@ -330,6 +356,68 @@ def serve_leg(P, args):
         P.cbdfs_destroy(ctx)
 
 
+def pdb_leg(P, args):
+    """The additive-PDB gather (the plain heuristic and fallback): the paper's 7-8 partition of
+    the 15-puzzle built on the device (57.7M + 518.9M one-byte entries, HBM-resident) and the
+    6-6-3 partition (11.5 MB, L2-resident), each over a batch of uniformly random states with
+    the bound test; the L2 is flushed before every timed launch."""
+    import torch
+    n = args.pdb_states
+    out = {"states_per_launch": n, "inputs": "seeded uniformly random solvable 15-puzzle states, g uniform in 0..59"}
+    ctx = P.cbdfs_create(0, max_batch=n, n_slots=1)
+    try:
+        dev = torch.device("cuda", 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hid78 = P.cbdfs_pdb_load(ctx, P.DOM_STP4, W.PATTERNS_78)  # no tables: built on the device
+        out["build_7_8_s"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        hid663 = P.cbdfs_pdb_load(ctx, P.DOM_STP4, W.PATTERNS_663)
+        out["build_6_6_3_s"] = time.perf_counter() - t0
+        states = W.random_stp_states(4, n, W.seed_for(W.TAG_C1, 3_000_000))
+        g = (W.splitmix64_array(W.seed_for(W.TAG_C1, 3_000_001), n) % np.uint64(60)).astype(np.uint8)
+        ds = torch.from_numpy(states.view(np.int64)).to(dev)
+        dg = torch.from_numpy(g).to(dev)
+        dh = torch.empty(n, dtype=torch.uint8, device=dev)
+        dm = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
+        dmin = torch.empty(1, dtype=torch.int32, device=dev)
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+        stream = torch.cuda.Stream(dev)
+        pk = peaks()
+        K = max(20, min(args.steps, 200))
+        for name, hid, npat, mb in (("7-8", hid78, 2, 576.6), ("6-6-3", hid663, 3, 11.5)):
+            ms = []
+            for k in range(3 + K):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                t = P.cbdfs_eval_profile(ctx, hid, P.DOM_STP4, ds, dg, BOUND, n, dh, dm, dmin, stream=stream)
+                if k >= 3:
+                    ms.append(t[0])
+            t = float(np.mean(ms))
+            # bytes a launch must move: the state (8), g (1), h (1), the mask bit, and per
+            # pattern one table byte -- which from DRAM is one 32-byte sector per lookup
+            alg = 8 + 1 + 1 + 1 / 8 + npat
+            sector = 8 + 1 + 1 + 1 / 8 + 32 * npat
+            rate = n / (t / 1e3)
+            out[name] = {"tables_mb": mb, "launch_ms": t, "states_per_s": rate,
+                         "algorithmic_bytes_per_state": alg, "sector_bytes_per_state": sector,
+                         "achieved_gbs_sectors": rate * sector / 1e9,
+                         "frac_of_hbm_sectors": rate * sector / 1e9 / pk["hbm"],
+                         "achieved_gbs_algorithmic": rate * alg / 1e9}
+        out["hbm_peak_gbs"] = pk["hbm"]
+        out["peak_source"] = f"{pk['src']} HBM copy"
+        out["traffic_per_launch"] = kernel_traffic("pdb78", "pdb_gather_7_8_b4m.md", ("pdb.cu", "common.cuh"))
+        # the 7-8 sum dominates Manhattan distance on every state of the batch
+        h = dh.cpu().numpy()  # last launch: the 6-6-3 heuristic
+        h78 = P.heur_submit_batch(ctx, hid78, P.DOM_STP4, states[:65536], g[:65536], BOUND)[0]
+        md = P.heur_submit_batch(ctx, P.HEUR_MD, P.DOM_STP4, states[:65536], g[:65536], BOUND)[0].astype(int)
+        assert (h78.astype(int) >= md).all() and (h[:65536].astype(int) >= md).all()
+        assert P.cbdfs_device_status(ctx) == 0
+    finally:
+        P.cbdfs_destroy(ctx)
+    return out
+
+
 def fp8_scales(P, ctx, Ws, bs):
     """Static activation scales for E4M3 (an input of cbdfs_net_load): the largest activation
     of each hidden layer over 4096 calibration states, from a float32 host forward of the
@@ -362,7 +450,7 @@ def run_ours(args):
     import paper_2507_11916_b300 as P
 
     B = BATCH
-    ctx = P.cbdfs_create(local, max_batch=B, n_slots=2)
+    ctx = P.cbdfs_create(local, max_batch=B, n_slots=4)
     Ws, bs = W.net_weights(**W.NET_C1)
     hid = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, P.PREC_BF16, P.HEAD_REGRESSION, 1)
     hid32 = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, P.PREC_FP32, P.HEAD_REGRESSION, 1)
@@ -501,6 +589,8 @@ def run_ours(args):
     if rank == 0 and not args.no_search:
         line["search"] = search_rates(P, ctx, {"bf16": hid, "fp8": hid8, "fp32": hid32}, args.search_seconds)
     P.cbdfs_destroy(ctx)
+    if rank == 0 and not args.no_pdb:
+        line["pdb_gather"] = pdb_leg(P, args)
     if rank == 0 and not args.no_train:
         line["train"] = train_leg(P, args)
     if rank == 0 and not args.no_serve:
@@ -521,6 +611,8 @@ def main():
     ap.add_argument("--no-search", action="store_true", help="skip the IDA* nodes/s leg")
     ap.add_argument("--no-train", action="store_true", help="skip the training leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-pdb", action="store_true", help="skip the PDB gather leg")
+    ap.add_argument("--pdb-states", type=int, default=1 << 22)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--search-seconds", type=float, default=3.0)
     ap.add_argument("--train-states", type=int, default=10_000_000)

@@ -89,6 +89,9 @@ def lib():
         L.or_pdb_rank.restype = ctypes.c_int64
         L.or_pdb_build.argtypes = [ctypes.c_int, ip, ctypes.c_int, ctypes.c_void_p]
         L.or_pdb_build.restype = ctypes.c_int64
+        L.or_pdb_ball.argtypes = [ctypes.c_int, ip, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                  ctypes.c_void_p, ctypes.c_void_p]
+        L.or_pdb_ball.restype = ctypes.c_int64
         L.or_pdb_h.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ip, ip,
                                ctypes.c_void_p]
         L.or_cbdfs.argtypes = [ctypes.c_int, u64p, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
@@ -198,6 +201,18 @@ def pdb_build(side: int, tiles) -> np.ndarray:
     if r < 0:
         raise MemoryError("pdb_build")
     return table
+
+
+def pdb_ball(side: int, tiles, maxd: int, cap: int = 1 << 24):
+    """(ranks, values) of every placement of the pattern within distance maxd of the goal,
+    from the same search as pdb_build stopped after level maxd: the entries of the full
+    table that are <= maxd, without building the table."""
+    ranks = np.empty(cap, dtype=np.int64)
+    vals = np.empty(cap, dtype=np.uint8)
+    m = lib().or_pdb_ball(side, _ints(tiles), len(tiles), maxd, cap, ranks.ctypes.data, vals.ctypes.data)
+    if m < 0:
+        raise MemoryError("pdb_ball: more than cap states within the distance")
+    return ranks[:m].copy(), vals[:m].copy()
 
 
 class PDB:

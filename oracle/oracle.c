@@ -471,6 +471,118 @@ int64_t or_pdb_build(int side, const int *tiles, int k, uint8_t *table) {
     return reached;
 }
 
+/* The part of a pattern database within distance maxd of the goal, found by the same
+ * cost-level search as or_pdb_build but stopped after level maxd and kept in a hash set, so
+ * that it can check tables far too large to build here.  Writes every placement whose
+ * least distance over blank cells is <= maxd (rank, value) into out_rank/out_val, sorted
+ * by rank; returns how many, or -1 if more than cap (rank, blank) states were reached. */
+typedef struct { int64_t *a; int64_t n, cap; } lvec;
+static void lvec_push(lvec *v, int64_t x) {
+    if (v->n == v->cap) {
+        v->cap = v->cap ? v->cap * 2 : 1024;
+        v->a = (int64_t *)realloc(v->a, sizeof(int64_t) * v->cap);
+    }
+    v->a[v->n++] = x;
+}
+
+typedef struct { uint64_t *key; uint8_t *val; uint64_t mask; int64_t used; } hset;
+static uint8_t *hset_slot(hset *h, uint64_t key, int *fresh) {
+    uint64_t i = (key * 0x9E3779B97F4A7C15ull) >> 20 & h->mask;
+    while (h->key[i] && h->key[i] != key + 1) i = (i + 1) & h->mask;
+    *fresh = h->key[i] == 0;
+    if (*fresh) { h->key[i] = key + 1; h->val[i] = 255; h->used++; }
+    return &h->val[i];
+}
+
+static int cmp_pair(const void *x, const void *y) {
+    const int64_t a = *(const int64_t *)x, b = *(const int64_t *)y;
+    return (a > b) - (a < b);
+}
+
+int64_t or_pdb_ball(int side, const int *tiles, int k, int maxd, int64_t cap, int64_t *out_rank,
+                    uint8_t *out_val) {
+    const int n = side * side;
+    uint64_t size = 1;
+    while (size < (uint64_t)cap * 2) size <<= 1;
+    hset h = {(uint64_t *)calloc(size, 8), (uint8_t *)malloc(size), size - 1, 0};
+    if (!h.key || !h.val) return -1;
+    int pos[16], fresh;
+    for (int i = 0; i < k; ++i) pos[i] = tiles[i];
+    const int64_t start = or_pdb_rank(pos, k, n) * n + 0;
+    *hset_slot(&h, (uint64_t)start, &fresh) = 0;
+    lvec cur = {0}, nxt = {0};
+    lvec_push(&cur, start);
+    static const int DR[4] = {-1, 0, 0, 1}, DC[4] = {0, -1, 1, 0};
+    int64_t result = 0;
+    for (int d = 0; d <= maxd && cur.n > 0 && result >= 0; ++d) {
+        for (int64_t qi = 0; qi < cur.n; ++qi) {
+            const int64_t u = cur.a[qi];
+            if (*hset_slot(&h, (uint64_t)u, &fresh) != d) continue;  /* stale entry */
+            const int64_t r = u / n;
+            const int b = (int)(u % n);
+            pdb_unrank(r, k, n, pos);
+            for (int m = 0; m < 4; ++m) {
+                int nr = b / side + DR[m], nc = b % side + DC[m];
+                if (nr < 0 || nr >= side || nc < 0 || nc >= side) continue;
+                int c = nr * side + nc, who = -1;
+                for (int i = 0; i < k; ++i)
+                    if (pos[i] == c) who = i;
+                int64_t v;
+                int cost;
+                if (who < 0) {
+                    v = r * n + c;
+                    cost = 0;
+                } else {
+                    pos[who] = b;
+                    v = or_pdb_rank(pos, k, n) * n + c;
+                    pos[who] = c;
+                    cost = 1;
+                }
+                const int nd = d + cost;
+                if (nd > maxd) continue;
+                uint8_t *dv = hset_slot(&h, (uint64_t)v, &fresh);
+                if (h.used > cap) { result = -1; break; }
+                if (*dv > nd) {
+                    *dv = (uint8_t)nd;
+                    lvec_push(cost == 0 ? &cur : &nxt, v);
+                }
+            }
+            if (result < 0) break;
+        }
+        lvec t = cur;
+        cur = nxt;
+        nxt = t;
+        nxt.n = 0;
+    }
+    if (result == 0) {
+        /* least value over blank cells per placement: sort (rank, value) pairs */
+        int64_t *pairs = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)(h.used ? h.used : 1));
+        int64_t m = 0;
+        for (uint64_t i = 0; i <= h.mask; ++i)
+            if (h.key[i]) {
+                pairs[2 * m] = (int64_t)(h.key[i] - 1) / n;
+                pairs[2 * m + 1] = h.val[i];
+                ++m;
+            }
+        qsort(pairs, (size_t)m, 2 * sizeof(int64_t), cmp_pair);
+        for (int64_t i = 0; i < m; ++i) {
+            if (result > 0 && out_rank[result - 1] == pairs[2 * i]) {
+                if (pairs[2 * i + 1] < out_val[result - 1]) out_val[result - 1] = (uint8_t)pairs[2 * i + 1];
+                continue;
+            }
+            out_rank[result] = pairs[2 * i];
+            out_val[result] = (uint8_t)pairs[2 * i + 1];
+            ++result;
+        }
+        free(pairs);
+    }
+    free(cur.a);
+    free(nxt.a);
+    free(h.key);
+    free(h.val);
+    return result;
+}
+
 /* Additive PDB value of an STP state: sum over patterns of table[rank(pattern positions)]. */
 int or_pdb_h(uint64_t s, int side, int npat, const int *k, const int *tiles,
              const uint8_t *const *tables) {

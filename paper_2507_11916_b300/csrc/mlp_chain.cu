@@ -9,10 +9,15 @@
 // earlier tiles of the sequence, and all CTAs are resident, so the earliest unfinished tile
 // can always proceed.  Activations of a row block stay in L2 between layers.
 //
+// Before the tiles, every warp of the grid decodes packed states into the one-hot input rows
+// (units of 8 rows, one coalesced state load per unit, 16-byte coalesced stores, every chunk
+// computed branch-free) and counts finished units per row block, so that layer 0 waits only
+// for its own 128 rows.
+//
 // Per CTA (192 threads):
-//   warp 0      producer: for layer 0 the whole warp writes the one-hot A k-block (decoded
-//               from the packed states) into the stage in the 128-byte swizzled layout; for
-//               later layers TMA loads the activation k-block; TMA loads the weight k-block
+//   warp 0      producer: TMA loads the A k-block (the one-hot rows for layer 0, the stored
+//               activations of layer l-1 otherwise) and the weight k-block into a 4-stage
+//               ring, once the rows it reads are published
 //   warp 1      owns 512 TMEM columns (two 256-column FP32 accumulators); one lane issues
 //               tcgen05.mma and commits stages back to the producer and finished
 //               accumulators to the epilogue, so one tile's epilogue overlaps the next main loop
@@ -124,76 +129,60 @@ __device__ __forceinline__ Tile tile_of(const ChainParams &P, int t) {
     return Tile{l, local / P.nt[l], local % P.nt[l]};
 }
 
-// One row of the one-hot input, written by one warp as coalesced 16-byte chunks: lane i
-// writes chunks i, i+32, ...  Chunk k holds elements [k*E, k*E+E) (E = 8 BF16 or 16 E4M3).
-template <int DOMAIN, bool FP8>
-__device__ __forceinline__ void onehot_row(const ChainParams &P, uint32_t row, int lane, uint64_t w0,
-                                           uint64_t w1) {
-    constexpr int E = FP8 ? 16 : 8;
-    const int nchunk = P.kdim[0] / E;
-    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(P.onehot) + (size_t)row * P.kdim[0] * (FP8 ? 1 : 2));
-    const bool live = row < P.n;
-    for (int k = lane; k < nchunk; k += 32) {
-        // four scalar words (a runtime-indexed array would live in local memory)
-        uint32_t v0 = 0, v1 = 0, v2 = 0, v3 = 0;
-        auto set = [&](int e) {  // element e of the chunk is 1
-            const uint32_t bits = FP8 ? (0x38u << (8 * (e & 3))) : (0x3F80u << (16 * (e & 1)));
-            const int wi = FP8 ? (e >> 2) : (e >> 1);
-            v0 |= wi == 0 ? bits : 0u;
-            v1 |= wi == 1 ? bits : 0u;
-            v2 |= wi == 2 ? bits : 0u;
-            v3 |= wi == 3 ? bits : 0u;
-        };
-        if (live) {
-            if (DOMAIN == CBDFS_DOM_STP4 && !FP8) {
-                // chunk k: tile k/2, cells (k%2)*8 .. +7
-                const uint32_t t = k >> 1;
-                int cell = 0;
+// The one-hot encoding (the network's input): slot j of the state (STP: tile j, whose value
+// is its cell; cube: cubie j, corners then edges, whose value is pos*k + ori in 0..23) sets
+// element j * W + value, W = cells (STP) or 24 (cube).
+template <int DOMAIN>
+struct OneHot {
+    static constexpr int W = DOMAIN == CBDFS_DOM_RC3 ? 24 : (DOMAIN == CBDFS_DOM_STP3 ? 9 : 16);
+    static constexpr int slots = DOMAIN == CBDFS_DOM_RC3 ? 20 : W;
+    // the per-row words: STP the inverse permutation (nibble j = cell of tile j), cube the
+    // two packed words
+    __device__ __forceinline__ static void prepare(uint64_t s0, uint64_t s1, uint64_t &a, uint64_t &b) {
+        if (DOMAIN == CBDFS_DOM_RC3) {
+            a = s0;
+            b = s1;
+        } else {
+            uint64_t where = 0;
 #pragma unroll
-                for (int p = 0; p < 16; ++p) cell = (((w0 >> (4 * p)) & 15u) == t) ? p : cell;
-                const int e = cell - (k & 1) * 8;
-                if (e >= 0 && e < 8) set(e);
-            } else if (DOMAIN == CBDFS_DOM_STP4 && FP8) {
-                // chunk k: tile k, cells 0..15
-                int cell = 0;
-#pragma unroll
-                for (int p = 0; p < 16; ++p) cell = (((w0 >> (4 * p)) & 15u) == (uint32_t)k) ? p : cell;
-                set(cell);
-            } else if (DOMAIN == CBDFS_DOM_RC3 && !FP8) {
-                // chunks 0..23: corner k/3; chunks 24..59: edge (k-24)/3; each cubie spans 3 chunks
-                if (k < 60) {
-                    const int cub = k < 24 ? k / 3 : (k - 24) / 3;
-                    const int sub = k < 24 ? k % 3 : (k - 24) % 3;
-                    const int f = (int)(((k < 24 ? w0 : w1) >> (5 * cub)) & 31u);
-                    const int e = f - sub * 8;
-                    if (e >= 0 && e < 8) set(e);
-                }
-            } else {
-                // general form: test every one-hot index against the chunk
-                const int lo = k * E;
-                if (DOMAIN == CBDFS_DOM_RC3) {
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const int j = c * 24 + (int)((w0 >> (5 * c)) & 31u) - lo;
-                        if (j >= 0 && j < E) set(j);
-                    }
-#pragma unroll
-                    for (int c = 0; c < 12; ++c) {
-                        const int j = 192 + c * 24 + (int)((w1 >> (5 * c)) & 31u) - lo;
-                        if (j >= 0 && j < E) set(j);
-                    }
-                } else {
-                    constexpr int N = DOMAIN == CBDFS_DOM_STP3 ? 9 : 16;
-#pragma unroll
-                    for (int p = 0; p < N; ++p) {
-                        const int j = (int)((w0 >> (4 * p)) & 15u) * N + p - lo;
-                        if (j >= 0 && j < E) set(j);
-                    }
-                }
-            }
+            for (int p = 0; p < W; ++p) where |= (uint64_t)p << (4 * ((s0 >> (4 * p)) & 15u));
+            a = where;
+            b = 0;
         }
-        dst[k] = make_uint4(v0, v1, v2, v3);
     }
+    // the value of slot j (0 for j >= slots, where no shift may reach 64 bits)
+    __device__ __forceinline__ static int value(uint64_t a, uint64_t b, int j) {
+        if (DOMAIN == CBDFS_DOM_RC3)
+            return j < 8 ? (int)((a >> (5 * j)) & 31u) : j < 20 ? (int)((b >> (5 * (j - 8))) & 31u) : 0;
+        return j < 16 ? (int)((a >> (4 * j)) & 15u) : 0;
+    }
+};
+
+// 16-byte chunk k of a row's one-hot encoding (elements k*E .. k*E+E-1, E = 8 BF16 or 16
+// E4M3): the ones of the slots whose columns the chunk covers.  Branch-free: a lane-dependent
+// branch per chunk would cost a reconvergence each.
+template <int DOMAIN, bool FP8>
+__device__ __forceinline__ uint4 onehot_chunk(uint64_t a, uint64_t b, bool live, int k) {
+    using OH = OneHot<DOMAIN>;
+    constexpr int E = FP8 ? 16 : 8;
+    constexpr int NS = OH::W % E == 0 ? 1 : (E + OH::W - 1) / OH::W + 1;  // slots a chunk can meet
+    constexpr uint32_t ONE = FP8 ? 0x38u : 0x3F80u;                       // E4M3 / BF16 1.0
+    const int e0 = k * E;
+    const int s0 = e0 / OH::W;
+    uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+#pragma unroll
+    for (int kk = 0; kk < NS; ++kk) {
+        const int sl = s0 + kk;
+        const int e = sl * OH::W + OH::value(a, b, sl) - e0;
+        const bool in = live && sl < OH::slots && (unsigned)e < (unsigned)E;
+        const int wi = FP8 ? (e >> 2) : (e >> 1);
+        const uint32_t bits = in ? (FP8 ? (ONE << (8 * (e & 3))) : (ONE << (16 * (e & 1)))) : 0u;
+        w0 |= wi == 0 ? bits : 0u;
+        w1 |= wi == 1 ? bits : 0u;
+        w2 |= wi == 2 ? bits : 0u;
+        w3 |= wi == 3 ? bits : 0u;
+    }
+    return make_uint4(w0, w1, w2, w3);
 }
 
 template <int DOMAIN, int CMAX>
@@ -289,6 +278,44 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
     const uint32_t tmem = *tmem_slot;
     constexpr int KBLK = FP8 ? 128 : 64;
 
+    {
+        // one-hot pre-pass by every warp of the grid: unit v = rows [8v, 8v+8) goes to warp
+        // v mod (warps in the grid); a row block counts its 16 units
+        constexpr int EB = FP8 ? 1 : 2;
+        constexpr int nwarps = kChainThreads / 32;
+        const int units = P.mblocks * (kBM / 8);
+        const int nchunk = P.kdim[0] * EB / 16;
+        for (int v = blockIdx.x * nwarps + warp; v < units; v += gridDim.x * nwarps) {
+            const uint32_t my = v * 8 + (lane & 7);
+            uint64_t s0 = 0, s1 = 0;
+            const bool lv = lane < 8 && my < P.n;
+            if (lv) {
+                if (DOMAIN == CBDFS_DOM_RC3) {
+                    const ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2 *>(P.states) + my);
+                    s0 = w.x;
+                    s1 = w.y;
+                } else {
+                    s0 = __ldg(P.states + my);
+                }
+            }
+            uint64_t wa, wb;
+            OneHot<DOMAIN>::prepare(s0, s1, wa, wb);
+#pragma unroll 1
+            for (int r = 0; r < 8; ++r) {
+                const uint64_t ar = __shfl_sync(0xFFFFFFFFu, wa, r);
+                const uint64_t br = DOMAIN == CBDFS_DOM_RC3 ? __shfl_sync(0xFFFFFFFFu, wb, r) : 0ull;
+                const bool lr = __shfl_sync(0xFFFFFFFFu, lv, r);
+                uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(P.onehot) +
+                                                       (size_t)(v * 8 + r) * P.kdim[0] * EB);
+                for (int k = lane; k < nchunk; k += 32) dst[k] = onehot_chunk<DOMAIN, FP8>(ar, br, lr, k);
+            }
+            fence_proxy_async_global();  // the rows are read by TMA (the async proxy)
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) atomicAdd(P.counters + v / (kBM / 8), 1);
+        }
+    }
+
     if (warp == 0) {
         // ------------------------------------------------------------- producer
         uint32_t it = 0, pi = 0;
@@ -375,34 +402,6 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
         const int q = warp & 3;
         const int row = q * 32 + lane;
         const int ep_tid = threadIdx.x - 64;
-        // one-hot pre-pass, spread over every epilogue warp of the grid in units of 8 rows:
-        // unit v = rows [8v, 8v+8) goes to warp v mod (4 * grid); each row block counts its
-        // 16 units
-        {
-            const int units = P.mblocks * (kBM / 8);
-            const int gw = blockIdx.x * 4 + q, nw = gridDim.x * 4;
-            for (int v = gw; v < units; v += nw) {
-                const uint32_t my = v * 8 + (lane & 7);
-                uint64_t s0 = 0, s1 = 0;
-                if (lane < 8 && my < P.n) {
-                    if (DOMAIN == CBDFS_DOM_RC3) {
-                        const ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2 *>(P.states) + my);
-                        s0 = w.x;
-                        s1 = w.y;
-                    } else {
-                        s0 = __ldg(P.states + my);
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < 8; ++r)
-                    onehot_row<DOMAIN, FP8>(P, v * 8 + r, lane, __shfl_sync(0xFFFFFFFFu, s0, r),
-                                            DOMAIN == CBDFS_DOM_RC3 ? __shfl_sync(0xFFFFFFFFu, s1, r) : 0ull);
-                fence_proxy_async_global();
-                __threadfence();
-                __syncwarp();
-                if (lane == 0) atomicAdd(P.counters + v / (kBM / 8), 1);
-            }
-        }
         uint32_t i = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
             const Tile T = tile_of(P, t);

@@ -38,30 +38,35 @@ k_pdb_gather(const uint64_t *__restrict__ states, uint32_t n, const PdbParams P,
              const uint8_t *__restrict__ g, uint32_t bound, uint8_t *__restrict__ h_out,
              uint32_t *__restrict__ mask, uint32_t *__restrict__ minf) {
     constexpr int N = SIDE * SIDE;
+    __shared__ uint32_t warp_min[8];
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool valid = i < n;
     uint64_t goal = 0;
 #pragma unroll
     for (int t = 0; t < N; ++t) goal |= (uint64_t)t << (4 * t);
     const uint64_t s = valid ? __ldg(states + i) : goal;
+    const uint32_t gi = valid ? (uint32_t)__ldg(g + i) : 0u;
     uint64_t where = 0;
 #pragma unroll
     for (int p = 0; p < N; ++p) where |= (uint64_t)p << (4 * ((s >> (4 * p)) & 15u));
+    // Both loops are unrolled to their maxima so that every PdbParams field is read at a
+    // constant offset (an instruction operand), never by a dynamic index into the
+    // parameter bank; the pattern sizes are the same for all threads, so the guards are
+    // uniform branches.
     uint32_t rank[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        rank[q] = 0;
-        if (q < P.n_patterns) {
-            uint32_t seen = 0, r = 0;
-            for (int j = 0; j < P.k[q]; ++j) {
+        uint32_t seen = 0, r = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (q < P.n_patterns && j < P.k[q]) {
                 const uint32_t c = (uint32_t)(where >> (4 * P.tiles[q][j])) & 15u;
-                const uint32_t d = c - __popc(seen & ((1u << c) - 1u));
-                r += d * P.weight[q][j];
+                r += (c - __popc(seen & ((1u << c) - 1u))) * P.weight[q][j];
                 seen |= 1u << c;
             }
-            rank[q] = r;
         }
+        rank[q] = r;
     }
     uint32_t v[4];
 #pragma unroll
@@ -72,14 +77,20 @@ k_pdb_gather(const uint64_t *__restrict__ states, uint32_t n, const PdbParams P,
     bool pass = false;
     if (valid) {
         h_out[i] = (uint8_t)hv;
-        f = (uint32_t)__ldg(g + i) + hv;
+        f = gi + hv;
         pass = f <= bound;
     }
     const uint32_t bits = __ballot_sync(0xFFFFFFFFu, pass);
     const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, pass ? 0xFFFFFFFFu : f);
-    if (lane == 0 && i < n) {
-        mask[i >> 5] = bits;
-        if (mn != 0xFFFFFFFFu) atomicMin(minf, mn);
+    if (lane == 0) {
+        if (i < n) mask[i >> 5] = bits;
+        warp_min[warp] = mn;
+    }
+    // one atomic per block for the least f above the bound
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t m = __reduce_min_sync(0xFFFFFFFFu, lane < (int)(blockDim.x >> 5) ? warp_min[lane] : 0xFFFFFFFFu);
+        if (lane == 0 && m != 0xFFFFFFFFu) atomicMin(minf, m);
     }
 }
 

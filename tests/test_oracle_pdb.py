@@ -61,3 +61,16 @@ def test_663_six_tile_table_shape(orc):
     assert tab.shape == (5765760,)
     assert (tab < 255).all() and tab[orc.pdb_rank([1, 2, 3, 5, 6, 7], 16)] == 0
     assert tab.max() <= 80
+
+
+@pytest.mark.parametrize("side,tiles,maxd", [(3, [1, 2, 3, 4], 40), (3, [5, 6, 7, 8], 5),
+                                             (4, [10, 11, 15], 6), (4, [4, 8, 12, 13], 7),
+                                             (4, [1, 2, 4, 5], 4)])
+def test_pdb_ball_is_the_table_near_the_goal(orc, side, tiles, maxd):
+    # the search stopped after level maxd finds exactly the entries <= maxd of the full table
+    # (at maxd 40 the whole 8-puzzle table)
+    T = orc.pdb_build(side, tiles)
+    ranks, vals = orc.pdb_ball(side, tiles, maxd, cap=1 << 22)
+    idx = np.nonzero(T <= maxd)[0]
+    assert np.array_equal(ranks, idx)
+    assert np.array_equal(vals, T[idx])

@@ -149,16 +149,19 @@ def random_stp_states(side: int, n: int, seed: int) -> np.ndarray:
     keys = splitmix64_array(seed, n * ncell).reshape(n, ncell)
     perm = np.argsort(keys, axis=1, kind="stable").astype(np.int64)  # perm[:, p] = tile at p
     # parity of the permutation (blank included as tile 0) by counting inversions
+    p8 = perm.astype(np.int8)
     inv = np.zeros(n, dtype=np.int64)
     for i in range(ncell):
-        inv += (perm[:, i:i + 1] > perm[:, i + 1:]).sum(axis=1)
+        inv += np.count_nonzero(p8[:, i:i + 1] > p8[:, i + 1:], axis=1)
     blank = np.argmax(perm == 0, axis=1)
     taxi = blank // side + blank % side  # blank's distance to its goal cell 0
     bad = (inv & 1) != (taxi & 1)
-    # swap the two non-blank tiles in the first two cells that do not hold the blank
-    for row in np.nonzero(bad)[0]:
-        idx = [p for p in range(ncell) if perm[row, p] != 0][:2]
-        perm[row, idx[0]], perm[row, idx[1]] = perm[row, idx[1]], perm[row, idx[0]]
+    # swap the tiles in the first two cells that do not hold the blank
+    rows = np.nonzero(bad)[0]
+    first = np.where(blank[rows] == 0, 1, 0)
+    second = np.where(blank[rows] <= 1, 2, 1)
+    a, b = perm[rows, first].copy(), perm[rows, second].copy()
+    perm[rows, first], perm[rows, second] = b, a
     shifts = (4 * np.arange(ncell, dtype=np.uint64))
     return (perm.astype(np.uint64) << shifts).sum(axis=1, dtype=np.uint64)
 
@@ -270,3 +273,9 @@ NET_C3 = dict(dims=[256, 1024, 1024, 512, 81], init="kaiming", seed=3)
 
 # instance tags (seed_for(tag, i) gives instance i's seed)
 TAG_C0, TAG_C1, TAG_C2, TAG_C3, TAG_C4 = 0xC0, 0xC1, 0xC2, 0xC3, 0xC4
+
+# 15-puzzle tile partitions for additive PDBs (tile numbers = goal cells): the 6-6-3 split used
+# for the training labels, and the 7-8 split of the paper's own STP heuristic (tiles 1-7 and
+# 8-15; tables of 16!/9! = 57,657,600 and 16!/8! = 518,918,400 one-byte entries).
+PATTERNS_663 = ([1, 2, 3, 5, 6, 7], [4, 8, 9, 12, 13, 14], [10, 11, 15])
+PATTERNS_78 = ([1, 2, 3, 4, 5, 6, 7], [8, 9, 10, 11, 12, 13, 14, 15])
