@@ -8,7 +8,7 @@
 #include <cstdio>
 #include <cstring>
 
-#include "common.cuh"
+#include "chain.h"
 
 namespace cbdfs {
 
@@ -36,52 +36,18 @@ int pdb_gather(int domain, const PdbParams &P, const uint64_t *states, uint32_t 
 int pdb_build_device(Ctx *c, int side, const int *tiles, int k, uint8_t *table, cudaStream_t st);
 uint64_t npk(int n, int k);
 
-constexpr int kChainBN = 256;
-constexpr int kChainMaxC = 32;
-struct ChainMaps {
-    CUtensorMap w[kMaxLayers];
-    CUtensorMap a[kMaxLayers];
-    CUtensorMap o[kMaxLayers];
-};
-struct ChainParams {
-    int nh;
-    int dims[kMaxLayers + 1];
-    int kdim[kMaxLayers];
-    int nt[kMaxLayers];
-    int tile_start[kMaxLayers + 1];
-    int mblocks;
-    uint32_t n;
-    const uint64_t *states;
-    void *onehot;
-    void *act[2];
-    const float *bias[kMaxLayers];
-    float acc_scale[kMaxLayers], out_qscale[kMaxLayers];
-    int *counters;
-    float *partial;
-    int rows_pad;
-    int C;
-    int head_kind, max_with_md;
-    const float *w_last, *b_last;
-    const uint8_t *g;
-    uint32_t bound;
-    uint8_t *h;
-    uint32_t *mask, *minf;
-    float *y;
-    int *err;
-    unsigned long long *trace;
-    int trace_tiles;
-};
-int chain_launch(int domain, bool fp8, const ChainMaps &maps, const ChainParams &P, int grid, cudaStream_t st);
 
-// the fused chain runs networks whose hidden widths are multiples of 256 and whose last
-// layer has at most 32 outputs
+
+// the fused chain runs low-precision networks whose hidden widths are multiples of 256; a last
+// layer of at most 32 outputs runs in its epilogue, a wider one in a separate kernel after it
 static bool chain_ok(const NetGPU &net) {
-    if (net.prec == CBDFS_PREC_FP32 || net.dims[net.L] > kChainMaxC) return false;
+    if (net.prec == CBDFS_PREC_FP32) return false;
     for (int l = 1; l < net.L; ++l)
         if (net.dims[l] % kChainBN) return false;
     return true;
 }
 static size_t chain_partial_floats(const NetGPU &net) {
+    if (net.dims[net.L] > kMaxHeadC) return 0;  // a separate kernel runs the last layer
     return (size_t)(net.dims[net.L - 1] / kChainBN) * net.dims[net.L];
 }
 
@@ -333,6 +299,8 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     P.n = n;
     int max_tiles = 0;
     P.tile_start[0] = 0;
+    P.fused_head = net.dims[L] <= kMaxHeadC;
+    P.bf16_store_layer = !P.fused_head && fp8 ? nh - 1 : -1;
     for (int l = 0; l < nh; ++l) {
         maps.w[l] = net.tm_w[l];
         if (l > 0) {
@@ -344,8 +312,8 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
             if (!m) return CBDFS_EDEVICE;
             maps.a[0] = *m;
         }
-        if (l < nh - 1) {  // stored activations: 32 x 32 boxes, written by TMA stores
-            const CUtensorMap *m = act_store_map(s, c, l & 1, net.dims[l + 1], eb);
+        if (l < nh - 1 || !P.fused_head) {  // stored activations: 32 x 32 boxes, by TMA stores
+            const CUtensorMap *m = act_store_map(s, c, l & 1, net.dims[l + 1], l == P.bf16_store_layer ? 2 : eb);
             if (!m) return CBDFS_EDEVICE;
             maps.o[l] = *m;
         } else {
@@ -386,6 +354,10 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     }
     CUDA_TRY(cudaMemsetAsync(s.counters, 0, sizeof(int) * (nh + 2) * P.mblocks, st));
     int rc = chain_launch(domain, fp8, maps, P, grid, st);
+    if (rc || (rc = mark(s, st)) || P.fused_head) return rc;
+    // the last layer (FP32) over the stored BF16 activations of the last hidden layer
+    rc = head(true, domain, net.head, s.act[(nh - 1) & 1], net.dims[nh], net.dims[L], net.w32[L - 1],
+              net.b32[L - 1], d_states, d_g, bound, n, net.max_with_md, d_h, d_mask, d_minf, d_y, st);
     return rc ? rc : mark(s, st);
 }
 
@@ -435,7 +407,8 @@ int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
         return rc ? rc : mark(s, st);
     }
     const bool fp8 = net.prec == CBDFS_PREC_FP8;
-    if (s.counters && s.partial && chain_ok(net) && chain_partial_floats(net) <= c->partial_floats)
+    if (s.counters && chain_ok(net) && chain_partial_floats(net) <= c->partial_floats &&
+        (s.partial || chain_partial_floats(net) == 0))
         return run_chain(c, s, net, domain, d_states, d_g, bound, n, d_h, d_mask, d_minf, d_y, st);
     int cur = 0;
     for (int l = 0; l < L - 1; ++l) {

@@ -1,0 +1,55 @@
+// chain.h -- what the host side and the fused network kernel (mlp_chain.cu) share.
+#pragma once
+#include "common.cuh"
+
+namespace cbdfs {
+
+constexpr int kChainBN = 256;     // output columns of a tile (one TMEM accumulator)
+constexpr int kChainStages = 4;
+constexpr int kChainThreads = 192;
+constexpr int kMaxHeadC = 32;     // widest last layer the in-epilogue head takes
+
+struct ChainMaps {
+    CUtensorMap w[kMaxLayers];  // weights of hidden layer l, [N][K] K-major
+    CUtensorMap a[kMaxLayers];  // A of hidden layer l: the one-hot rows (l = 0) or activations
+    CUtensorMap o[kMaxLayers];  // activations written by hidden layer l (32 x 32 store boxes)
+};
+
+struct ChainParams {
+    int nh;                        // hidden layers (tensor-core layers) = L-1
+    int dims[kMaxLayers + 1];
+    int kdim[kMaxLayers];          // K of hidden layer l (layer 0: padded one-hot width)
+    int nt[kMaxLayers];            // n-tiles of hidden layer l
+    int tile_start[kMaxLayers + 1];
+    int mblocks;
+    uint32_t n;
+    const uint64_t *states;
+    void *onehot;                  // [rows_pad][kdim[0]] one-hot input, written by the pre-pass
+    void *act[2];
+    const float *bias[kMaxLayers];
+    float acc_scale[kMaxLayers], out_qscale[kMaxLayers];
+    int *counters;                 // [mblocks] one-hot units (16 = all rows), then [nh][mblocks]
+                                   // stored warp-tiles (4 per tile), then [mblocks] head counts
+    float *partial;                // [nt_last][rows_pad][C]
+    int rows_pad;
+    int fused_head;                // 1: the last layer runs in the last hidden layer's epilogue;
+                                   // 0: every hidden layer is stored and a separate kernel
+                                   // runs the last layer
+    int bf16_store_layer;          // hidden layer whose stored output is BF16 in an E4M3
+                                   // network (the separate last layer reads BF16); -1 none
+    int C;                         // outputs of the last layer
+    int head_kind, max_with_md;
+    const float *w_last, *b_last;  // [C][dims[nh]], [C]
+    const uint8_t *g;
+    uint32_t bound;
+    uint8_t *h;
+    uint32_t *mask, *minf;
+    float *y;
+    int *err;
+    unsigned long long *trace;     // optional: [grid][trace_tiles][8] %globaltimer stamps
+    int trace_tiles;
+};
+
+int chain_launch(int domain, bool fp8, const ChainMaps &maps, const ChainParams &P, int grid, cudaStream_t st);
+
+}  // namespace cbdfs

@@ -30,51 +30,9 @@
 // Every wait is bounded (2 s of %globaltimer) and reports through the error flag.
 #include <cuda_fp8.h>
 
-#include "common.cuh"
+#include "chain.h"
 
 namespace cbdfs {
-
-constexpr int kChainBN = 256;
-constexpr int kChainStages = 4;
-constexpr int kChainThreads = 192;
-constexpr int kMaxHeadC = 32;
-
-struct ChainMaps {
-    CUtensorMap w[kMaxLayers];  // weights of hidden layer l, [N][K] K-major
-    CUtensorMap a[kMaxLayers];  // activations read by hidden layer l >= 1
-    CUtensorMap o[kMaxLayers];  // activations written by hidden layer l (32 x 32 store boxes)
-};
-
-struct ChainParams {
-    int nh;                        // hidden layers (tensor-core layers) = L-1
-    int dims[kMaxLayers + 1];
-    int kdim[kMaxLayers];          // K of hidden layer l (layer 0: padded one-hot width)
-    int nt[kMaxLayers];            // n-tiles of hidden layer l
-    int tile_start[kMaxLayers + 1];
-    int mblocks;
-    uint32_t n;
-    const uint64_t *states;
-    void *onehot;                  // [rows_pad][kdim[0]] one-hot input, written by the pre-pass
-    void *act[2];
-    const float *bias[kMaxLayers];
-    float acc_scale[kMaxLayers], out_qscale[kMaxLayers];
-    int *counters;                 // [mblocks] one-hot rows ready (4 = all warps), then
-                                   // [nh][mblocks] stored warp-tiles (4 per tile), then
-                                   // [mblocks] head partial counts
-    float *partial;                // [nt_last][rows_pad][C]
-    int rows_pad;
-    int C;                         // outputs of the last layer (fused head)
-    int head_kind, max_with_md;
-    const float *w_last, *b_last;  // [C][dims[nh]], [C]
-    const uint8_t *g;
-    uint32_t bound;
-    uint8_t *h;
-    uint32_t *mask, *minf;
-    float *y;
-    int *err;
-    unsigned long long *trace;     // optional: [grid][trace_tiles][8] %globaltimer stamps
-    int trace_tiles;
-};
 
 namespace {
 
@@ -248,7 +206,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int total = P.tile_start[P.nh];
-    const int last_l = P.nh - 1;
+    const int last_l = P.fused_head ? P.nh - 1 : P.nh;  // the layer whose epilogue runs the head
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kChainStages; ++s) {
@@ -423,7 +381,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
             const float *bias = bt;  // shared memory
             const float sc = P.acc_scale[T.l];
             if (T.l < last_l) {
-                const bool out8 = FP8;  // every stored activation is read by the next layer's TMA
+                const bool out8 = FP8 && T.l != P.bf16_store_layer;  // E4M3 unless the BF16 head reads it
                 const float oq = P.out_qscale[T.l];
                 uint8_t *wstg = stg + q * kStagingWarp;
 #pragma unroll 1
@@ -587,7 +545,7 @@ template <int D, bool F>
 static int launch_t(const ChainMaps &maps, const ChainParams &P, int grid, cudaStream_t st) {
     const size_t smem = chain_smem_bytes();
     void (*kern)(const ChainMaps, const ChainParams) =
-        P.C == 1 ? k_chain<D, F, 1> : P.C <= 24 ? k_chain<D, F, 24> : k_chain<D, F, kMaxHeadC>;
+        P.C == 1 || !P.fused_head ? k_chain<D, F, 1> : P.C <= 24 ? k_chain<D, F, 24> : k_chain<D, F, kMaxHeadC>;
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -604,7 +562,7 @@ static int launch_t(const ChainMaps &maps, const ChainParams &P, int grid, cudaS
 }
 
 int chain_launch(int domain, bool fp8, const ChainMaps &maps, const ChainParams &P, int grid, cudaStream_t st) {
-    if (P.C < 1 || P.C > kMaxHeadC) return fail(CBDFS_EINVAL, "fused head width %d", P.C);
+    if (P.fused_head && (P.C < 1 || P.C > kMaxHeadC)) return fail(CBDFS_EINVAL, "fused head width %d", P.C);
     if (fp8) {
         if (domain == CBDFS_DOM_STP3) return launch_t<CBDFS_DOM_STP3, true>(maps, P, grid, st);
         if (domain == CBDFS_DOM_STP4) return launch_t<CBDFS_DOM_STP4, true>(maps, P, grid, st);

@@ -3,10 +3,12 @@
 //   k_first_gather  FP32 first layer as what it is algorithmically: a sum of the weight
 //                   columns picked by the one-hot input (16 / 9 / 20 of them), + bias, ReLU.
 //   k_sgemm_relu    FP32 hidden layer, C = ReLU(A W^T + b), 128x128 tiles on the CUDA cores.
-//   k_head          the last layer in FP32 fused with the integer-h rule and the bound test
+//   k_head_tiled    the last layer in FP32 fused with the integer-h rule and the bound test
 //                   (Algorithm 3's expansion test g + h <= bound; the smallest f above the
-//                   bound feeds UpdateThreshold, Algorithm 1).  Reads BF16 or FP32
-//                   activations.  One block = 32 states = one mask word.
+//                   bound feeds UpdateThreshold, Algorithm 1), for up to 128 outputs: a block
+//                   computes 64 states x all outputs as a register-tiled FP32 GEMM over
+//                   k-chunks staged in shared memory.  Reads BF16 or FP32 activations.
+//   k_head          the same for wider last layers: one warp per state and output.
 #include "common.cuh"
 
 namespace cbdfs {
@@ -204,10 +206,177 @@ k_head(const TIn *__restrict__ act, int K, int C, const float *__restrict__ W,
     }
 }
 
+// ---- the last layer, register-tiled: Y[64][CPAD] = A[64][K] W^T + b ------------------
+// 256 threads, 64 states; thread (ty, tx) = (tid / 16, tid % 16) owns rows 4ty..4ty+3 and
+// columns CPT*tx..CPT*tx+CPT-1 (CPAD = 16 CPT).  K is walked in chunks of 32, the next
+// chunk's activations and weights loaded into registers while the current one is used: A
+// transposed into As[k][row] (a thread's four rows are one float4), W as Ws[col][k] padded to
+// 33 floats a row.  Then the logits go to shared memory and each warp finishes eight rows.
+constexpr int HT_BM = 64, HT_BK = 32, HT_THREADS = 256;
+static_assert(HT_BM * HT_BK == 8 * HT_THREADS && HT_BM == 8 * (HT_THREADS / 32), "head tile shape");
+
+template <typename TIn, int DOMAIN, int HEAD, int CPT>
+__global__ void __launch_bounds__(HT_THREADS)
+k_head_tiled(const TIn *__restrict__ act, int K, int C, const float *__restrict__ W,
+             const float *__restrict__ bL, const uint64_t *__restrict__ states,
+             const uint8_t *__restrict__ g, uint32_t bound, uint32_t n, int max_with_md,
+             uint8_t *__restrict__ h_out, uint32_t *__restrict__ mask, uint32_t *__restrict__ minf,
+             float *__restrict__ y_out) {
+    constexpr int CPAD = 16 * CPT;
+    constexpr int NW4 = (CPAD * HT_BK / 4 + HT_THREADS - 1) / HT_THREADS;  // float4 of W per thread
+    // As + Ws while the K loop runs, then the logits Ys in the same memory
+    constexpr int kLoop = HT_BK * HT_BM + CPAD * (HT_BK + 1), kOut = HT_BM * (CPAD + 1);
+    __shared__ __align__(16) float buf[kLoop > kOut ? kLoop : kOut];
+    float (*As)[HT_BM] = reinterpret_cast<float (*)[HT_BM]>(buf);
+    float (*Ws)[HT_BK + 1] = reinterpret_cast<float (*)[HT_BK + 1]>(buf + HT_BK * HT_BM);
+    float (*Ys)[CPAD + 1] = reinterpret_cast<float (*)[CPAD + 1]>(buf);
+    __shared__ uint32_t fval[HT_BM];
+    __shared__ uint8_t pass[HT_BM];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ty = tid >> 4, tx = tid & 15;
+    const uint32_t r0 = blockIdx.x * HT_BM;
+    float acc[4][CPT];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) acc[i][j] = 0.f;
+    // loaders: A row lr, k offset lk (8 elements); W float4 number tid + q * HT_THREADS
+    const int lr = tid >> 2, lk = (tid & 3) * 8;
+    float av[8];
+    float4 wv[NW4];
+    auto load = [&](int k0) {
+        if (r0 + lr < n) load8(act + (size_t)(r0 + lr) * K + k0 + lk, av);
+        else
+#pragma unroll
+            for (int j = 0; j < 8; ++j) av[j] = 0.f;
+#pragma unroll
+        for (int q = 0; q < NW4; ++q) {
+            const int idx = tid + q * HT_THREADS;  // column idx / 8, k idx % 8 * 4
+            const int c = idx >> 3;
+            wv[q] = (idx < CPAD * HT_BK / 4 && c < C)
+                        ? __ldg(reinterpret_cast<const float4 *>(W + (size_t)c * K + k0) + (idx & 7))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    load(0);
+    for (int k0 = 0; k0 < K; k0 += HT_BK) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) As[lk + j][lr] = av[j];
+#pragma unroll
+        for (int q = 0; q < NW4; ++q) {
+            const int idx = tid + q * HT_THREADS;
+            if (idx < CPAD * HT_BK / 4) {
+                float *w = &Ws[idx >> 3][(idx & 7) * 4];
+                w[0] = wv[q].x;
+                w[1] = wv[q].y;
+                w[2] = wv[q].z;
+                w[3] = wv[q].w;
+            }
+        }
+        __syncthreads();
+        if (k0 + HT_BK < K) load(k0 + HT_BK);  // in flight while this chunk is used
+#pragma unroll 8
+        for (int k = 0; k < HT_BK; ++k) {
+            const float4 a = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                const float w = Ws[tx * CPT + j][k];
+                acc[0][j] = fmaf(a.x, w, acc[0][j]);
+                acc[1][j] = fmaf(a.y, w, acc[1][j]);
+                acc[2][j] = fmaf(a.z, w, acc[2][j]);
+                acc[3][j] = fmaf(a.w, w, acc[3][j]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+            const int c = tx * CPT + j;
+            Ys[ty * 4 + i][c] = acc[i][j] + (c < C ? __ldg(bL + c) : 0.f);
+        }
+    __syncthreads();
+    // warp w finishes rows 8w .. 8w+7
+    for (int i = 0; i < 8; ++i) {
+        const int loc = warp * 8 + i;
+        const uint32_t m = r0 + loc;
+        if (m >= n) {  // warp-uniform
+            if (lane == 0) { pass[loc] = 0; fval[loc] = 0xFFFFFFFFu; }
+            continue;
+        }
+        if (y_out)
+            for (int c = lane; c < C; c += 32) y_out[(size_t)m * C + c] = Ys[loc][c];
+        int hv;
+        if (HEAD == CBDFS_HEAD_REGRESSION) {
+            hv = (int)fminf(fmaxf(rintf(Ys[loc][0]), 0.f), 255.f);
+        } else {
+            // argmax, lowest index on ties
+            float bv = -INFINITY;
+            int bi = 0x7FFFFFFF;
+            for (int c = lane; c < C; c += 32)
+                if (Ys[loc][c] > bv) { bv = Ys[loc][c]; bi = c; }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(0xFFFFFFFFu, bv, o);
+                const int oi = __shfl_xor_sync(0xFFFFFFFFu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+            }
+            hv = bi;
+        }
+        if (lane == 0) {
+            bool goal;
+            if (DOMAIN == CBDFS_DOM_RC3) {
+                goal = rc_is_goal(states[2 * m], states[2 * m + 1]);
+            } else {
+                constexpr int SIDE = DOMAIN == CBDFS_DOM_STP3 ? 3 : 4;
+                const uint64_t s = states[m];
+                if (max_with_md) hv = max(hv, manhattan<SIDE>(s));
+                goal = stp_is_goal<SIDE>(s);
+            }
+            hv = goal ? 0 : min(hv, 255);
+            h_out[m] = (uint8_t)hv;
+            const uint32_t f = (uint32_t)g[m] + (uint32_t)hv;
+            pass[loc] = f <= bound;
+            fval[loc] = f <= bound ? 0xFFFFFFFFu : f;
+        }
+    }
+    __syncthreads();
+    if (warp < HT_BM / 32) {
+        const int loc = warp * 32 + lane;
+        const uint32_t bits = __ballot_sync(0xFFFFFFFFu, pass[loc] != 0);
+        const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, fval[loc]);
+        if (lane == 0 && r0 + warp * 32 < n) {
+            mask[(r0 >> 5) + warp] = bits;
+            if (mn != 0xFFFFFFFFu) atomicMin(minf, mn);
+        }
+    }
+}
+
+template <typename TIn, int DOMAIN, int HEAD>
+int head_tiled(const TIn *act, int K, int C, const float *W, const float *b, const uint64_t *states,
+               const uint8_t *g, uint32_t bound, uint32_t n, int md, uint8_t *h, uint32_t *mask,
+               uint32_t *minf, float *y, cudaStream_t st) {
+    const unsigned blocks = (n + HT_BM - 1) / HT_BM;
+#define HT_LAUNCH(CPT) k_head_tiled<TIn, DOMAIN, HEAD, CPT><<<blocks, HT_THREADS, 0, st>>>(act, K, C, W, b, states, g, bound, n, md, h, mask, minf, y)
+    if (C <= 16) HT_LAUNCH(1);
+    else if (C <= 32) HT_LAUNCH(2);
+    else if (C <= 64) HT_LAUNCH(4);
+    else if (C <= 96) HT_LAUNCH(6);
+    else HT_LAUNCH(8);
+#undef HT_LAUNCH
+    CUDA_TRY(cudaGetLastError());
+    return CBDFS_OK;
+}
+
 template <typename TIn, int DOMAIN>
 int head_dom(int head, const TIn *act, int K, int C, const float *W, const float *b,
              const uint64_t *states, const uint8_t *g, uint32_t bound, uint32_t n, int md,
              uint8_t *h, uint32_t *mask, uint32_t *minf, float *y, cudaStream_t st) {
+    if (C <= 128 && K % HT_BK == 0 && (size_t)act % 16 == 0 && (size_t)W % 16 == 0)
+        return head == CBDFS_HEAD_REGRESSION
+                   ? head_tiled<TIn, DOMAIN, CBDFS_HEAD_REGRESSION>(act, K, C, W, b, states, g, bound, n, md, h, mask, minf, y, st)
+                   : head_tiled<TIn, DOMAIN, CBDFS_HEAD_CLASSIFIER>(act, K, C, W, b, states, g, bound, n, md, h, mask, minf, y, st);
     const unsigned blocks = (n + 31) / 32;
     const size_t sm = 4 * C * sizeof(float);
     if (head == CBDFS_HEAD_REGRESSION)

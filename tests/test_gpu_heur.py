@@ -273,3 +273,51 @@ def test_fused_chain_matches_per_layer_kernels(P, ctx, orc, prec):
     assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1]) and outs[0][2] == outs[1][2]
     assert P.cbdfs_device_status(ctx) == 0
+
+
+# The 81-class network of the training configuration: wider than the fused head, so the chain
+# stores its last hidden layer (BF16) and the register-tiled FP32 head kernel runs after it.
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+@pytest.mark.parametrize("n", [1, 129, 1000])
+def test_c3_classifier_81(P, ctx, orc, prec, n):
+    Ws, bs = W.net_weights(**W.NET_C3)
+    sc = fp8_act_scales(orc, 1, Ws, bs, W.random_stp_states(4, 4096, 13)) if prec == "fp8" else None
+    hid = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, PREC[prec], P.HEAD_CLASSIFIER, 1, act_scales=sc)
+    s = W.random_stp_states(4, n, 90 + n)
+    s[0] = W.stp_goal(4)
+    g = _g(n, n + 6, 60)
+    h, mask, minf, y = P.heur_submit_batch(ctx, hid, P.DOM_STP4, s, g, 70, want_y=True, n_out=81)
+    ye, he, margin = oracle_net(orc, 1, Ws, bs, prec, s, "classifier", True, act_scales=sc)
+    check_logits(y, ye, prec)
+    nm = check_h(h, he, margin)
+    assert h[0] == 0
+    _check_bound(orc, h, g, 70, mask, minf)
+    print(f"{prec} 81-class margin mismatches: {nm} of {n}")
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_c3_chain_matches_per_layer_kernels(P, ctx, orc, prec):
+    """Chain + separate head against the per-layer kernels + the same head: both store the last
+    hidden layer in BF16 after the same tensor-core arithmetic, so results are identical."""
+    import torch
+    Ws, bs = W.net_weights(**W.NET_C3)
+    sc = fp8_act_scales(orc, 1, Ws, bs, W.random_stp_states(4, 4096, 13)) if prec == "fp8" else None
+    hid = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, PREC[prec], P.HEAD_CLASSIFIER, 1, act_scales=sc)
+    dev = torch.device("cuda:0")
+    n = 4000
+    s = W.random_stp_states(4, n, 5432)
+    g = _g(n, 18, 60)
+    ds = torch.from_numpy(s.view(np.int64)).to(dev)
+    dg = torch.from_numpy(g).to(dev)
+    outs = []
+    for fn in (P.heur_eval_device, P.heur_eval_device_static):
+        dh = torch.empty(n, dtype=torch.uint8, device=dev)
+        dm = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
+        dmin = torch.empty(1, dtype=torch.int32, device=dev)
+        fn(ctx, hid, P.DOM_STP4, ds, dg, 70, n, dh, dm, dmin, stream=torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        outs.append((dh.cpu().numpy(), dm.cpu().numpy(), int(dmin.cpu()[0])))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1]) and outs[0][2] == outs[1][2]
+    assert P.cbdfs_device_status(ctx) == 0
