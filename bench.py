@@ -93,7 +93,7 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def kernel_traffic(key, summary="chain_c1_bf16_b8192.md", sources=("mlp_chain.cu", "common.cuh")):
+def kernel_traffic(key, summary="chain_c1_bf16_b8192.md", sources=("mlp_chain.cu", "chain.h", "common.cuh")):
     """DRAM bytes per launch of a kernel from its committed ncu summary, if the kernel source
     is the one the counters were taken on; else None."""
     path = os.path.join(ROOT, "profiles", summary)
@@ -406,7 +406,19 @@ def pdb_leg(P, args):
                          "achieved_gbs_algorithmic": rate * alg / 1e9}
         out["hbm_peak_gbs"] = pk["hbm"]
         out["peak_source"] = f"{pk['src']} HBM copy"
-        out["traffic_per_launch"] = kernel_traffic("pdb78", "pdb_gather_7_8_b4m.md", ("pdb.cu", "common.cuh"))
+        # roofline of the HBM-resident case: achieved = bytes at 32-byte-sector granularity per
+        # launch / event time; traffic = the DRAM bytes ncu measured for this launch size (a
+        # random byte lookup costs DRAM a 64-byte access, so the device moves more than that)
+        r = out["7-8"]
+        traffic = kernel_traffic("pdb78", "pdb_gather_7_8_b4m.md", ("pdb.cu", "common.cuh"))
+        if traffic is not None and n != 1 << 22:
+            traffic = traffic * n / (1 << 22)
+        out["roofline"] = {"kernel": "k_pdb_gather (7-8 tables, HBM-resident)", "bound": "hbm",
+                           "achieved": r["achieved_gbs_sectors"], "peak": pk["hbm"], "unit": "GB/s",
+                           "frac": r["frac_of_hbm_sectors"], "traffic": traffic,
+                           "traffic_gbs": traffic / (r["launch_ms"] / 1e3) / 1e9 if traffic else None,
+                           "traffic_frac": traffic / (r["launch_ms"] / 1e3) / 1e9 / pk["hbm"] if traffic else None,
+                           "bytes_per_state_model": "8 state + 1 g + 1 h + 1/8 mask + 32 per table lookup"}
         # the 7-8 sum dominates Manhattan distance on every state of the batch
         h = dh.cpu().numpy()  # last launch: the 6-6-3 heuristic
         h78 = P.heur_submit_batch(ctx, hid78, P.DOM_STP4, states[:65536], g[:65536], BOUND)[0]
