@@ -362,6 +362,9 @@ typedef struct {
     double seconds;                 /* wall time of the solve */
     int d_init;                     /* initial partition depth used */
     int64_t work_items;             /* subtrees in the shared work queue */
+    double batch_fill_us;           /* mean time from a batch's first state to its submission */
+    double batch_flight_us;         /* mean time from submission to its results being readable */
+    double submit_us;               /* mean host time the batch processor spends submitting one */
 } cbdfs_result;
 
 /* Solve from `start` (packed words).  heur_id: a network, a PDB or a built-in id.

@@ -116,7 +116,8 @@ class Result(ctypes.Structure):
                 ("expanded", ctypes.c_int64), ("generated", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("evaluated", ctypes.c_int64),
                 ("seconds", ctypes.c_double), ("d_init", ctypes.c_int),
-                ("work_items", ctypes.c_int64)]
+                ("work_items", ctypes.c_int64), ("batch_fill_us", ctypes.c_double),
+                ("batch_flight_us", ctypes.c_double), ("submit_us", ctypes.c_double)]
 
 
 _vp, _u64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)
@@ -449,7 +450,8 @@ def cbdfs_solve(ctx, domain, start, algo=ALGO_IDA, heur_id=HEUR_MD, partial_ok=F
                 iter_limit=list(r.iter_limit[:k]), iter_cut=list(r.iter_cut[:k]),
                 n_iters=r.n_iters, expanded=r.expanded, generated=r.generated,
                 batches=r.batches, evaluated=r.evaluated, seconds=r.seconds, d_init=r.d_init,
-                work_items=r.work_items)
+                work_items=r.work_items, batch_fill_us=r.batch_fill_us,
+                batch_flight_us=r.batch_flight_us, submit_us=r.submit_us)
 
 
 def cbdfs_cancel(ctx):

@@ -40,6 +40,9 @@ uint64_t npk(int n, int k);
 
 // the fused chain runs low-precision networks whose hidden widths are multiples of 256; a last
 // layer of at most 32 outputs runs in its epilogue, a wider one in a separate kernel after it
+// ints of a slot's chain counters: (layers + 2) per row block, and the finished-CTA count
+static int chain_counter_ints(const Ctx *c) { return (kMaxLayers + 2) * (c->max_batch_pad / kBM) + 1; }
+
 static bool chain_ok(const NetGPU &net) {
     if (net.prec == CBDFS_PREC_FP32) return false;
     for (int l = 1; l < net.L; ++l)
@@ -206,10 +209,11 @@ int ensure_act(Ctx *c, size_t width) {
 
 // chain scratch of every slot: tile counters, and head partials of `floats` per row
 int ensure_chain(Ctx *c, size_t floats) {
-    const size_t cbytes = sizeof(int) * (kMaxLayers + 2) * (c->max_batch_pad / kBM);
+    const size_t cbytes = sizeof(int) * chain_counter_ints(c);
     for (auto &s : c->slots)
         if (!s.counters) {
             int rc = dev_alloc(c, (void **)&s.counters, cbytes);
+            if (!rc && cudaMemset(s.counters, 0, cbytes) != cudaSuccess) rc = fail(CBDFS_EDEVICE, "counter init");
             if (!rc) rc = dev_alloc(c, &s.onehot, (size_t)c->max_batch_pad * 1024);
             if (rc) return rc;
         }
@@ -352,7 +356,7 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
         *s.trace_grid = grid;
         CUDA_TRY(cudaMemsetAsync(s.trace, 0, sizeof(unsigned long long) * grid * s.trace_tiles * 8, st));
     }
-    CUDA_TRY(cudaMemsetAsync(s.counters, 0, sizeof(int) * (nh + 2) * P.mblocks, st));
+    P.done_index = chain_counter_ints(c) - 1;
     int rc = chain_launch(domain, fp8, maps, P, grid, st);
     if (rc || (rc = mark(s, st)) || P.fused_head) return rc;
     // the last layer (FP32) over the stored BF16 activations of the last hidden layer
@@ -458,10 +462,8 @@ void cbdfs_destroy(cbdfs_ctx *ctx) {
         for (int i = 0; i < 2; ++i) dev_free(c, s.act[i], c->act_bytes);
         dev_free(c, s.d_states, (size_t)c->max_batch_pad * 16);
         dev_free(c, s.d_g, c->max_batch_pad);
-        dev_free(c, s.d_h, c->max_batch_pad);
-        dev_free(c, s.d_mask, c->max_batch_pad / 8);
-        dev_free(c, s.d_minf, 4);
-        dev_free(c, s.counters, sizeof(int) * (kMaxLayers + 2) * (c->max_batch_pad / kBM));
+        dev_free(c, s.d_h, slot_out_bytes(c));  // h, mask and minf share one allocation
+        dev_free(c, s.counters, sizeof(int) * chain_counter_ints(c));
         dev_free(c, s.onehot, (size_t)c->max_batch_pad * 1024);
         dev_free(c, s.partial, s.partial_bytes);
         if (s.stream) cudaStreamDestroy(s.stream);
@@ -512,9 +514,12 @@ int cbdfs_create(const cbdfs_config *cfg, cbdfs_ctx **out) {
         if (i == 0) continue;
         rc = dev_alloc(c, (void **)&s.d_states, (size_t)c->max_batch_pad * 16);
         if (!rc) rc = dev_alloc(c, (void **)&s.d_g, c->max_batch_pad);
-        if (!rc) rc = dev_alloc(c, (void **)&s.d_h, c->max_batch_pad);
-        if (!rc) rc = dev_alloc(c, (void **)&s.d_mask, c->max_batch_pad / 8);
-        if (!rc) rc = dev_alloc(c, (void **)&s.d_minf, 4);
+        // h, mask and minf in one block (slot_out_bytes), so that one copy returns them all
+        if (!rc) rc = dev_alloc(c, (void **)&s.d_h, slot_out_bytes(c));
+        if (!rc) {
+            s.d_mask = reinterpret_cast<uint32_t *>(s.d_h + c->max_batch_pad);
+            s.d_minf = s.d_mask + c->max_batch_pad / 32;
+        }
     }
     if (rc) {
         cbdfs_destroy(reinterpret_cast<cbdfs_ctx *>(c));

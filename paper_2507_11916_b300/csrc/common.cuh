@@ -142,6 +142,10 @@ int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
              const uint8_t *d_g, uint32_t bound, uint32_t n, uint8_t *d_h, uint32_t *d_mask,
              uint32_t *d_minf, float *d_y, cudaStream_t st);
 
+// a slot's outputs, one allocation: h [max_batch_pad] bytes, then mask [max_batch_pad / 32]
+// words, then minf (one word)
+inline size_t slot_out_bytes(const Ctx *c) { return (size_t)c->max_batch_pad + c->max_batch_pad / 8 + 4; }
+
 // per-domain facts
 inline int dom_words(int d) { return d == CBDFS_DOM_RC3 ? 2 : 1; }
 inline int dom_side(int d) { return d == CBDFS_DOM_STP3 ? 3 : 4; }

@@ -30,6 +30,9 @@
 // Every wait is bounded (2 s of %globaltimer) and reports through the error flag.
 #include <cuda_fp8.h>
 
+#include <mutex>
+#include <set>
+
 #include "chain.h"
 
 namespace cbdfs {
@@ -534,19 +537,48 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
         tc_fence_after();
         tmem_dealloc(tmem, 512);
     }
+    // the last CTA to finish (none polls a counter any more) leaves the counters zeroed for
+    // the next launch on this slot
+    if (threadIdx.x == 0) {
+        __threadfence();
+        *flag = atomicAdd(P.counters + P.done_index, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (*flag) {
+        __threadfence();
+        const int nints = (P.nh + 2) * P.mblocks;
+        for (int i = threadIdx.x; i < nints; i += blockDim.x) P.counters[i] = 0;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicExch(P.counters + P.done_index, 0);
+    }
 }
 
 }  // namespace
 
 size_t chain_smem_bytes() { return 1024 + kChainStages * (kStageA + kStageB) + kStaging + kBiasSmem + 256; }
 
-// Launch the chain for one batch.  P.counters must be zeroed (on stream st) beforehand.
+// the kernel's dynamic shared-memory limit, raised once per kernel and device
+static int allow_smem(const void *kern, size_t smem) {
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({kern, dev})) return CBDFS_OK;
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    done.insert({kern, dev});
+    return CBDFS_OK;
+}
+
+// Launch the chain for one batch.  P.counters must be zero (they are after the previous
+// launch on the same counters, and after allocation).
 template <int D, bool F>
 static int launch_t(const ChainMaps &maps, const ChainParams &P, int grid, cudaStream_t st) {
     const size_t smem = chain_smem_bytes();
     void (*kern)(const ChainMaps, const ChainParams) =
         P.C == 1 || !P.fused_head ? k_chain<D, F, 1> : P.C <= 24 ? k_chain<D, F, 24> : k_chain<D, F, kMaxHeadC>;
-    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (int rc = allow_smem(reinterpret_cast<const void *>(kern), smem)) return rc;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kChainThreads);

@@ -36,9 +36,10 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 // shared batches
 // ---------------------------------------------------------------------------------------
 struct Batch {
-    // pinned host arrays
+    // pinned host arrays; h, mask and minf lie in `out` in the slot's device layout
+    // (slot_out_bytes), so that one copy returns them
     uint64_t *states = nullptr;
-    uint8_t *g = nullptr, *h = nullptr;
+    uint8_t *g = nullptr, *h = nullptr, *out = nullptr;
     uint32_t *mask = nullptr, *minf = nullptr;
     uint8_t *h2 = nullptr;  // fixed-tree mode: the evaluated (not pruning) heuristic
     uint32_t *mask2 = nullptr, *minf2 = nullptr;
@@ -49,7 +50,7 @@ struct Batch {
     int state = 0;                        // 0 free, 1 open, 2 in flight, 3 done, 4 full
     int slot = -1;
     cudaEvent_t ev = nullptr;
-    Clock::time_point first_add;
+    Clock::time_point first_add, submitted;
 };
 
 struct Shared;
@@ -109,6 +110,7 @@ struct Shared {
     std::vector<int> slot_free;
     // results
     std::atomic<int64_t> expanded{0}, generated{0}, evaluated{0}, nbatches{0};
+    int64_t fill_ns = 0, flight_ns = 0, submit_ns = 0;  // batch timing sums (processor thread)
     std::atomic<uint32_t> minf{kNone};
     std::atomic<int> found{0}, stop{0}, cut{0};
     std::mutex sol_mu;
@@ -152,6 +154,8 @@ bool open_batch(Shared &S) {
 // slots asynchronously; publishes results.
 // ---------------------------------------------------------------------------------------
 int submit(Shared &S, Batch &b) {
+    const auto t_in = Clock::now();
+    S.fill_ns += std::chrono::duration_cast<std::chrono::nanoseconds>(t_in - b.first_add).count();
     Ctx *c = S.c;
     const int si = S.slot_free.back();
     S.slot_free.pop_back();
@@ -174,13 +178,13 @@ int submit(Shared &S, Batch &b) {
     rc = run_eval(c, sl, S.prune_heur, S.D->dom, sl.d_states, sl.d_g, S.bound, n, sl.d_h, sl.d_mask,
                   sl.d_minf, nullptr, st);
     if (rc) return rc;
-    if ((n && (cudaMemcpyAsync(b.h, sl.d_h, n, cudaMemcpyDeviceToHost, st) ||
-               cudaMemcpyAsync(b.mask, sl.d_mask, (size_t)(n + 31) / 32 * 4, cudaMemcpyDeviceToHost, st))) ||
-        cudaMemcpyAsync(b.minf, sl.d_minf, 4, cudaMemcpyDeviceToHost, st) || cudaEventRecord(b.ev, st))
+    if (cudaMemcpyAsync(b.out, sl.d_h, slot_out_bytes(c), cudaMemcpyDeviceToHost, st) || cudaEventRecord(b.ev, st))
         return fail(CBDFS_EDEVICE, "result download");
     b.state = 2;
     S.nbatches++;
     S.evaluated += n;
+    b.submitted = Clock::now();
+    S.submit_ns += std::chrono::duration_cast<std::chrono::nanoseconds>(b.submitted - t_in).count();
     return CBDFS_OK;
 }
 
@@ -196,6 +200,7 @@ void processor(Shared &S) {
                 Batch &b = *S.batches[inflight[i]];
                 cudaError_t q = cudaEventQuery(b.ev);
                 if (q == cudaSuccess) {
+                    S.flight_ns += std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - b.submitted).count();
                     if (b.n) atomic_min(S.minf, *b.minf);
                     b.state = 3;
                     S.slot_free.push_back(b.slot);
@@ -474,7 +479,8 @@ struct Solver {
     int d_init = 0;
     std::vector<int> slots;
     std::vector<std::unique_ptr<Batch>> batches;
-    int64_t evaluated = 0, nbatches = 0;
+    int64_t evaluated = 0, nbatches = 0, search_batches = 0;
+    int64_t fill_ns = 0, flight_ns = 0, submit_ns = 0;
     double seconds = 0;
     int64_t expanded_total = 0;
 
@@ -668,6 +674,10 @@ struct Solver {
         proc.join();
         evaluated += S.evaluated.load();
         nbatches += S.nbatches.load();
+        search_batches += S.nbatches.load();
+        fill_ns += S.fill_ns;
+        flight_ns += S.flight_ns;
+        submit_ns += S.submit_ns;
         if (S.error.load()) return fail(S.error.load(), "%s", S.error_msg.c_str());
         o.expanded += S.expanded.load();
         o.generated += S.generated.load();
@@ -855,10 +865,15 @@ int cbdfs_solve(cbdfs_ctx *ctx, int domain, const uint64_t *start, int algo, int
     for (size_t i = 0; i < 2 * sv.slots.size() && !rc; ++i) {
         auto b = std::make_unique<Batch>();
         const size_t cap = cfg.batch;
-        if (cudaMallocHost(&b->states, cap * 8 * w) || cudaMallocHost(&b->g, cap) || cudaMallocHost(&b->h, cap) ||
-            cudaMallocHost(&b->h2, cap) || cudaMallocHost(&b->mask, (cap + 31) / 32 * 4 + 4) ||
-            cudaMallocHost(&b->minf, 4) || cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming))
+        if (cudaMallocHost(&b->states, cap * 8 * w) || cudaMallocHost(&b->g, cap) ||
+            cudaMallocHost(&b->out, slot_out_bytes(c)) || cudaMallocHost(&b->h2, cap) ||
+            cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming))
             rc = fail(CBDFS_ENOMEM, "pinned batch buffers");
+        if (b->out) {
+            b->h = b->out;
+            b->mask = reinterpret_cast<uint32_t *>(b->out + c->max_batch_pad);
+            b->minf = b->mask + c->max_batch_pad / 32;
+        }
         sv.batches.push_back(std::move(b));
     }
     if (!rc) rc = sv.generate_work(sv.D.make(start));
@@ -866,10 +881,8 @@ int cbdfs_solve(cbdfs_ctx *ctx, int domain, const uint64_t *start, int algo, int
     for (auto &b : sv.batches) {
         cudaFreeHost(b->states);
         cudaFreeHost(b->g);
-        cudaFreeHost(b->h);
+        cudaFreeHost(b->out);
         cudaFreeHost(b->h2);
-        cudaFreeHost(b->mask);
-        cudaFreeHost(b->minf);
         if (b->ev) cudaEventDestroy(b->ev);
     }
     {
@@ -879,6 +892,10 @@ int cbdfs_solve(cbdfs_ctx *ctx, int domain, const uint64_t *start, int algo, int
     c->slot_cv.notify_all();
     out->batches = sv.nbatches;
     out->evaluated = sv.evaluated;
+    const double nb = (double)std::max<int64_t>(1, sv.search_batches);
+    out->batch_fill_us = sv.fill_ns / nb / 1e3;
+    out->batch_flight_us = sv.flight_ns / nb / 1e3;
+    out->submit_us = sv.submit_ns / nb / 1e3;
     out->d_init = sv.d_init;
     out->work_items = sv.tree.empty() ? 0 : (int64_t)(sv.level_start[sv.d_init + 1] - sv.level_start[sv.d_init]);
     out->seconds = std::chrono::duration<double>(Clock::now() - t0).count();
