@@ -301,12 +301,15 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     P.mblocks = rows_pad / kBM;
     P.rows_pad = rows_pad;
     P.n = n;
+    // small batches: 64-wide tiles, so that a layer's tiles spread over more CTAs (the head
+    // partials then need four times the floats per row, within the slot's allocation)
+    const int bn = P.mblocks <= kChainSmallMBlocks && 4 * rows_pad <= c->max_batch_pad ? kChainBNSmall : kChainBN;
     int max_tiles = 0;
     P.tile_start[0] = 0;
     P.fused_head = net.dims[L] <= kMaxHeadC;
     P.bf16_store_layer = !P.fused_head && fp8 ? nh - 1 : -1;
     for (int l = 0; l < nh; ++l) {
-        maps.w[l] = net.tm_w[l];
+        maps.w[l] = bn == kChainBNSmall ? net.tm_w64[l] : net.tm_w[l];
         if (l > 0) {
             const CUtensorMap *m = act_map(s, c, (l - 1) & 1, net.dims[l], eb);
             if (!m) return CBDFS_EDEVICE;
@@ -324,7 +327,7 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
             maps.o[l] = net.tm_w[0];  // unused
         }
         P.kdim[l] = l == 0 ? net.k1pad : net.dims[l];
-        P.nt[l] = net.dims[l + 1] / kChainBN;
+        P.nt[l] = net.dims[l + 1] / bn;
         P.tile_start[l + 1] = P.tile_start[l] + P.nt[l] * P.mblocks;
         max_tiles = std::max(max_tiles, P.nt[l] * P.mblocks);
         P.bias[l] = net.b32[l];
@@ -357,7 +360,7 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
         CUDA_TRY(cudaMemsetAsync(s.trace, 0, sizeof(unsigned long long) * grid * s.trace_tiles * 8, st));
     }
     P.done_index = chain_counter_ints(c) - 1;
-    int rc = chain_launch(domain, fp8, maps, P, grid, st);
+    int rc = chain_launch(domain, fp8, bn, maps, P, grid, st);
     if (rc || (rc = mark(s, st)) || P.fused_head) return rc;
     // the last layer (FP32) over the stored BF16 activations of the last hidden layer
     rc = head(true, domain, net.head, s.act[(nh - 1) & 1], net.dims[nh], net.dims[L], net.w32[L - 1],
@@ -612,6 +615,11 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
             if ((rc = make_tmap_2d(&N.tm_w[l], N.w_lp[l],
                                    fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                                    fp8 ? 1 : 2, (uint64_t)Kp, (uint64_t)O, kblk, N.bn[l])))
+                return rc;
+            if (O % kChainBNSmall == 0 &&
+                (rc = make_tmap_2d(&N.tm_w64[l], N.w_lp[l],
+                                   fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                                   fp8 ? 1 : 2, (uint64_t)Kp, (uint64_t)O, kblk, kChainBNSmall)))
                 return rc;
         }
     }

@@ -5,12 +5,14 @@
 namespace cbdfs {
 
 constexpr int kChainBN = 256;     // output columns of a tile (one TMEM accumulator)
+constexpr int kChainBNSmall = 64; // the same for small batches (more tiles in flight per layer)
+constexpr int kChainSmallMBlocks = 2;  // batches of at most this many 128-state row blocks
 constexpr int kChainStages = 4;
 constexpr int kChainThreads = 192;
 constexpr int kMaxHeadC = 32;     // widest last layer the in-epilogue head takes
 
 struct ChainMaps {
-    CUtensorMap w[kMaxLayers];  // weights of hidden layer l, [N][K] K-major
+    CUtensorMap w[kMaxLayers];  // weights of hidden layer l, [N][K] K-major, boxes of bn rows
     CUtensorMap a[kMaxLayers];  // A of hidden layer l: the one-hot rows (l = 0) or activations
     CUtensorMap o[kMaxLayers];  // activations written by hidden layer l (32 x 32 store boxes)
 };
@@ -52,6 +54,8 @@ struct ChainParams {
     int trace_tiles;
 };
 
-int chain_launch(int domain, bool fp8, const ChainMaps &maps, const ChainParams &P, int grid, cudaStream_t st);
+// bn: kChainBN, or kChainBNSmall (maps.w with 64-row boxes)
+int chain_launch(int domain, bool fp8, int bn, const ChainMaps &maps, const ChainParams &P, int grid,
+                 cudaStream_t st);
 
 }  // namespace cbdfs

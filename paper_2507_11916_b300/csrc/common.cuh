@@ -61,7 +61,8 @@ struct NetGPU {
     void *w_lp[kMaxLayers] = {};
     float w_scale[kMaxLayers] = {};    // FP8: weight scale per layer (1 for BF16)
     float a_scale[kMaxLayers] = {};    // FP8: activation scale of layer l's OUTPUT
-    CUtensorMap tm_w[kMaxLayers];      // TMA maps of w_lp
+    CUtensorMap tm_w[kMaxLayers];      // TMA maps of w_lp (k-block x bn rows)
+    CUtensorMap tm_w64[kMaxLayers];    // the same with 64-row boxes (small-batch chain tiles)
     int bn[kMaxLayers] = {};           // N tile per layer
     // FP32 weights for every layer (the FP32 path; the last layer for every path)
     float *w32[kMaxLayers] = {};

@@ -42,7 +42,6 @@ namespace {
 using namespace dev;
 
 constexpr int kStageA = kBM * 128;
-constexpr int kStageB = kChainBN * 128;
 constexpr int kStagingWarp = 2 * 32 * 64;   // two 32-row x 64-byte boxes per epilogue warp
 constexpr int kStaging = 4 * kStagingWarp;
 constexpr int kBiasSmem = 2 * kChainBN * 4;  // the tile's biases, double-buffered
@@ -191,18 +190,21 @@ __device__ __forceinline__ void finish_row(const ChainParams &P, uint32_t row_g,
     }
 }
 
-template <int DOMAIN, bool FP8, int CMAX>
+// BN: outputs of a tile (one TMEM accumulator); STAGES: depth of the (A, B) k-block ring
+template <int DOMAIN, bool FP8, int CMAX, int BN, int STAGES>
 __global__ void __launch_bounds__(kChainThreads, 1)
 k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainParams P) {
+    constexpr int kStageB = BN * 128;
+    constexpr int HS = BN < 128 ? BN : 128;  // columns of a last-layer slice in shared memory
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *A = smem;
-    uint8_t *B = smem + kChainStages * kStageA;
-    uint8_t *stg = B + kChainStages * kStageB;  // epilogue staging: 4 warps x 2 x 2 KB
+    uint8_t *B = smem + STAGES * kStageA;
+    uint8_t *stg = B + STAGES * kStageB;  // epilogue staging: 4 warps x 2 x 2 KB
     float *bsm = reinterpret_cast<float *>(stg + kStaging);  // [2][256] tile biases
     uint64_t *bars = reinterpret_cast<uint64_t *>(stg + kStaging + kBiasSmem);
-    uint64_t *full = bars, *empty = bars + kChainStages;
-    uint64_t *acc_full = bars + 2 * kChainStages, *acc_empty = acc_full + 2;
+    uint64_t *full = bars, *empty = bars + STAGES;
+    uint64_t *acc_full = bars + 2 * STAGES, *acc_empty = acc_full + 2;
     uint64_t *drain = acc_empty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
     int *flag = reinterpret_cast<int *>(tmem_slot + 1);
@@ -212,7 +214,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
     const int last_l = P.fused_head ? P.nh - 1 : P.nh;  // the layer whose epilogue runs the head
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kChainStages; ++s) {
+        for (int s = 0; s < STAGES; ++s) {
             mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
         }
@@ -230,7 +232,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
         }
     }
     if (warp == 1) {
-        tmem_alloc(smem_u32(tmem_slot), 512);
+        tmem_alloc(smem_u32(tmem_slot), 2 * BN);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -295,9 +297,9 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
             fence_proxy_async_global();
             if (lane == 0) stamp(P, pi, 1);
             for (int kb = 0; kb < KB; ++kb, ++it) {
-                const int s = it % kChainStages;
-                const uint32_t u = it / kChainStages;
-                if (it >= kChainStages) {
+                const int s = it % STAGES;
+                const uint32_t u = it / STAGES;
+                if (it >= STAGES) {
                     bool w = true;
                     if (lane == 0) w = mbar_wait(smem_u32(&empty[s]), (u - 1) & 1, P.err, DEVERR_STAGE_EMPTY);
                     w = __shfl_sync(0xFFFFFFFFu, w, 0);
@@ -308,7 +310,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                     tma_load_2d(smem_u32(A + s * kStageA), &maps.a[T.l], smem_u32(&full[s]), kb * KBLK,
                                 T.m * kBM);
                     tma_load_2d(smem_u32(B + s * kStageB), &maps.w[T.l], smem_u32(&full[s]), kb * KBLK,
-                                T.n * kChainBN);
+                                T.n * BN);
                 }
                 __syncwarp();
             }
@@ -316,15 +318,15 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
         }
         // every TMA load this CTA issued has landed before the CTA can exit (bounded)
         if (lane == 0) {
-            const uint32_t first = it > kChainStages ? it - kChainStages : 0;
+            const uint32_t first = it > STAGES ? it - STAGES : 0;
             for (uint32_t j = first; j < it; ++j)
-                mbar_wait(smem_u32(&full[j % kChainStages]), (j / kChainStages) & 1, P.err,
+                mbar_wait(smem_u32(&full[j % STAGES]), (j / STAGES) & 1, P.err,
                           DEVERR_TMA_FULL, 100000000ull);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = FP8 ? make_idesc(kBM, kChainBN, 0, 0) : make_idesc(kBM, kChainBN, 1, 1);
+            constexpr uint32_t idesc = FP8 ? make_idesc(kBM, BN, 0, 0) : make_idesc(kBM, BN, 1, 1);
             uint32_t it = 0, i = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
@@ -334,10 +336,10 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                 if (i >= 2 && !mbar_wait(smem_u32(&acc_empty[b]), (u - 1) & 1, P.err, DEVERR_ACCUM)) break;
                 tc_fence_after();
                 stamp(P, i, 3);
-                const uint32_t d = tmem + b * kChainBN;
+                const uint32_t d = tmem + b * BN;
                 for (int kb = 0; kb < KB; ++kb, ++it) {
-                    const int s = it % kChainStages;
-                    if (!mbar_wait(smem_u32(&full[s]), (it / kChainStages) & 1, P.err, DEVERR_TMA_FULL)) {
+                    const int s = it % STAGES;
+                    if (!mbar_wait(smem_u32(&full[s]), (it / STAGES) & 1, P.err, DEVERR_TMA_FULL)) {
                         ok = false;
                         break;
                     }
@@ -370,17 +372,16 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
             // the tile's biases into shared memory while the MMAs run (buffer i & 1 was last
             // read two tiles ago, before everyone passed the previous tile's barrier)
             float *bt = bsm + (i & 1) * kChainBN;
-            bt[2 * ep_tid] = __ldg(P.bias[T.l] + T.n * kChainBN + 2 * ep_tid);
-            bt[2 * ep_tid + 1] = __ldg(P.bias[T.l] + T.n * kChainBN + 2 * ep_tid + 1);
+            for (int j = ep_tid; j < BN; j += 128) bt[j] = __ldg(P.bias[T.l] + T.n * BN + j);
             epi_bar();
             // after a failed wait the warps skip the work but keep every barrier, so that
             // the four epilogue warps stay in step
             const bool good = mbar_wait(smem_u32(&acc_full[b]), u & 1, P.err, DEVERR_ACCUM);
             tc_fence_after();
             if (ep_tid == 0) stamp(P, i, 5);
-            const uint32_t taddr = tmem + b * kChainBN + ((uint32_t)(q * 32) << 16);
+            const uint32_t taddr = tmem + b * BN + ((uint32_t)(q * 32) << 16);
             const uint32_t rg = T.m * kBM + row;
-            const int n0 = T.n * kChainBN;
+            const int n0 = T.n * BN;
             const float *bias = bt;  // shared memory
             const float sc = P.acc_scale[T.l];
             if (T.l < last_l) {
@@ -388,7 +389,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                 const float oq = P.out_qscale[T.l];
                 uint8_t *wstg = stg + q * kStagingWarp;
 #pragma unroll 1
-                for (int c2 = 0; c2 < kChainBN / 32 && good; c2 += 2) {
+                for (int c2 = 0; c2 < BN / 32 && good; c2 += 2) {
                     uint32_t ra[2][32];
                     tmem_ld32(taddr + c2 * 32, ra[0]);
                     tmem_ld32(taddr + (c2 + 1) * 32, ra[1]);
@@ -467,16 +468,16 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
 #pragma unroll
                 for (int c = 0; c < CMAX; ++c) acc[c] = 0.f;
                 const int K = P.dims[T.l + 1];
-                float *wsm = reinterpret_cast<float *>(stg);  // [C][128] slice of the last layer
+                float *wsm = reinterpret_cast<float *>(stg);  // [C][HS] slice of the last layer
 #pragma unroll 1
-                for (int half = 0; half < 2; ++half) {
+                for (int half = 0; half < BN / HS; ++half) {
                     epi_bar();  // the previous slice has been read
 #pragma unroll 8
-                    for (int idx = ep_tid; idx < P.C * 128; idx += 128)
-                        wsm[idx] = __ldg(P.w_last + (size_t)(idx >> 7) * K + n0 + half * 128 + (idx & 127));
+                    for (int idx = ep_tid; idx < P.C * HS; idx += 128)
+                        wsm[idx] = __ldg(P.w_last + (size_t)(idx / HS) * K + n0 + half * HS + idx % HS);
                     epi_bar();
 #pragma unroll 1
-                    for (int c = half * 4; c < half * 4 + 4 && good; ++c) {
+                    for (int c = half * (HS / 32); c < (half + 1) * (HS / 32) && good; ++c) {
                         uint32_t r[32];
                         tmem_ld32(taddr + c * 32, r);
                         tmem_ld_wait();
@@ -486,11 +487,11 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
 #pragma unroll
                             for (int jj = 0; jj < 4; ++jj)
                                 v[jj] = fmaxf(fmaf(__uint_as_float(r[j + jj]), sc, bias[c * 32 + j + jj]), 0.f);
-                            const float *wj = wsm + (c - half * 4) * 32 + j;
+                            const float *wj = wsm + (c - half * (HS / 32)) * 32 + j;
 #pragma unroll
                             for (int o = 0; o < CMAX; ++o) {
                                 if (o < P.C) {  // predicated: the loop stays unrolled, acc in registers
-                                    const float4 w4 = *reinterpret_cast<const float4 *>(wj + o * 128);
+                                    const float4 w4 = *reinterpret_cast<const float4 *>(wj + o * HS);
                                     acc[o] = fmaf(v[0], w4.x, fmaf(v[1], w4.y, fmaf(v[2], w4.z, fmaf(v[3], w4.w, acc[o]))));
                                 }
                             }
@@ -535,7 +536,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, 512);
+        tmem_dealloc(tmem, 2 * BN);
     }
     // the last CTA to finish (none polls a counter any more) leaves the counters zeroed for
     // the next launch on this slot
@@ -556,7 +557,8 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
 
 }  // namespace
 
-size_t chain_smem_bytes() { return 1024 + kChainStages * (kStageA + kStageB) + kStaging + kBiasSmem + 256; }
+template <int BN, int STAGES>
+static size_t chain_smem_bytes() { return 1024 + STAGES * (kStageA + BN * 128) + kStaging + kBiasSmem + 256; }
 
 // the kernel's dynamic shared-memory limit, raised once per kernel and device
 static int allow_smem(const void *kern, size_t smem) {
@@ -573,11 +575,13 @@ static int allow_smem(const void *kern, size_t smem) {
 
 // Launch the chain for one batch.  P.counters must be zero (they are after the previous
 // launch on the same counters, and after allocation).
-template <int D, bool F>
+template <int D, bool F, int BN, int STAGES>
 static int launch_t(const ChainMaps &maps, const ChainParams &P, int grid, cudaStream_t st) {
-    const size_t smem = chain_smem_bytes();
+    const size_t smem = chain_smem_bytes<BN, STAGES>();
     void (*kern)(const ChainMaps, const ChainParams) =
-        P.C == 1 || !P.fused_head ? k_chain<D, F, 1> : P.C <= 24 ? k_chain<D, F, 24> : k_chain<D, F, kMaxHeadC>;
+        P.C == 1 || !P.fused_head ? k_chain<D, F, 1, BN, STAGES>
+        : P.C <= 24              ? k_chain<D, F, 24, BN, STAGES>
+                                 : k_chain<D, F, kMaxHeadC, BN, STAGES>;
     if (int rc = allow_smem(reinterpret_cast<const void *>(kern), smem)) return rc;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -593,16 +597,24 @@ static int launch_t(const ChainMaps &maps, const ChainParams &P, int grid, cudaS
     return CBDFS_OK;
 }
 
-int chain_launch(int domain, bool fp8, const ChainMaps &maps, const ChainParams &P, int grid, cudaStream_t st) {
-    if (P.fused_head && (P.C < 1 || P.C > kMaxHeadC)) return fail(CBDFS_EINVAL, "fused head width %d", P.C);
+template <int BN, int STAGES>
+static int launch_bn(int domain, bool fp8, const ChainMaps &maps, const ChainParams &P, int grid, cudaStream_t st) {
     if (fp8) {
-        if (domain == CBDFS_DOM_STP3) return launch_t<CBDFS_DOM_STP3, true>(maps, P, grid, st);
-        if (domain == CBDFS_DOM_STP4) return launch_t<CBDFS_DOM_STP4, true>(maps, P, grid, st);
-        return launch_t<CBDFS_DOM_RC3, true>(maps, P, grid, st);
+        if (domain == CBDFS_DOM_STP3) return launch_t<CBDFS_DOM_STP3, true, BN, STAGES>(maps, P, grid, st);
+        if (domain == CBDFS_DOM_STP4) return launch_t<CBDFS_DOM_STP4, true, BN, STAGES>(maps, P, grid, st);
+        return launch_t<CBDFS_DOM_RC3, true, BN, STAGES>(maps, P, grid, st);
     }
-    if (domain == CBDFS_DOM_STP3) return launch_t<CBDFS_DOM_STP3, false>(maps, P, grid, st);
-    if (domain == CBDFS_DOM_STP4) return launch_t<CBDFS_DOM_STP4, false>(maps, P, grid, st);
-    return launch_t<CBDFS_DOM_RC3, false>(maps, P, grid, st);
+    if (domain == CBDFS_DOM_STP3) return launch_t<CBDFS_DOM_STP3, false, BN, STAGES>(maps, P, grid, st);
+    if (domain == CBDFS_DOM_STP4) return launch_t<CBDFS_DOM_STP4, false, BN, STAGES>(maps, P, grid, st);
+    return launch_t<CBDFS_DOM_RC3, false, BN, STAGES>(maps, P, grid, st);
+}
+
+int chain_launch(int domain, bool fp8, int bn, const ChainMaps &maps, const ChainParams &P, int grid,
+                 cudaStream_t st) {
+    if (P.fused_head && (P.C < 1 || P.C > kMaxHeadC)) return fail(CBDFS_EINVAL, "fused head width %d", P.C);
+    if (bn == kChainBNSmall) return launch_bn<kChainBNSmall, 8>(domain, fp8, maps, P, grid, st);
+    if (bn == kChainBN) return launch_bn<kChainBN, kChainStages>(domain, fp8, maps, P, grid, st);
+    return fail(CBDFS_EINVAL, "chain tile width %d", bn);
 }
 
 }  // namespace cbdfs
