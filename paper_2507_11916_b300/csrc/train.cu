@@ -37,6 +37,8 @@ namespace {
 using namespace dev;
 
 constexpr int kThreads = 192;
+constexpr int kDwRows = 512;   // rows of one split of the last layer's dW
+constexpr int kSumRows = 256;  // rows of one chunk of a column sum
 constexpr int kStageA = kBM * 128;
 
 // ---------------------------------------------------------------------------------------
@@ -197,20 +199,6 @@ __global__ void k_onehot_t(const uint64_t *__restrict__ states, uint32_t n, int 
     }
 }
 
-// logits[m][c] = sum_k A[m][k] W[c][k] + b[c] (A BF16, W FP32), one warp per row
-__global__ void k_logits(const __nv_bfloat16 *__restrict__ A, int K, int C, const float *__restrict__ W,
-                         const float *__restrict__ b, int n, float *__restrict__ logits) {
-    const int m = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (m >= n) return;
-    const __nv_bfloat16 *a = A + (size_t)m * K;
-    for (int c = 0; c < C; ++c) {
-        float part = 0.f;
-        for (int k = lane; k < K; k += 32) part = fmaf(__bfloat162float(a[k]), __ldg(W + (size_t)c * K + k), part);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
-        if (lane == 0) logits[(size_t)m * C + c] = part + __ldg(b + c);
-    }
-}
 
 // loss and dZ = dLoss/dlogits (mean over n rows).  loss 0: softmax cross-entropy against
 // the class index; loss 1: 0.5 (y - label)^2 on one output.  Per-row losses to row_loss.
@@ -238,38 +226,91 @@ __global__ void k_loss(const float *__restrict__ logits, const uint8_t *__restri
     }
 }
 
-// dZ_prev[m][k] = (sum_c dZ[m][c] W[c][k]) * [A[m][k] > 0], BF16 out; rows >= n zero
-__global__ void k_back_last(const float *__restrict__ dz, int C, const float *__restrict__ W, int K,
-                            const __nv_bfloat16 *__restrict__ A, int n, int Bp, __nv_bfloat16 *__restrict__ out) {
-    const int m = blockIdx.y;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K || m >= Bp) return;
-    float s = 0.f;
-    if (m < n) {
-        for (int c = 0; c < C; ++c) s = fmaf(dz[(size_t)m * C + c], __ldg(W + (size_t)c * K + k), s);
-        if (!(__bfloat162float(A[(size_t)m * K + k]) > 0.f)) s = 0.f;
+
+
+
+// ---- FP32 GEMM on the CUDA cores (the last layer's products) ----------------------------
+// out[z][m][n] = sum over k in split z of A(m,k) B(k,n), FP32: A(m,k) = A[m*sam + k*sak],
+// B(k,n) = B[k*sbk + n*sbn].  64x64 tiles, k-steps of 16, 256 threads each owning a 4x4 block.
+// AK: A is contiguous along k (else along m); BNC: B is contiguous along n (else along k).
+// EPI 0: write split z's partial sums; 1: write + bias[n] (one split); 2: write BF16
+// acc * [mask[m][n] > 0], zero for rows m >= nvalid (one split).
+constexpr int FG_T = 64, FG_BK = 16;
+__device__ __forceinline__ float tof(float x) { return x; }
+__device__ __forceinline__ float tof(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <typename TA, typename TB, bool AK, bool BNC, int EPI>
+__global__ void __launch_bounds__(256)
+k_fgemm(const TA *__restrict__ A, long sam, long sak, const TB *__restrict__ B, long sbk, long sbn, int M,
+        int N, int K, int kchunk, float *__restrict__ out, const float *__restrict__ bias,
+        const __nv_bfloat16 *__restrict__ mask, int nvalid, __nv_bfloat16 *__restrict__ out16) {
+    __shared__ __align__(16) float As[FG_BK][FG_T];
+    __shared__ __align__(16) float Bs[FG_BK][FG_T];
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int m0 = blockIdx.y * FG_T, n0 = blockIdx.x * FG_T;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k0 = kb; k0 < ke; k0 += FG_BK) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            // A: 64 (m) x 16 (k), 4 values per thread along the contiguous index
+            const int am = AK ? (tid >> 2) : ((tid & 15) * 4 + j), ak = AK ? ((tid & 3) * 4 + j) : (tid >> 4);
+            const int gm = m0 + am, gk = k0 + ak;
+            As[ak][am] = (gm < M && gk < ke) ? tof(A[(size_t)gm * sam + (size_t)gk * sak]) : 0.f;
+            // B: 16 (k) x 64 (n)
+            const int bn = BNC ? ((tid & 15) * 4 + j) : (tid >> 2), bk = BNC ? (tid >> 4) : ((tid & 3) * 4 + j);
+            const int gn = n0 + bn, gk2 = k0 + bk;
+            Bs[bk][bn] = (gn < N && gk2 < ke) ? tof(B[(size_t)gk2 * sbk + (size_t)gn * sbn]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < FG_BK; ++k) {
+            const float4 a = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
     }
-    out[(size_t)m * K + k] = __float2bfloat16(s);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
+            if (m >= M || n >= N) continue;
+            const size_t o = (size_t)m * N + n;
+            if (EPI == 0) out[(size_t)blockIdx.z * M * N + o] = acc[i][j];
+            else if (EPI == 1) out[o] = acc[i][j] + bias[n];
+            else out16[o] = __float2bfloat16(m < nvalid && __bfloat162float(mask[o]) > 0.f ? acc[i][j] : 0.f);
+        }
 }
 
-// dW[c][k] = sum_m dZ[m][c] A[m][k] (FP32, fixed order over m)
-__global__ void k_dw_last(const float *__restrict__ dz, int C, const __nv_bfloat16 *__restrict__ A, int K, int n,
-                          float *__restrict__ dw) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x, c = blockIdx.y;
-    if (k >= K) return;
+// out[i] = sum over z of part[z][i] (+ bias), in split order
+__global__ void k_sum_splits(const float *__restrict__ part, int S, int len, float *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
     float s = 0.f;
-    for (int m = 0; m < n; ++m) s = fmaf(dz[(size_t)m * C + c], __bfloat162float(A[(size_t)m * K + k]), s);
-    dw[(size_t)c * K + k] = s;
+    for (int z = 0; z < S; ++z) s += part[(size_t)z * len + i];
+    out[i] = s;
 }
 
-// column sums: out[j] = sum_m X[m][j] over m < n (FP32 or BF16 X), fixed order
+// column sums by row chunks: part[r][j] = sum of X[m][j] over m in chunk r (fixed order);
+// k_sum_splits then adds the chunks in order
 template <typename T>
-__global__ void k_colsum(const T *__restrict__ X, int n, int J, float *__restrict__ out) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_colsum_part(const T *__restrict__ X, int n, int J, int chunk, float *__restrict__ part) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
     if (j >= J) return;
+    const int mb = r * chunk, me = min(n, mb + chunk);
     float s = 0.f;
-    for (int m = 0; m < n; ++m) s += (float)X[(size_t)m * J + j];
-    out[j] = s;
+    for (int m = mb; m < me; ++m) s += tof(X[(size_t)m * J + j]);
+    part[(size_t)r * J + j] = s;
 }
 
 // sum of per-row losses (one block, fixed order), divided by n
@@ -382,6 +423,8 @@ struct TrainState {
     __nv_bfloat16 *dz[kMaxLayers] = {};                    // dZ_l BF16 [Bp][dims[l+1]]
     __nv_bfloat16 *t_dz = nullptr, *t_a = nullptr;         // transposes (largest)
     float *logits = nullptr, *dzl = nullptr, *row_loss = nullptr, *loss = nullptr;
+    float *red = nullptr;                                  // split / row-chunk partial sums
+    size_t red_floats = 0;
     uint64_t *states = nullptr;
     uint8_t *labels = nullptr;
     int64_t step = 0;
@@ -452,6 +495,13 @@ static int train_setup(Ctx *c, NetGPU &net, int B, const float *const *host_w, c
         if (!rc) rc = talloc(c, *T, (void **)&T->logits, (size_t)Bp * C * 4);
         if (!rc) rc = talloc(c, *T, (void **)&T->dzl, (size_t)Bp * C * 4);
         if (!rc) rc = talloc(c, *T, (void **)&T->row_loss, (size_t)Bp * 4);
+        {
+            // partials: the last layer's dW in row splits, and column sums in row chunks
+            const size_t KL = net.dims[L - 1];
+            T->red_floats = std::max((size_t)((Bp + kDwRows - 1) / kDwRows) * C * KL,
+                                     (size_t)((Bp + kSumRows - 1) / kSumRows) * std::max(maxw, (size_t)C));
+            if (!rc) rc = talloc(c, *T, (void **)&T->red, T->red_floats * 4);
+        }
         if (!rc) rc = talloc(c, *T, (void **)&T->loss, 4);
         if (!rc) rc = talloc(c, *T, (void **)&T->states, (size_t)Bp * 16);
         if (!rc) rc = talloc(c, *T, (void **)&T->labels, (size_t)Bp);
@@ -492,6 +542,17 @@ static int train_setup(Ctx *c, NetGPU &net, int B, const float *const *host_w, c
 }
 
 // forward + loss + backward on the batch already in T.states / T.labels (n rows)
+// out[j] = sum of X[m][j] over m < n, by row chunks then chunks in order (deterministic)
+template <typename T>
+static int colsum(TrainState &S, const T *X, int n, int J, float *out, cudaStream_t st) {
+    const int R = (n + kSumRows - 1) / kSumRows;
+    if ((size_t)R * J > S.red_floats) return fail(CBDFS_EINVAL, "column-sum scratch");
+    k_colsum_part<T><<<dim3((J + 255) / 256, R), 256, 0, st>>>(X, n, J, kSumRows, S.red);
+    k_sum_splits<<<(J + 255) / 256, 256, 0, st>>>(S.red, R, J, out);
+    CUDA_TRY(cudaGetLastError());
+    return CBDFS_OK;
+}
+
 static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t st) {
     TrainState &T = *net.train;
     const int L = net.L, C = net.dims[L];
@@ -508,14 +569,21 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
         if (rc) return rc;
     }
     const int KL = net.dims[L - 1];
-    k_logits<<<(n + 7) / 8, 256, 0, st>>>(T.act[L - 2], KL, C, T.w[L - 1], T.b[L - 1], n, T.logits);
+    const dim3 blk(256);
+    // logits[m][c] = sum_k A[m][k] W[c][k] + b[c]
+    k_fgemm<__nv_bfloat16, float, true, false, 1><<<dim3((C + FG_T - 1) / FG_T, (n + FG_T - 1) / FG_T, 1), blk, 0, st>>>(
+        T.act[L - 2], KL, 1, T.w[L - 1], 1, KL, n, C, KL, KL, T.logits, T.b[L - 1], nullptr, 0, nullptr);
     k_loss<<<(n + 255) / 256, 256, 0, st>>>(T.logits, T.labels, n, C, loss_kind, T.dzl, T.row_loss);
     k_mean<<<1, 256, 0, st>>>(T.row_loss, n, T.loss);
-    // last layer backward (FP32)
-    k_dw_last<<<dim3((KL + 255) / 256, C), 256, 0, st>>>(T.dzl, C, T.act[L - 2], KL, n, T.gw[L - 1]);
-    k_colsum<float><<<(C + 255) / 256, 256, 0, st>>>(T.dzl, n, C, T.gb[L - 1]);
-    k_back_last<<<dim3((KL + 255) / 256, Bp), 256, 0, st>>>(T.dzl, C, T.w[L - 1], KL, T.act[L - 2], n, Bp,
-                                                            T.dz[L - 2]);
+    // last layer backward (FP32): dW[c][k] = sum_m dZ[m][c] A[m][k] in row splits, then the
+    // splits in order; db = column sums of dZ; dZ_prev = (dZ W) * [A > 0] in BF16
+    const int sdw = (n + kDwRows - 1) / kDwRows;
+    k_fgemm<float, __nv_bfloat16, false, true, 0><<<dim3((KL + FG_T - 1) / FG_T, (C + FG_T - 1) / FG_T, sdw), blk, 0, st>>>(
+        T.dzl, 1, C, T.act[L - 2], KL, 1, C, KL, n, kDwRows, T.red, nullptr, nullptr, 0, nullptr);
+    k_sum_splits<<<(C * KL + 255) / 256, 256, 0, st>>>(T.red, sdw, C * KL, T.gw[L - 1]);
+    if (int r = colsum(T, T.dzl, n, C, T.gb[L - 1], st)) return r;
+    k_fgemm<float, float, true, true, 2><<<dim3((KL + FG_T - 1) / FG_T, Bp / FG_T, 1), blk, 0, st>>>(
+        T.dzl, C, 1, T.w[L - 1], KL, 1, Bp, KL, C, C, nullptr, nullptr, T.act[L - 2], n, T.dz[L - 2]);
     // hidden layers, last to first
     for (int l = L - 2; l >= 0; --l) {
         const int O = net.dims[l + 1], I = l == 0 ? net.k1pad : net.dims[l];
@@ -537,7 +605,7 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
         rc = (I % 256 == 0) ? gemm_tn<256, 1>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st)
                             : gemm_tn<128, 1>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st);
         if (rc) return rc;
-        k_colsum<__nv_bfloat16><<<(O + 255) / 256, 256, 0, st>>>(T.dz[l], n, O, T.gb[l]);
+        if (int r = colsum(T, T.dz[l], n, O, T.gb[l], st)) return r;
         if (l > 0) {
             // dZ_{l-1} = (dZ_l W_l) * [A_{l-1} > 0]
             const CUtensorMap *mz = bmap(T, T.dz[l], O, T.Bp, kBM);
