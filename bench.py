@@ -190,7 +190,7 @@ def run_reference(args):
         "e2e": {"value": v, "unit": "states/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
-def search_rates(P, ctx, hids, seconds, work_num=256):
+def search_rates(P, ctx, hids, seconds, work_num=1024):
     """IDA* nodes/s with the network heuristic in each precision at equal solution cost.
 
     fixed_tree: Manhattan distance prunes and the network is evaluated on every generated node
@@ -430,6 +430,140 @@ def pdb_leg(P, args):
     return out
 
 
+def networks_leg(P, args):
+    """States/s of every workload network in each precision it runs in, at the batch size of
+    its configuration (8-puzzle 256, 15-puzzle 8192, cube 4096, 81-class 8192): one
+    graph-replayed evaluation (states resident in HBM, L2 flushed before each), event-timed."""
+    import torch
+    dev = torch.device("cuda", 0)
+    out = {}
+    ctx = P.cbdfs_create(0, max_batch=8192, n_slots=1)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(dev)
+    try:
+        cases = [("8-puzzle 81-256-256-1", W.NET_C0, P.DOM_STP3, P.HEAD_REGRESSION, 1, 256, ["fp32"]),
+                 ("15-puzzle 256-1024-1024-512-1", W.NET_C1, P.DOM_STP4, P.HEAD_REGRESSION, 1, 8192, ["bf16", "fp8", "fp32"]),
+                 ("cube 480-2048-2048-1024-21", W.NET_C2, P.DOM_RC3, P.HEAD_CLASSIFIER, 0, 4096, ["bf16", "fp8", "fp32"]),
+                 ("15-puzzle 81-class 256-1024-1024-512-81", W.NET_C3, P.DOM_STP4, P.HEAD_CLASSIFIER, 1, 8192, ["bf16", "fp8", "fp32"])]
+        for name, cfg, dom, head, md, B, precs in cases:
+            Ws, bs = W.net_weights(**cfg)
+            if dom == P.DOM_RC3:
+                states = W.random_rc_states(B, 77).reshape(-1)
+            else:
+                states = W.random_stp_states(3 if dom == P.DOM_STP3 else 4, B, 77)
+            ds = torch.from_numpy(states.view(np.int64)).to(dev)
+            dg = torch.zeros(B, dtype=torch.uint8, device=dev)
+            dh = torch.empty(B, dtype=torch.uint8, device=dev)
+            dm = torch.empty((B + 31) // 32, dtype=torch.int32, device=dev)
+            dmin = torch.empty(1, dtype=torch.int32, device=dev)
+            row = {"batch": B}
+            for prec in precs:
+                kw = {}
+                if prec == "fp8":
+                    kw["act_scales"] = calib_scales(Ws, bs, dom)
+                hid = P.cbdfs_net_load(ctx, dom, Ws, bs, {"fp32": P.PREC_FP32, "bf16": P.PREC_BF16, "fp8": P.PREC_FP8}[prec],
+                                       head, md, **kw)
+                with torch.cuda.stream(stream):
+                    for _ in range(3):
+                        P.heur_eval_device(ctx, hid, dom, ds, dg, 50, B, dh, dm, dmin, stream=stream)
+                stream.synchronize()
+                gr = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(gr, stream=stream):
+                    P.heur_eval_device(ctx, hid, dom, ds, dg, 50, B, dh, dm, dmin, stream=stream)
+                K = 50
+                e0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+                e1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+                with torch.cuda.stream(stream):
+                    for k in range(K):
+                        flush.zero_()
+                        e0[k].record(stream)
+                        gr.replay()
+                        e1[k].record(stream)
+                stream.synchronize()
+                ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / K
+                dims = cfg["dims"]
+                flops = 2 * B * sum(dims[l] * dims[l + 1] for l in range(len(dims) - 1))
+                row[prec] = {"states_per_s": B / (ms / 1e3), "ms": ms, "tflops": flops / (ms / 1e3) / 1e12}
+                del gr
+            out[name] = row
+        assert P.cbdfs_device_status(ctx) == 0
+    finally:
+        P.cbdfs_destroy(ctx)
+    return out
+
+
+def kernel_micro_leg(P, args):
+    """The fused chain for the 15-puzzle network (BF16 and E4M3) over batch sizes: states/s,
+    TFLOP/s and the fraction of the measured BF16 peak (E4M3 against twice it, the dense
+    FP8:BF16 ratio), event-timed per launch with the L2 flushed before each."""
+    import torch
+    dev = torch.device("cuda", 0)
+    sizes = [512, 2048, 8192, 65536, 262144]
+    out = {"network": "256-1024-1024-512-1", "sizes": {}}
+    ctx = P.cbdfs_create(0, max_batch=max(sizes), n_slots=1)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(dev)
+    pk = peaks()
+    try:
+        Ws, bs = W.net_weights(**W.NET_C1)
+        hids = {"bf16": P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, P.PREC_BF16, P.HEAD_REGRESSION, 1),
+                "fp8": P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, P.PREC_FP8, P.HEAD_REGRESSION, 1,
+                                        act_scales=calib_scales(Ws, bs, 1))}
+        states = W.random_stp_states(4, max(sizes), 5151)
+        ds = torch.from_numpy(states.view(np.int64)).to(dev)
+        dg = torch.zeros(max(sizes), dtype=torch.uint8, device=dev)
+        dh = torch.empty(max(sizes), dtype=torch.uint8, device=dev)
+        dm = torch.empty(max(sizes) // 32, dtype=torch.int32, device=dev)
+        dmin = torch.empty(1, dtype=torch.int32, device=dev)
+        dims = W.NET_C1["dims"]
+        for n in sizes:
+            row = {}
+            flops = 2 * n * sum(dims[l] * dims[l + 1] for l in range(len(dims) - 1))
+            for prec, hid in hids.items():
+                ts = []
+                for k in range(13):
+                    with torch.cuda.stream(stream):
+                        flush.zero_()
+                    t = P.cbdfs_eval_profile(ctx, hid, P.DOM_STP4, ds, dg, 50, n, dh, dm, dmin, stream=stream)
+                    if k >= 3:
+                        ts.append(sum(t))
+                ms = float(np.median(ts))
+                peak = pk["bf16"] * (2 if prec == "fp8" else 1)
+                row[prec] = {"states_per_s": n / (ms / 1e3), "launch_ms": ms, "tflops": flops / (ms / 1e3) / 1e12,
+                             "frac": flops / (ms / 1e3) / 1e12 / peak}
+            out["sizes"][n] = row
+        out["peak_source"] = f"{pk['src']} bf16 dense (burst); E4M3 against 2x"
+    finally:
+        P.cbdfs_destroy(ctx)
+    return out
+
+
+def calib_scales(Ws, bs, dom):
+    """Static E4M3 activation scales from a float32 host forward over 4096 calibration states
+    (calibration only; nothing timed runs on the host)."""
+    if dom == 2:  # cube
+        st = W.random_rc_states(4096, 4096)
+        X = np.zeros((4096, 480), np.float32)
+        for c in range(8):
+            X[np.arange(4096), c * 24 + ((st[:, 0] >> np.uint64(5 * c)) & np.uint64(31)).astype(np.int64)] = 1.0
+        for e in range(12):
+            X[np.arange(4096), 192 + e * 24 + ((st[:, 1] >> np.uint64(5 * e)) & np.uint64(31)).astype(np.int64)] = 1.0
+    else:
+        side = 3 if dom == 0 else 4
+        N = side * side
+        st = W.random_stp_states(side, 4096, 4096)
+        X = np.zeros((4096, N * N), np.float32)
+        for p in range(N):
+            t = ((st >> np.uint64(4 * p)) & np.uint64(15)).astype(np.int64)
+            X[np.arange(4096), t * N + p] = 1.0
+    a = X
+    sc = []
+    for l in range(len(Ws) - 1):
+        a = np.maximum(a @ Ws[l].T + bs[l], 0.0)
+        sc.append(max(float(a.max()), 1e-6) / 448.0)
+    return np.array(sc, np.float32)
+
+
 def fp8_scales(P, ctx, Ws, bs):
     """Static activation scales for E4M3 (an input of cbdfs_net_load): the largest activation
     of each hidden layer over 4096 calibration states, from a float32 host forward of the
@@ -601,6 +735,9 @@ def run_ours(args):
     if rank == 0 and not args.no_search:
         line["search"] = search_rates(P, ctx, {"bf16": hid, "fp8": hid8, "fp32": hid32}, args.search_seconds)
     P.cbdfs_destroy(ctx)
+    if rank == 0 and not args.no_nets:
+        line["networks"] = networks_leg(P, args)
+        line["kernel_micro"] = kernel_micro_leg(P, args)
     if rank == 0 and not args.no_pdb:
         line["pdb_gather"] = pdb_leg(P, args)
     if rank == 0 and not args.no_train:
@@ -624,6 +761,7 @@ def main():
     ap.add_argument("--no-train", action="store_true", help="skip the training leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-pdb", action="store_true", help="skip the PDB gather leg")
+    ap.add_argument("--no-nets", action="store_true", help="skip the per-network states/s leg")
     ap.add_argument("--pdb-states", type=int, default=1 << 22)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--search-seconds", type=float, default=3.0)
