@@ -153,7 +153,11 @@ int pdb_build(cbdfs_ctx *ctx, int domain, const int *pattern_tiles, int k, uint8
  * n = 0 is allowed (mask nothing, minf 0xFFFFFFFF).  n > max_batch: EINVAL.
  * ------------------------------------------------------------------------------------- */
 
-/* Host buffers; returns when the results are in h_out/mask_out/minf_out. */
+/* Host buffers; returns when the results are in h_out/mask_out/minf_out.  When states, g,
+ * h_out and mask_out are all page-locked (cudaMallocHost / cudaHostRegister) and y_out is
+ * NULL, the kernels read and write them in place over the bus (no staging copies); other
+ * buffers are copied through the slot's device staging.  The buffers must not change
+ * until the call returns. */
 int heur_submit_batch(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *states,
                       const uint8_t *g, uint32_t bound, uint32_t n, uint8_t *h_out,
                       uint32_t *mask_out, uint32_t *minf_out, float *y_out);

@@ -471,6 +471,7 @@ void cbdfs_destroy(cbdfs_ctx *ctx) {
         dev_free(c, s.partial, s.partial_bytes);
         if (s.stream) cudaStreamDestroy(s.stream);
         if (s.done) cudaEventDestroy(s.done);
+        if (s.h_small) cudaFreeHost(s.h_small);
     }
     for (auto &n : c->nets) {
         train_free(c, n->train);
@@ -523,6 +524,7 @@ int cbdfs_create(const cbdfs_config *cfg, cbdfs_ctx **out) {
             s.d_mask = reinterpret_cast<uint32_t *>(s.d_h + c->max_batch_pad);
             s.d_minf = s.d_mask + c->max_batch_pad / 32;
         }
+        if (!rc && cudaMallocHost(&s.h_small, 16) != cudaSuccess) rc = fail(CBDFS_ENOMEM, "pinned words");
     }
     if (rc) {
         cbdfs_destroy(reinterpret_cast<cbdfs_ctx *>(c));
@@ -733,6 +735,18 @@ int heur_eval_device(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_
     return rc;
 }
 
+// the device address of page-locked host memory (cudaMallocHost / cudaHostRegister), else false
+static bool host_mapped(const void *p, void **dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+    *dev = a.devicePointer;
+    return true;
+}
+
 int heur_submit_batch(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *states, const uint8_t *g,
                       uint32_t bound, uint32_t n, uint8_t *h_out, uint32_t *mask_out, uint32_t *minf_out,
                       float *y_out) {
@@ -765,26 +779,39 @@ int heur_submit_batch(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *s
     if (C) {
         rc = dev_alloc(c, (void **)&d_y, (size_t)n * C * 4 + 4);
     }
-    if (!rc && n) {
-        if (cudaMemcpyAsync(s.d_states, states, (size_t)n * 8 * w, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-            cudaMemcpyAsync(s.d_g, g, n, cudaMemcpyHostToDevice, st) != cudaSuccess)
-            rc = fail(CBDFS_EDEVICE, "batch upload");
+    // Page-locked caller buffers are read and written by the kernels in place (mapped host
+    // memory, over the bus inside the launch); other buffers go through the slot's device
+    // staging with copies.
+    void *zs = nullptr, *zg = nullptr, *zh = nullptr, *zm = nullptr;
+    const bool zero_copy = !rc && n && !C && host_mapped(states, &zs) && host_mapped(g, &zg) &&
+                           host_mapped(h_out, &zh) && host_mapped(mask_out, &zm);
+    if (zero_copy) {
+        rc = run_eval(c, s, heur_id, domain, static_cast<const uint64_t *>(zs), static_cast<const uint8_t *>(zg),
+                      bound, n, static_cast<uint8_t *>(zh), static_cast<uint32_t *>(zm), s.d_minf, nullptr, st);
+    } else {
+        if (!rc && n) {
+            if (cudaMemcpyAsync(s.d_states, states, (size_t)n * 8 * w, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                cudaMemcpyAsync(s.d_g, g, n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+                rc = fail(CBDFS_EDEVICE, "batch upload");
+        }
+        if (!rc) rc = run_eval(c, s, heur_id, domain, s.d_states, s.d_g, bound, n, s.d_h, s.d_mask, s.d_minf, d_y, st);
+        if (!rc) {
+            if ((n && (cudaMemcpyAsync(h_out, s.d_h, n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                       cudaMemcpyAsync(mask_out, s.d_mask, (size_t)(n + 31) / 32 * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)) ||
+                (C && cudaMemcpyAsync(y_out, d_y, (size_t)n * C * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess))
+                rc = fail(CBDFS_EDEVICE, "result download");
+        }
     }
-    if (!rc) rc = run_eval(c, s, heur_id, domain, s.d_states, s.d_g, bound, n, s.d_h, s.d_mask, s.d_minf, d_y, st);
-    if (!rc) {
-        if ((n && (cudaMemcpyAsync(h_out, s.d_h, n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                   cudaMemcpyAsync(mask_out, s.d_mask, (size_t)(n + 31) / 32 * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)) ||
-            cudaMemcpyAsync(minf_out, s.d_minf, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            (C && cudaMemcpyAsync(y_out, d_y, (size_t)n * C * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess))
-            rc = fail(CBDFS_EDEVICE, "result download");
-    }
+    // the least f above the bound and the device error flag, read in stream order
+    if (!rc && (cudaMemcpyAsync(s.h_small, s.d_minf, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaMemcpyAsync(s.h_small + 1, c->d_err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess))
+        rc = fail(CBDFS_EDEVICE, "result download");
     cudaError_t e = cudaStreamSynchronize(st);
     if (!rc && e != cudaSuccess) rc = fail(CBDFS_EDEVICE, "evaluation: %s", cudaGetErrorString(e));
     if (d_y) dev_free(c, d_y, (size_t)n * C * 4 + 4);
     if (!rc) {
-        int flag = 0;
-        if (cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && flag)
-            rc = fail(CBDFS_ETIMEDOUT, "a device wait ran out (code %d)", flag);
+        *minf_out = s.h_small[0];
+        if (s.h_small[1]) rc = fail(CBDFS_ETIMEDOUT, "a device wait ran out (code %d)", (int)s.h_small[1]);
     }
     {
         std::lock_guard<std::mutex> lk(c->slot_mu);

@@ -89,6 +89,7 @@ struct Slot {
     uint8_t *d_g = nullptr, *d_h = nullptr;
     uint32_t *d_mask = nullptr, *d_minf = nullptr;
     float *d_y = nullptr;
+    uint32_t *h_small = nullptr;       // pinned host words: [0] minf, [1] the device error flag
     // TMA maps of the activation buffers, keyed by (buffer, width, dtype bytes)
     std::map<long long, CUtensorMap> tm_act;
     cudaEvent_t done = nullptr;
