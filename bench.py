@@ -750,6 +750,44 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def profile_case(P, args):
+    """A small case for ncu: four launches of one kernel, each after a 512 MB L2 flush, on the
+    default stream; the third is the one a capture with `-s 2 -c 1` takes.
+      chain  -- the 15-puzzle regression network (Kaiming, seed 1) in BF16, regression head with
+                the Manhattan max, on --profile-states random states (k_chain);
+      pdb78  -- the 7-8 partition with tables of the real sizes (57,657,600 + 518,918,400 bytes;
+                content does not change the access pattern) on --profile-states states
+                (k_pdb_gather)."""
+    import torch
+    n = args.profile_states
+    ctx = P.cbdfs_create(0, max_batch=n, n_slots=1)
+    try:
+        if args.profile_case == "chain":
+            Ws, bs = W.net_weights(**W.NET_C1)
+            hid = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, P.PREC_BF16, P.HEAD_REGRESSION, 1)
+        else:
+            tabs = [np.full(57_657_600, 9, np.uint8), np.full(518_918_400, 11, np.uint8)]
+            hid = P.cbdfs_pdb_load(ctx, P.DOM_STP4, W.PATTERNS_78, tabs)
+            del tabs
+        dev = torch.device("cuda", 0)
+        states = W.random_stp_states(4, n, 1)
+        ds = torch.from_numpy(states.view(np.int64)).to(dev)
+        dg = torch.zeros(n, dtype=torch.uint8, device=dev)
+        dh = torch.empty(n, dtype=torch.uint8, device=dev)
+        dm = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
+        dmin = torch.empty(1, dtype=torch.int32, device=dev)
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+        st = torch.cuda.current_stream()
+        for _ in range(4):
+            flush.zero_()
+            t = P.cbdfs_eval_profile(ctx, hid, P.DOM_STP4, ds, dg, BOUND, n, dh, dm, dmin, stream=st)
+            print(f"{args.profile_case} {n} states: kernel ms {t}")
+        if P.cbdfs_device_status(ctx) != 0:
+            raise SystemExit("device error flag set")
+    finally:
+        P.cbdfs_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -769,8 +807,14 @@ def main():
     ap.add_argument("--train-epochs", type=int, default=5)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-threads", type=int, default=64)
+    ap.add_argument("--profile-case", choices=["chain", "pdb78"],
+                    help="run four launches of one kernel for an ncu capture and exit")
+    ap.add_argument("--profile-states", type=int, default=BATCH)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        import paper_2507_11916_b300 as P
+        profile_case(P, args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

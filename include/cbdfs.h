@@ -106,7 +106,7 @@ typedef struct {
 /* Copy a network into device memory.  Weights are rounded there to the precision (FP32
  * master values -> BF16 round-to-nearest-even, or -> E4M3 with the scale).  *heur_id
  * receives its id.  Hidden widths must be multiples of 128 for BF16/FP8.
- * Errors: EINVAL (shape), ENOMEM, EDEVICE. */
+ * Errors: EINVAL (shape; a server is running on the context), ENOMEM, EDEVICE. */
 int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id);
 
 /* ---------------------------------------------------------------------------------------
@@ -127,7 +127,7 @@ typedef struct {
 } cbdfs_pdb_desc;
 
 /* Register an additive PDB (copying the tables to the device, or building them there).
- * *heur_id receives its id.  Errors: EINVAL, ENOMEM, EDEVICE. */
+ * *heur_id receives its id.  Errors: EINVAL (also while a server runs), ENOMEM, EDEVICE. */
 int cbdfs_pdb_load(cbdfs_ctx *ctx, const cbdfs_pdb_desc *d, int *heur_id);
 
 /* Build one pattern's table on the GPU by breadth-first search over the abstract space
@@ -293,7 +293,8 @@ typedef struct {
 
 /* Train network heur_id on n (state, label) pairs (host buffers, copied).  Labels are class
  * indices (< outputs) for cross-entropy, target values for MSE.
- * Errors: EINVAL (not a BF16 network, label range, sizes), ENOMEM, EDEVICE, ETIMEDOUT. */
+ * Errors: EINVAL (not a BF16 network, label range, sizes, a server is running), ENOMEM,
+ * EDEVICE, ETIMEDOUT. */
 int net_train(cbdfs_ctx *ctx, int heur_id, const uint64_t *states, const uint8_t *labels,
               uint64_t n, const cbdfs_train_cfg *cfg, cbdfs_train_report *rep);
 

@@ -204,6 +204,7 @@ int ensure_act(Ctx *c, size_t width) {
         }
     c->act_bytes = bytes;
     c->max_width = width;
+    ++c->buf_gen;
     return CBDFS_OK;
 }
 
@@ -216,6 +217,7 @@ int ensure_chain(Ctx *c, size_t floats) {
             if (!rc && cudaMemset(s.counters, 0, cbytes) != cudaSuccess) rc = fail(CBDFS_EDEVICE, "counter init");
             if (!rc) rc = dev_alloc(c, &s.onehot, (size_t)c->max_batch_pad * 1024);
             if (rc) return rc;
+            ++c->buf_gen;
         }
     if (floats <= c->partial_floats) return CBDFS_OK;
     const size_t pbytes = sizeof(float) * floats * c->max_batch_pad;
@@ -228,6 +230,7 @@ int ensure_chain(Ctx *c, size_t floats) {
         s.partial_bytes = pbytes;
     }
     c->partial_floats = floats;
+    ++c->buf_gen;
     return CBDFS_OK;
 }
 
@@ -538,6 +541,8 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
     if (!ctx || !d || !heur_id || !d->dims || !d->weights || !d->biases)
         return fail(CBDFS_EINVAL, "null argument");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    // a load may move the slots' scratch under the server's launches and captured graphs
+    if (c->server) return fail(CBDFS_EINVAL, "stop the server before loading a heuristic");
     CUDA_TRY(cudaSetDevice(c->device));
     const int L = d->n_layers;
     if (L < 2 || L > kMaxLayers) return fail(CBDFS_EINVAL, "n_layers %d outside 2..%d", L, kMaxLayers);
@@ -637,6 +642,7 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
 int cbdfs_pdb_load(cbdfs_ctx *ctx, const cbdfs_pdb_desc *d, int *heur_id) {
     if (!ctx || !d || !heur_id || !d->k || !d->tiles) return fail(CBDFS_EINVAL, "null argument");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (c->server) return fail(CBDFS_EINVAL, "stop the server before loading a heuristic");
     CUDA_TRY(cudaSetDevice(c->device));
     if (d->domain != CBDFS_DOM_STP3 && d->domain != CBDFS_DOM_STP4)
         return fail(CBDFS_EINVAL, "pattern databases are for sliding-tile domains");

@@ -127,6 +127,7 @@ struct Ctx {
     size_t max_width = 0;
     size_t partial_floats = 0;         // per-row head partials the chain scratch holds
     int num_sms = 0;
+    uint64_t buf_gen = 0;              // bumped whenever slot scratch moves (captured graphs hold its pointers)
     Server *server = nullptr;
 };
 

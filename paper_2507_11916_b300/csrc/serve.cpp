@@ -51,7 +51,8 @@ struct Launch {
 struct SlotIO {
     uint64_t *h_states = nullptr;  // pinned staging
     uint8_t *h_g = nullptr, *h_h = nullptr;
-    std::map<long long, cudaGraphExec_t> graphs;  // (heur, bucket) -> instantiated graph
+    // (heur, domain, bucket) -> instantiated graph and the scratch generation it was captured at
+    std::map<long long, std::pair<uint64_t, cudaGraphExec_t>> graphs;
 };
 
 }  // namespace
@@ -92,8 +93,12 @@ int get_graph(Server &S, int si, int heur, int domain, uint32_t bucket, cudaGrap
     const long long key = ((long long)heur << 40) ^ ((long long)domain << 32) ^ bucket;
     auto it = io.graphs.find(key);
     if (it != io.graphs.end()) {
-        *out = it->second;
-        return CBDFS_OK;
+        if (it->second.first == c->buf_gen) {
+            *out = it->second.second;
+            return CBDFS_OK;
+        }
+        cudaGraphExecDestroy(it->second.second);  // captured against scratch that has since moved
+        io.graphs.erase(it);
     }
     Slot &sl = c->slots[S.slots[si]];
     cudaStream_t st = sl.stream;
@@ -119,7 +124,7 @@ int get_graph(Server &S, int si, int heur, int domain, uint32_t bucket, cudaGrap
     e = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(CBDFS_EDEVICE, "graph instantiate: %s", cudaGetErrorString(e));
-    io.graphs.emplace(key, ex);
+    io.graphs.emplace(key, std::make_pair(c->buf_gen, ex));
     *out = ex;
     return CBDFS_OK;
 }
@@ -275,7 +280,7 @@ void server_loop(Server *Sp) {
 void server_free(Ctx *c, Server *S) {
     if (!S) return;
     for (auto &io : S->io) {
-        for (auto &kv : io.graphs) cudaGraphExecDestroy(kv.second);
+        for (auto &kv : io.graphs) cudaGraphExecDestroy(kv.second.second);
         cudaFreeHost(io.h_states);
         cudaFreeHost(io.h_g);
         cudaFreeHost(io.h_h);

@@ -719,6 +719,8 @@ int net_train(cbdfs_ctx *ctx, int net_id, const uint64_t *states, const uint8_t 
     if (rc) return rc;
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!states || !labels || !cfg || !rep || n == 0) return fail(CBDFS_EINVAL, "null argument");
+    // the server's launches read the weights the optimizer rewrites
+    if (c->server) return fail(CBDFS_EINVAL, "stop the server before training");
     cbdfs_train_cfg tc = *cfg;
     if (tc.batch == 0 || tc.batch > c->max_batch) return fail(CBDFS_EINVAL, "batch %u outside 1..max_batch", tc.batch);
     if (tc.epochs < 1) return fail(CBDFS_EINVAL, "epochs %d", tc.epochs);

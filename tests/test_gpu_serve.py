@@ -107,6 +107,19 @@ def test_memory_budget_and_errors(P):
             rs[0][0].wait()
         with pytest.raises(P.CbdfsError):
             P.heur_request_submit(ctx, hid, P.DOM_STP4, np.zeros(5000, np.uint64), np.zeros(5000, np.uint8), 1)
+        # a load could move the scratch the server's graphs were captured on: refused while it runs
+        W2, b2 = W.net_weights(**W.NET_C2)
+        with pytest.raises(P.CbdfsError):
+            P.cbdfs_net_load(ctx, P.DOM_RC3, W2, b2, PREC["bf16"], P.HEAD_CLASSIFIER, 0)
+        P.cbdfs_server_stop(ctx)
+        # after a wider network moved the scratch, a new server serves the first network unchanged
+        P.cbdfs_net_load(ctx, P.DOM_RC3, W2, b2, PREC["bf16"], P.HEAD_CLASSIFIER, 0)
+        s = W.random_stp_states(4, 3000, 99)
+        g = np.zeros(len(s), np.uint8)
+        want = P.heur_submit_batch(ctx, hid, P.DOM_STP4, s, g, 50)[0]
+        P.cbdfs_server_start(ctx, max_inflight=2, coalesce=1)
+        h, _, _ = P.heur_request_submit(ctx, hid, P.DOM_STP4, s, g, 50).wait()
+        assert np.array_equal(h, want)
         P.cbdfs_server_stop(ctx)
         with pytest.raises(P.CbdfsError):
             P.heur_request_submit(ctx, hid, P.DOM_STP4, np.zeros(8, np.uint64), np.zeros(8, np.uint8), 1)
