@@ -21,6 +21,11 @@ Section map (paper sections, equations and algorithms):
     enhancements: node limit, initial limit 10,000, initial bound h(root)+1).
     Parity unpinned against the paper for the bound-search schedule (the paper gives only
     the two constants and the requirement of exponential growth).
+  * real-valued heuristics ....................... oracle.c `or_cbdfs_real`, `ida_star_real`,
+    `bts_real`, `h_real`, `bound_test_real` (section "Regression-Based Neural Heuristics":
+    real h, real f-costs and thresholds; Experimental Setup: the regression model's
+    predictions minus 2.2).  `bts_real`'s binary search over real bounds is this oracle's
+    reading (parity unpinned against the paper beyond the costs and the integer case).
   * network heuristic ............................ `mlp_forward`, `h_regression`,
     `h_classifier` (Experimental Setup: a classifier heuristic and a regression heuristic;
     Background, Heuristics: classes are integer h values)
@@ -62,6 +67,16 @@ class OrResult(ctypes.Structure):
 
 HEUR_CB = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p)
 
+
+class OrResultReal(ctypes.Structure):
+    _fields_ = [("expanded", ctypes.c_int64), ("generated", ctypes.c_int64),
+                ("minf", ctypes.c_double), ("found", ctypes.c_int), ("cost", ctypes.c_int),
+                ("cut", ctypes.c_int), ("path_len", ctypes.c_int),
+                ("path", ctypes.c_int * 256)]
+
+
+HEUR_REAL_CB = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p)
+
 _lib = None
 
 
@@ -100,6 +115,10 @@ def lib():
         L.or_heuristic.argtypes = [ctypes.c_int, u64p, ctypes.c_int, ctypes.c_int, ip, ip,
                                    ctypes.c_void_p]
         assert L.or_result_size() == ctypes.sizeof(OrResult)
+        L.or_cbdfs_real.argtypes = [ctypes.c_int, u64p, ctypes.c_double, ctypes.c_int64,
+                                    ctypes.c_int, HEUR_REAL_CB, ctypes.c_void_p,
+                                    ctypes.POINTER(OrResultReal)]
+        assert L.or_result_real_size() == ctypes.sizeof(OrResultReal)
     return _lib
 
 
@@ -386,6 +405,135 @@ def bts(domain, start, heur: Heur, c1=BTS_C1, c2=BTS_C2, n0=BTS_N0, max_searches
 
 
 # ---------------------------------------------------------------------------------------
+# real-valued heuristics (section "Regression-Based Neural Heuristics": a regression
+# network's h is real, so f-costs are real and IDA*'s thresholds move by small steps; BTS's
+# search over bounds does not depend on how far apart f-costs lie)
+# ---------------------------------------------------------------------------------------
+
+class HeurReal:
+    """A real-valued h: a callable on the packed words (a tuple of two ints), cached per
+    state.  The goal gets 0 without a call."""
+
+    def __init__(self, fn):
+        self.fn = fn
+        self._cache = {}
+
+        def _cb(ptr, _user):
+            key = (ptr[0], ptr[1])
+            v = self._cache.get(key)
+            if v is None:
+                v = float(self.fn(key))
+                self._cache[key] = v
+            return v
+
+        self._cb = HEUR_REAL_CB(_cb)
+
+    def h(self, domain, state) -> float:
+        w = _words(state)
+        if (domain == DOM_RC3 and (w[0], w[1]) == rc_goal()) or \
+                (domain != DOM_RC3 and w[0] == stp_goal(3 if domain == DOM_STP3 else 4)):
+            return 0.0
+        return float(self.fn((w[0], w[1])))
+
+
+def cbdfs_real(domain, start, bound, heur: HeurReal, limit=-1, complete=True) -> OrResultReal:
+    """One cost-bounded DFS with f = g + h and the bound in float64 (oracle.c
+    `or_cbdfs_real`; the same tree rules as `cbdfs`).  minf < 0: no f above the bound."""
+    res = OrResultReal()
+    lib().or_cbdfs_real(domain, _words(start), float(bound), int(limit), int(complete),
+                        heur._cb, None, ctypes.byref(res))
+    return res
+
+
+def ida_star_real(domain, start, heur: HeurReal, complete=True, max_iters=100000):
+    """Algorithm 1 with a real-valued h: bound = h(start), then the least f above each
+    iteration's bound.  Returns dict(cost, iters=[(bound, expanded, generated)], path)."""
+    bound = heur.h(domain, start)
+    iters = []
+    for _ in range(max_iters):
+        r = cbdfs_real(domain, start, bound, heur, -1, complete)
+        iters.append((bound, r.expanded, r.generated))
+        if r.found:
+            return dict(cost=r.cost, iters=iters, path=list(r.path[:r.path_len]))
+        if r.minf < 0:
+            return dict(cost=None, iters=iters, path=None)
+        bound = r.minf
+    raise RuntimeError("iteration cap reached")
+
+
+def bts_real(domain, start, heur: HeurReal, c1=None, c2=None, n0=None, max_searches=100000):
+    """`bts` with real bounds.  The same schedule (first bound h(root)+1; the IDA* next
+    bound, then next + 2^j, then a binary search between the last small bound lo and the
+    first big one hi), with one change that the real line needs: the binary search runs
+    while some f-cost lies strictly between lo and hi -- lo's least f above its bound,
+    minf(lo), is below hi -- and probes mid = max((lo+hi)/2, minf(lo)), so that every probe
+    can change the tree.  (With integer f-costs this accepts the same bound as `bts`: the
+    least big bound.)  Returns dict(cost, searches=[(bound, limit, expanded, generated, cut,
+    found)])."""
+    c1 = BTS_C1 if c1 is None else c1
+    c2 = BTS_C2 if c2 is None else c2
+    n0 = BTS_N0 if n0 is None else n0
+    searches = []
+
+    def run(b, limit):
+        r = cbdfs_real(domain, start, b, heur, limit, True)
+        searches.append((b, limit, r.expanded, r.generated, r.cut, r.found))
+        if len(searches) > max_searches:
+            raise RuntimeError("search cap reached")
+        return r
+
+    class Done(Exception):
+        pass
+
+    def ends(r):
+        if not r.cut and r.found:
+            raise Done(r.cost)
+        if not r.cut and r.minf < 0:
+            raise Done(None)
+
+    N = n0
+    nxt = heur.h(domain, start) + 1.0
+    try:
+        while True:
+            limit = c2 * N
+            r = run(nxt, limit)
+            ends(r)
+            if r.cut:
+                r = run(nxt, -1)
+                ends(r)
+                N, nxt = max(r.expanded, 1), r.minf
+                continue
+            if r.expanded >= c1 * N:
+                N, nxt = r.expanded, r.minf
+                continue
+            lo, lo_minf, j = nxt, r.minf, 0
+            while True:
+                b = nxt + float(1 << j)
+                r = run(b, limit)
+                ends(r)
+                if r.cut or r.expanded >= c1 * N:
+                    hi, hi_r = b, r
+                    break
+                lo, lo_minf, j = b, r.minf, j + 1
+            while lo_minf < hi:
+                mid = max((lo + hi) / 2.0, lo_minf)
+                if mid >= hi:
+                    mid = lo_minf
+                r = run(mid, limit)
+                ends(r)
+                if r.cut or r.expanded >= c1 * N:
+                    hi, hi_r = mid, r
+                else:
+                    lo, lo_minf = mid, r.minf
+            if hi_r.cut:
+                hi_r = run(hi, -1)
+                ends(hi_r)
+            N, nxt = max(hi_r.expanded, 1), hi_r.minf
+    except Done as d:
+        return dict(cost=d.args[0], searches=searches)
+
+
+# ---------------------------------------------------------------------------------------
 # the network heuristic (float64)
 # ---------------------------------------------------------------------------------------
 
@@ -549,6 +697,32 @@ def h_classifier(logits, md=None, goal=None) -> np.ndarray:
     if goal is not None:
         h = np.where(goal, 0, h)
     return h
+
+
+def h_real(y, offset, md=None, goal=None) -> np.ndarray:
+    """The real-valued regression heuristic (Experimental Setup: the regression model's
+    predictions minus 2.2, for admissibility): h = max(y + offset, 0), max'ed with MD when
+    given; the goal gets 0."""
+    h = np.maximum(np.asarray(y, np.float64).reshape(-1) + offset, 0.0)
+    if md is not None:
+        h = np.maximum(h, np.asarray(md, np.float64))
+    if goal is not None:
+        h = np.where(goal, 0.0, h)
+    return h
+
+
+def bound_test_real(g, h, bound, dtype=np.float64):
+    """The bound test with real h: mask_i = (g_i + h_i <= bound) with the sum and the
+    comparison in `dtype`; minf = least g_i + h_i above the bound (inf if none)."""
+    f = np.asarray(g, dtype) + np.asarray(h, dtype)
+    ok = f <= dtype(bound)
+    n = len(f)
+    words = np.zeros((n + 31) // 32, dtype=np.uint64)
+    for i in np.nonzero(ok)[0]:
+        words[i // 32] |= np.uint64(1) << np.uint64(i % 32)
+    above = f[~ok]
+    minf = float(above.min()) if above.size else float("inf")
+    return words.astype(np.uint32), minf
 
 
 def regression_margin(y, width=1e-2) -> np.ndarray:

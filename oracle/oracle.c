@@ -739,3 +739,90 @@ int or_heuristic(int domain, const uint64_t *s, int hkind, int npat, const int *
 }
 
 int or_result_size(void) { return (int)sizeof(or_result); }
+
+/* ======================================================================================
+ * one cost-bounded depth-first search with a real-valued heuristic
+ * (section "Regression-Based Neural Heuristics": a regression network gives real h; IDA*'s
+ * thresholds then move by small steps).  f = g + h in double; the bound is a double; the
+ * least f above the bound is the next threshold.  Same tree rules as `dfs` above.
+ * ==================================================================================== */
+
+typedef double (*or_heur_real_cb)(const uint64_t *state, void *user);
+
+typedef struct {
+    int64_t expanded, generated;
+    double minf;                  /* least f above the bound (-1: none) */
+    int found, cost, cut, path_len;
+    int path[256];
+} or_result_real;
+
+typedef struct {
+    int domain;
+    or_heur_real_cb cb;
+    void *user;
+    double bound;
+    int complete;
+    int64_t limit;
+    or_result_real *res;
+    int path[256];
+    int stop;
+} dfs_real_ctx;
+
+static double eval_h_real(const dfs_real_ctx *c, const uint64_t *s) {
+    if (is_goal(c->domain, s)) return 0.0;
+    return c->cb(s, c->user);
+}
+
+static void dfs_real(dfs_real_ctx *c, const uint64_t *s, int g, int last, double hval, int depth) {
+    int w = dom_words(c->domain);
+    double f = (double)g + hval;
+    if (f > c->bound) {
+        if (c->res->minf < 0 || f < c->res->minf) c->res->minf = f;
+        return;
+    }
+    if (is_goal(c->domain, s)) {
+        if (!c->res->found || g < c->res->cost) {
+            c->res->cost = g;
+            c->res->path_len = depth;
+            memcpy(c->res->path, c->path, sizeof(int) * depth);
+        }
+        c->res->found = 1;
+        if (!c->complete) c->stop = 1;
+        return;
+    }
+    if (c->limit >= 0 && c->res->expanded >= c->limit) {
+        c->res->cut = 1;
+        c->stop = 1;
+        return;
+    }
+    c->res->expanded++;
+    uint64_t kids[2 * 18];
+    int moves[18];
+    int nk = children(c->domain, s, last, kids, moves);
+    c->res->generated += nk;
+    for (int i = 0; i < nk && !c->stop; ++i) {
+        if (depth < 256) c->path[depth] = moves[i];
+        dfs_real(c, &kids[w * i], g + 1, moves[i], eval_h_real(c, &kids[w * i]), depth + 1);
+    }
+}
+
+/* One CB-DFS with a real threshold; h from `cb` (the goal gets 0). */
+int or_cbdfs_real(int domain, const uint64_t *start, double bound, int64_t limit, int complete,
+                  or_heur_real_cb cb, void *user, or_result_real *out) {
+    memset(out, 0, sizeof(*out));
+    out->minf = -1;
+    out->cost = -1;
+    dfs_real_ctx c;
+    memset(&c, 0, sizeof(c));
+    c.domain = domain;
+    c.cb = cb;
+    c.user = user;
+    c.bound = bound;
+    c.complete = complete;
+    c.limit = limit;
+    c.res = out;
+    dfs_real(&c, start, 0, -1, eval_h_real(&c, start), 0);
+    return 0;
+}
+
+int or_result_real_size(void) { return (int)sizeof(or_result_real); }
