@@ -48,7 +48,7 @@ typedef enum {
 
 typedef enum { CBDFS_DOM_STP3 = 0, CBDFS_DOM_STP4 = 1, CBDFS_DOM_RC3 = 2 } cbdfs_domain;
 typedef enum { CBDFS_PREC_FP32 = 0, CBDFS_PREC_BF16 = 1, CBDFS_PREC_FP8 = 2 } cbdfs_prec;
-typedef enum { CBDFS_HEAD_REGRESSION = 0, CBDFS_HEAD_CLASSIFIER = 1 } cbdfs_head;
+typedef enum { CBDFS_HEAD_REGRESSION = 0, CBDFS_HEAD_CLASSIFIER = 1, CBDFS_HEAD_REAL = 2 } cbdfs_head;
 typedef enum { CBDFS_ALGO_IDA = 0, CBDFS_ALGO_BTS = 1 } cbdfs_algo;
 
 /* Built-in heuristic ids (network and PDB ids from the load calls are >= 0). */
@@ -90,6 +90,12 @@ size_t cbdfs_mem_used(const cbdfs_ctx *ctx);
  *               when max_with_md != 0, clamped to 255;
  *   classifier: h = argmax over the outputs (lowest index on ties), max'ed with Manhattan
  *               distance when max_with_md != 0.
+ * Real-valued h (section "Regression-Based Neural Heuristics"; Experimental Setup: the
+ * regression model's predictions minus 2.2):
+ *   real:       one output; h = max(y + h_offset, 0) in FP32, max'ed with Manhattan distance
+ *               when max_with_md != 0; the goal gets 0.  f = g + h is an FP32 sum and the
+ *               bound is an FP32 value: these networks are evaluated through the *_real
+ *               calls below, and cbdfs_solve searches them with real thresholds.
  * ------------------------------------------------------------------------------------- */
 typedef struct {
     int domain;                     /* cbdfs_domain */
@@ -101,6 +107,7 @@ typedef struct {
     int head;                       /* cbdfs_head */
     int max_with_md;                /* STP only */
     const float *act_scales;        /* FP8 only: L-1 activation scales (host), else NULL */
+    float h_offset;                 /* CBDFS_HEAD_REAL: added to y (the paper: -2.2); else 0 */
 } cbdfs_net_desc;
 
 /* Copy a network into device memory.  Weights are rounded there to the precision (FP32
@@ -150,7 +157,8 @@ int pdb_build(cbdfs_ctx *ctx, int domain, const int *pattern_tiles, int k, uint8
  *   minf_out the least g_i + h_i above the bound, 0xFFFFFFFF if none
  *   y_out   optional (may be NULL): the raw FP32 network outputs, n x dims[L] row-major
  *           (ignored for PDB / built-in heuristics)
- * n = 0 is allowed (mask nothing, minf 0xFFFFFFFF).  n > max_batch: EINVAL.
+ * n = 0 is allowed (mask nothing, minf 0xFFFFFFFF).  n > max_batch: EINVAL.  A network with
+ * the real-valued head is refused here (EINVAL): use heur_submit_batch_real.
  * ------------------------------------------------------------------------------------- */
 
 /* Host buffers; returns when the results are in h_out/mask_out/minf_out.  When states, g,
@@ -173,6 +181,23 @@ int heur_eval_device(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_
                      const uint8_t *d_g, uint32_t bound, uint32_t n, uint8_t *d_h,
                      uint32_t *d_mask, uint32_t *d_minf, float *d_y, void *stream);
 
+/* Real-valued heuristic (a network loaded with CBDFS_HEAD_REAL), host buffers: the bound
+ * test with f = g + h in FP32 (Algorithm 3's expansion test with real f-costs).
+ *   bound    a finite or infinite FP32 bound >= 0 (negative or NaN: EINVAL)
+ *   h_out    n real heuristic values
+ *   mask_out ceil(n/32) words, bit i set iff g_i + h_i <= bound
+ *   minf_out the least g_i + h_i above the bound; +infinity if none
+ * Other heuristics are refused (EINVAL).  Returns when the results are in the buffers. */
+int heur_submit_batch_real(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *states,
+                           const uint8_t *g, float bound, uint32_t n, float *h_out,
+                           uint32_t *mask_out, float *minf_out);
+
+/* The same on device buffers, enqueued on `stream` as heur_eval_device.  *d_minf receives
+ * the least f above the bound, or the bit pattern 0xFFFFFFFF (a NaN) if none. */
+int heur_eval_device_real(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_states,
+                          const uint8_t *d_g, float bound, uint32_t n, float *d_h,
+                          uint32_t *d_mask, float *d_minf, void *stream);
+
 /* Like heur_eval_device, for callers that cannot allocate device memory when they evaluate
  * a batch (a real-time or latency-budgeted caller that must not enter the allocator, or a
  * process whose device memory another framework's allocator owns).  The paper has no
@@ -189,7 +214,7 @@ int heur_eval_device(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_
  *   - Every call shares the array, which keeps the previous call's contents; nothing in it
  *     needs to start at zero (each call writes every activation row it reads).  Calls that
  *     overlap on the GPU (other streams, other threads) race on the array: order them.
- * Errors: EINVAL (arguments, size limit), EDEVICE. */
+ * Errors: EINVAL (arguments, size limit, a real-valued network), EDEVICE. */
 int heur_eval_device_static(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_states,
                             const uint8_t *d_g, uint32_t bound, uint32_t n, uint8_t *d_h,
                             uint32_t *d_mask, uint32_t *d_minf, void *stream);
@@ -248,7 +273,7 @@ typedef struct {
 } cbdfs_server_stats;
 
 /* Start the server (at most one per context).  Errors: EINVAL (no free slot, buckets),
- * ENOMEM, EDEVICE.  Load networks before starting: a later load may reallocate scratch. */
+ * ENOMEM, EDEVICE.  Load networks before starting: loads are refused while it runs. */
 int cbdfs_server_start(cbdfs_ctx *ctx, const cbdfs_server_cfg *cfg);
 /* Finish every queued request, then stop the server and release its slots. */
 int cbdfs_server_stop(cbdfs_ctx *ctx);
@@ -370,6 +395,9 @@ typedef struct {
     double batch_fill_us;           /* mean time from a batch's first state to its submission */
     double batch_flight_us;         /* mean time from submission to its results being readable */
     double submit_us;               /* mean host time the batch processor spends submitting one */
+    int real_valued;                /* 1: the pruning heuristic is real-valued (CBDFS_HEAD_REAL);
+                                       its bounds are in iter_bound_real, iter_bound holds 0 */
+    double iter_bound_real[CBDFS_MAX_ITERS];  /* every search's bound as a real number */
 } cbdfs_result;
 
 /* Solve from `start` (packed words).  heur_id: a network, a PDB or a built-in id.

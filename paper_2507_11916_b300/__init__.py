@@ -34,7 +34,7 @@ CBDFS_OK, CBDFS_EINVAL, CBDFS_ENOMEM, CBDFS_ETIMEDOUT = 0, -1, -2, -3
 CBDFS_EDEVICE, CBDFS_ECANCELED, CBDFS_ENOTFOUND = -4, -5, -6
 DOM_STP3, DOM_STP4, DOM_RC3 = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
-HEAD_REGRESSION, HEAD_CLASSIFIER = 0, 1
+HEAD_REGRESSION, HEAD_CLASSIFIER, HEAD_REAL = 0, 1, 2
 LOSS_CE, LOSS_MSE = 0, 1
 ALGO_IDA, ALGO_BTS = 0, 1
 HEUR_ZERO, HEUR_MD, HEUR_NONE = -1, -2, -100
@@ -61,7 +61,7 @@ class NetDesc(ctypes.Structure):
                 ("weights", ctypes.POINTER(ctypes.POINTER(ctypes.c_float))),
                 ("biases", ctypes.POINTER(ctypes.POINTER(ctypes.c_float))),
                 ("prec", ctypes.c_int), ("head", ctypes.c_int), ("max_with_md", ctypes.c_int),
-                ("act_scales", ctypes.POINTER(ctypes.c_float))]
+                ("act_scales", ctypes.POINTER(ctypes.c_float)), ("h_offset", ctypes.c_float)]
 
 
 class PdbDesc(ctypes.Structure):
@@ -117,7 +117,8 @@ class Result(ctypes.Structure):
                 ("batches", ctypes.c_int64), ("evaluated", ctypes.c_int64),
                 ("seconds", ctypes.c_double), ("d_init", ctypes.c_int),
                 ("work_items", ctypes.c_int64), ("batch_fill_us", ctypes.c_double),
-                ("batch_flight_us", ctypes.c_double), ("submit_us", ctypes.c_double)]
+                ("batch_flight_us", ctypes.c_double), ("submit_us", ctypes.c_double),
+                ("real_valued", ctypes.c_int), ("iter_bound_real", ctypes.c_double * MAX_ITERS)]
 
 
 _vp, _u64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)
@@ -135,6 +136,10 @@ _lib.heur_submit_batch.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ct
                                    ctypes.c_uint32, _vp, _vp, _vp, _vp]
 _lib.heur_eval_device.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint32,
                                   ctypes.c_uint32, _vp, _vp, _vp, _vp, _vp]
+_lib.heur_submit_batch_real.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_float,
+                                        ctypes.c_uint32, _vp, _vp, _vp]
+_lib.heur_eval_device_real.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_float,
+                                       ctypes.c_uint32, _vp, _vp, _vp, _vp]
 _lib.cbdfs_device_status.argtypes = [_vp]
 _lib.cbdfs_eval_trace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint32,
                                   ctypes.c_uint32, _vp, _vp, _vp, _vp, _vp, ctypes.c_int,
@@ -172,7 +177,7 @@ _lib.cbdfs_cancel.restype = None
 # every symbol include/cbdfs.h declares
 EXPORTED = ["cbdfs_create", "cbdfs_destroy", "cbdfs_last_error", "cbdfs_mem_used", "cbdfs_net_load",
             "cbdfs_pdb_load", "pdb_build", "heur_submit_batch", "heur_eval_device",
-            "heur_eval_device_static",
+            "heur_submit_batch_real", "heur_eval_device_real", "heur_eval_device_static",
             "cbdfs_device_status", "cbdfs_eval_profile", "cbdfs_eval_trace", "net_train",
             "cbdfs_train_grad", "cbdfs_net_read", "cbdfs_gen_walk_states", "cbdfs_server_start",
             "cbdfs_server_stop", "heur_request_submit", "heur_request_wait", "cbdfs_server_get_stats", "cbdfs_apply_moves", "cbdfs_manhattan", "cbdfs_solve",
@@ -214,7 +219,7 @@ def cbdfs_mem_used(ctx) -> int:
 
 
 def cbdfs_net_load(ctx, domain, weights, biases, prec=PREC_BF16, head=HEAD_REGRESSION,
-                   max_with_md=0, act_scales=None) -> int:
+                   max_with_md=0, act_scales=None, h_offset=0.0) -> int:
     Ws = [np.ascontiguousarray(w, dtype=np.float32) for w in weights]
     bs = [np.ascontiguousarray(b, dtype=np.float32) for b in biases]
     dims = [Ws[0].shape[1]] + [w.shape[0] for w in Ws]
@@ -226,7 +231,7 @@ def cbdfs_net_load(ctx, domain, weights, biases, prec=PREC_BF16, head=HEAD_REGRE
         sc_arr = np.ascontiguousarray(act_scales, dtype=np.float32)
         sc = sc_arr.ctypes.data_as(FP)
     d = NetDesc(domain, len(Ws), (ctypes.c_int * len(dims))(*dims), wp, bp, prec, head,
-                max_with_md, sc)
+                max_with_md, sc, h_offset)
     out = ctypes.c_int()
     _check(_lib.cbdfs_net_load(ctx, ctypes.byref(d), ctypes.byref(out)))
     return out.value
@@ -270,6 +275,27 @@ def heur_submit_batch(ctx, heur_id, domain, states, g, bound, want_y=False, n_ou
     _check(_lib.heur_submit_batch(ctx, heur_id, domain, _ptr(states), _ptr(g), bound, n,
                                   _ptr(h), _ptr(mask), _ptr(minf), _ptr(y)))
     return (h, mask, int(minf[0]), y) if want_y else (h, mask, int(minf[0]))
+
+
+def heur_submit_batch_real(ctx, heur_id, domain, states, g, bound):
+    """A real-valued network: (h float32[n], mask uint32[ceil(n/32)], minf float)."""
+    states = np.ascontiguousarray(states, dtype=np.uint64)
+    g = np.ascontiguousarray(g, dtype=np.uint8)
+    n = len(g)
+    h = np.empty(n, dtype=np.float32)
+    mask = np.empty((n + 31) // 32, dtype=np.uint32)
+    minf = np.empty(1, dtype=np.float32)
+    _check(_lib.heur_submit_batch_real(ctx, heur_id, domain, _ptr(states), _ptr(g), float(bound), n,
+                                       _ptr(h), _ptr(mask), _ptr(minf)))
+    return h, mask, float(minf[0])
+
+
+def heur_eval_device_real(ctx, heur_id, domain, d_states, d_g, bound, n, d_h, d_mask, d_minf,
+                          stream=None):
+    """Device tensors: d_h float32[n], d_mask int32[ceil(n/32)], d_minf float32[1]."""
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(_lib.heur_eval_device_real(ctx, heur_id, domain, _ptr(d_states), _ptr(d_g), float(bound), n,
+                                      _ptr(d_h), _ptr(d_mask), _ptr(d_minf), s))
 
 
 def heur_eval_device(ctx, heur_id, domain, d_states, d_g, bound, n, d_h, d_mask, d_minf, d_y=None,
@@ -446,7 +472,9 @@ def cbdfs_solve(ctx, domain, start, algo=ALGO_IDA, heur_id=HEUR_MD, partial_ok=F
         _check(status)
     k = min(r.n_iters, MAX_ITERS)
     return dict(status=status, cost=r.cost, path=list(r.path[:r.path_len]),
-                iters=[(r.iter_bound[i], r.iter_expanded[i], r.iter_generated[i]) for i in range(k)],
+                iters=[(r.iter_bound_real[i] if r.real_valued else r.iter_bound[i], r.iter_expanded[i],
+                        r.iter_generated[i]) for i in range(k)],
+                real_valued=bool(r.real_valued),
                 iter_limit=list(r.iter_limit[:k]), iter_cut=list(r.iter_cut[:k]),
                 n_iters=r.n_iters, expanded=r.expanded, generated=r.generated,
                 batches=r.batches, evaluated=r.evaluated, seconds=r.seconds, d_init=r.d_init,

@@ -23,7 +23,8 @@ int sgemm_relu(const float *A, const float *W, const float *b, float *C, int M, 
                int relu, cudaStream_t st);
 int head(bool bf16_in, int domain, int head_kind, const void *act, int K, int C, const float *W,
          const float *b, const uint64_t *states, const uint8_t *g, uint32_t bound, uint32_t n,
-         int max_with_md, uint8_t *h, uint32_t *mask, uint32_t *minf, float *y, cudaStream_t st);
+         int max_with_md, float offset, uint8_t *h, uint32_t *mask, uint32_t *minf, float *y,
+         cudaStream_t st);
 struct PdbParams {
     int n_patterns;
     int k[4];
@@ -346,6 +347,7 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     P.C = net.dims[L];
     P.head_kind = net.head;
     P.max_with_md = net.max_with_md;
+    P.h_offset = net.h_offset;
     P.w_last = net.w32[L - 1];
     P.b_last = net.b32[L - 1];
     P.g = d_g;
@@ -367,7 +369,8 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     if (rc || (rc = mark(s, st)) || P.fused_head) return rc;
     // the last layer (FP32) over the stored BF16 activations of the last hidden layer
     rc = head(true, domain, net.head, s.act[(nh - 1) & 1], net.dims[nh], net.dims[L], net.w32[L - 1],
-              net.b32[L - 1], d_states, d_g, bound, n, net.max_with_md, d_h, d_mask, d_minf, d_y, st);
+              net.b32[L - 1], d_states, d_g, bound, n, net.max_with_md, net.h_offset, d_h, d_mask, d_minf,
+              d_y, st);
     return rc ? rc : mark(s, st);
 }
 
@@ -412,8 +415,8 @@ int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
             if (rc || (rc = mark(s, st))) return rc;
             std::swap(a, b);
         }
-        rc = head(false, domain, net.head, a, net.dims[L - 1], net.dims[L], net.w32[L - 1],
-                    net.b32[L - 1], d_states, d_g, bound, n, net.max_with_md, d_h, d_mask, d_minf, d_y, st);
+        rc = head(false, domain, net.head, a, net.dims[L - 1], net.dims[L], net.w32[L - 1], net.b32[L - 1],
+                  d_states, d_g, bound, n, net.max_with_md, net.h_offset, d_h, d_mask, d_minf, d_y, st);
         return rc ? rc : mark(s, st);
     }
     const bool fp8 = net.prec == CBDFS_PREC_FP8;
@@ -439,8 +442,14 @@ int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
         cur = out_buf;
     }
     rc = head(true, domain, net.head, s.act[cur], net.dims[L - 1], net.dims[L], net.w32[L - 1],
-              net.b32[L - 1], d_states, d_g, bound, n, net.max_with_md, d_h, d_mask, d_minf, d_y, st);
+              net.b32[L - 1], d_states, d_g, bound, n, net.max_with_md, net.h_offset, d_h, d_mask, d_minf,
+              d_y, st);
     return rc ? rc : mark(s, st);
+}
+
+bool heur_is_real(const Ctx *c, int heur_id) {
+    return heur_id >= 0 && heur_id < (int)c->heur_kind.size() && c->heur_kind[heur_id] == 0 &&
+           c->nets[c->heur_index[heur_id]]->head == CBDFS_HEAD_REAL;
 }
 
 }  // namespace cbdfs
@@ -550,8 +559,11 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
     if (d->dims[0] != dom_onehot(d->domain))
         return fail(CBDFS_EINVAL, "dims[0]=%d but the domain's one-hot width is %d", d->dims[0], dom_onehot(d->domain));
     if (d->prec < 0 || d->prec > 2) return fail(CBDFS_EINVAL, "precision %d", d->prec);
-    if (d->head != CBDFS_HEAD_REGRESSION && d->head != CBDFS_HEAD_CLASSIFIER) return fail(CBDFS_EINVAL, "head %d", d->head);
-    if (d->head == CBDFS_HEAD_REGRESSION && d->dims[L] != 1) return fail(CBDFS_EINVAL, "a regression head has one output");
+    if (d->head != CBDFS_HEAD_REGRESSION && d->head != CBDFS_HEAD_CLASSIFIER && d->head != CBDFS_HEAD_REAL)
+        return fail(CBDFS_EINVAL, "head %d", d->head);
+    if (d->head != CBDFS_HEAD_CLASSIFIER && d->dims[L] != 1) return fail(CBDFS_EINVAL, "a regression head has one output");
+    if (!std::isfinite(d->h_offset) || (d->head != CBDFS_HEAD_REAL && d->h_offset != 0.f))
+        return fail(CBDFS_EINVAL, "h_offset %g (finite, and only for the real-valued head)", d->h_offset);
     if (d->max_with_md && d->domain == CBDFS_DOM_RC3) return fail(CBDFS_EINVAL, "Manhattan distance needs a sliding-tile domain");
     for (int l = 1; l < L; ++l)
         if (d->dims[l] % 128 != 0) return fail(CBDFS_EINVAL, "hidden width %d is not a multiple of 128", d->dims[l]);
@@ -560,6 +572,7 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
     auto net = std::make_unique<NetGPU>();
     NetGPU &N = *net;
     N.domain = d->domain; N.L = L; N.prec = d->prec; N.head = d->head; N.max_with_md = d->max_with_md;
+    N.h_offset = d->h_offset;
     for (int l = 0; l <= L; ++l) N.dims[l] = d->dims[l];
     size_t maxw = 0;
     for (int l = 1; l < L; ++l) maxw = std::max(maxw, (size_t)d->dims[l]);
@@ -709,23 +722,30 @@ int pdb_build(cbdfs_ctx *ctx, int domain, const int *pattern_tiles, int k, uint8
     return rc;
 }
 
-static int check_eval_args(Ctx *c, int heur_id, int domain, uint32_t n) {
+// real: the call is one of the *_real entry points (which take exactly the real-valued heads)
+static int check_eval_args(Ctx *c, int heur_id, int domain, uint32_t n, bool real = false) {
     if (domain < 0 || domain > 2) return fail(CBDFS_EINVAL, "domain %d", domain);
     if (n > c->max_batch) return fail(CBDFS_EINVAL, "n=%u exceeds max_batch=%u", n, c->max_batch);
     if (heur_id >= (int)c->heur_kind.size() || heur_id < CBDFS_HEUR_MD)
         return fail(CBDFS_EINVAL, "unknown heuristic id %d", heur_id);
     if (heur_id == CBDFS_HEUR_MD && domain == CBDFS_DOM_RC3)
         return fail(CBDFS_EINVAL, "Manhattan distance is defined for sliding-tile domains only");
+    if (heur_is_real(c, heur_id) != real)
+        return fail(CBDFS_EINVAL, real ? "heuristic %d is not real-valued" : "heuristic %d is real-valued: use the *_real calls",
+                    heur_id);
     return CBDFS_OK;
 }
 
-int heur_eval_device(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_states, const uint8_t *d_g,
-                     uint32_t bound, uint32_t n, uint8_t *d_h, uint32_t *d_mask, uint32_t *d_minf,
-                     float *d_y, void *stream) {
-    if (!ctx || !d_minf || (n && (!d_states || !d_g || !d_h || !d_mask))) return fail(CBDFS_EINVAL, "null argument");
-    Ctx *c = reinterpret_cast<Ctx *>(ctx);
-    int rc = check_eval_args(c, heur_id, domain, n);
-    if (rc) return rc;
+// an FP32 bound as the kernels' key (its bit pattern; f >= 0 orders like the key)
+static int real_bound_key(float bound, uint32_t *key) {
+    if (!(bound >= 0.f)) return fail(CBDFS_EINVAL, "bound %g: a real bound is >= 0 and not NaN", bound);
+    memcpy(key, &bound, 4);
+    return CBDFS_OK;
+}
+
+static int eval_device(Ctx *c, int heur_id, int domain, const uint64_t *d_states, const uint8_t *d_g,
+                       uint32_t bound, uint32_t n, uint8_t *d_h, uint32_t *d_mask, uint32_t *d_minf,
+                       float *d_y, void *stream) {
     CUDA_TRY(cudaSetDevice(c->device));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     std::lock_guard<std::mutex> lk(c->device_call_mu);
@@ -736,9 +756,32 @@ int heur_eval_device(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_
     CUDA_TRY(cudaStreamIsCapturing(st, &cs));
     const bool capturing = cs != cudaStreamCaptureStatusNone;
     if (!capturing) CUDA_TRY(cudaStreamWaitEvent(st, s.done, 0));
-    rc = run_eval(c, s, heur_id, domain, d_states, d_g, bound, n, d_h, d_mask, d_minf, d_y, st);
+    int rc = run_eval(c, s, heur_id, domain, d_states, d_g, bound, n, d_h, d_mask, d_minf, d_y, st);
     if (!capturing) CUDA_TRY(cudaEventRecord(s.done, st));
     return rc;
+}
+
+int heur_eval_device(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_states, const uint8_t *d_g,
+                     uint32_t bound, uint32_t n, uint8_t *d_h, uint32_t *d_mask, uint32_t *d_minf,
+                     float *d_y, void *stream) {
+    if (!ctx || !d_minf || (n && (!d_states || !d_g || !d_h || !d_mask))) return fail(CBDFS_EINVAL, "null argument");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    int rc = check_eval_args(c, heur_id, domain, n);
+    if (rc) return rc;
+    return eval_device(c, heur_id, domain, d_states, d_g, bound, n, d_h, d_mask, d_minf, d_y, stream);
+}
+
+int heur_eval_device_real(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_states,
+                          const uint8_t *d_g, float bound, uint32_t n, float *d_h, uint32_t *d_mask,
+                          float *d_minf, void *stream) {
+    if (!ctx || !d_minf || (n && (!d_states || !d_g || !d_h || !d_mask))) return fail(CBDFS_EINVAL, "null argument");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    uint32_t key;
+    int rc = check_eval_args(c, heur_id, domain, n, true);
+    if (rc || (rc = real_bound_key(bound, &key))) return rc;
+    // the real h goes where the raw outputs would; no uint8 h
+    return eval_device(c, heur_id, domain, d_states, d_g, key, n, nullptr, d_mask,
+                       reinterpret_cast<uint32_t *>(d_minf), d_h, stream);
 }
 
 // the device address of page-locked host memory (cudaMallocHost / cudaHostRegister), else false
@@ -753,13 +796,12 @@ static bool host_mapped(const void *p, void **dev) {
     return true;
 }
 
-int heur_submit_batch(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *states, const uint8_t *g,
-                      uint32_t bound, uint32_t n, uint8_t *h_out, uint32_t *mask_out, uint32_t *minf_out,
-                      float *y_out) {
-    if (!ctx || !minf_out || (n && (!states || !g || !h_out || !mask_out))) return fail(CBDFS_EINVAL, "null argument");
-    Ctx *c = reinterpret_cast<Ctx *>(ctx);
-    int rc = check_eval_args(c, heur_id, domain, n);
-    if (rc) return rc;
+// One host-buffer batch on a free slot (slots 1..).  h8: uint8 h (null for a real-valued
+// head); yf: C floats per row (the raw outputs, or for a real-valued head its h, C = 1), or
+// null.  *minf_key receives the least f above the bound as the kernels' key.
+static int submit_host(Ctx *c, int heur_id, int domain, const uint64_t *states, const uint8_t *g,
+                       uint32_t bound, uint32_t n, uint8_t *h8, uint32_t *mask_out, uint32_t *minf_key,
+                       float *yf, int C) {
     CUDA_TRY(cudaSetDevice(c->device));
     int si;
     {
@@ -776,35 +818,32 @@ int heur_submit_batch(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *s
     Slot &s = c->slots[si];
     cudaStream_t st = s.stream;
     const int w = dom_words(domain);
-    int C = 0;
-    if (y_out && heur_id >= 0 && c->heur_kind[heur_id] == 0) {
-        const NetGPU &net = *c->nets[c->heur_index[heur_id]];
-        C = net.dims[net.L];
-    }
-    float *d_y = nullptr;
-    if (C) {
-        rc = dev_alloc(c, (void **)&d_y, (size_t)n * C * 4 + 4);
-    }
+    int rc = CBDFS_OK;
     // Page-locked caller buffers are read and written by the kernels in place (mapped host
     // memory, over the bus inside the launch); other buffers go through the slot's device
     // staging with copies.
-    void *zs = nullptr, *zg = nullptr, *zh = nullptr, *zm = nullptr;
-    const bool zero_copy = !rc && n && !C && host_mapped(states, &zs) && host_mapped(g, &zg) &&
-                           host_mapped(h_out, &zh) && host_mapped(mask_out, &zm);
+    void *zs = nullptr, *zg = nullptr, *zh = nullptr, *zm = nullptr, *zy = nullptr;
+    const bool zero_copy = n && host_mapped(states, &zs) && host_mapped(g, &zg) && host_mapped(mask_out, &zm) &&
+                           (!h8 || host_mapped(h8, &zh)) && (!yf || host_mapped(yf, &zy));
+    float *d_y = nullptr;
+    if (!zero_copy && yf && n) rc = dev_alloc(c, (void **)&d_y, (size_t)n * C * 4 + 4);
     if (zero_copy) {
         rc = run_eval(c, s, heur_id, domain, static_cast<const uint64_t *>(zs), static_cast<const uint8_t *>(zg),
-                      bound, n, static_cast<uint8_t *>(zh), static_cast<uint32_t *>(zm), s.d_minf, nullptr, st);
+                      bound, n, static_cast<uint8_t *>(zh), static_cast<uint32_t *>(zm), s.d_minf,
+                      static_cast<float *>(zy), st);
     } else {
         if (!rc && n) {
             if (cudaMemcpyAsync(s.d_states, states, (size_t)n * 8 * w, cudaMemcpyHostToDevice, st) != cudaSuccess ||
                 cudaMemcpyAsync(s.d_g, g, n, cudaMemcpyHostToDevice, st) != cudaSuccess)
                 rc = fail(CBDFS_EDEVICE, "batch upload");
         }
-        if (!rc) rc = run_eval(c, s, heur_id, domain, s.d_states, s.d_g, bound, n, s.d_h, s.d_mask, s.d_minf, d_y, st);
-        if (!rc) {
-            if ((n && (cudaMemcpyAsync(h_out, s.d_h, n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                       cudaMemcpyAsync(mask_out, s.d_mask, (size_t)(n + 31) / 32 * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)) ||
-                (C && cudaMemcpyAsync(y_out, d_y, (size_t)n * C * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess))
+        if (!rc)
+            rc = run_eval(c, s, heur_id, domain, s.d_states, s.d_g, bound, n, h8 ? s.d_h : nullptr, s.d_mask,
+                          s.d_minf, d_y, st);
+        if (!rc && n) {
+            if ((h8 && cudaMemcpyAsync(h8, s.d_h, n, cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+                cudaMemcpyAsync(mask_out, s.d_mask, (size_t)(n + 31) / 32 * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                (d_y && cudaMemcpyAsync(yf, d_y, (size_t)n * C * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess))
                 rc = fail(CBDFS_EDEVICE, "result download");
         }
     }
@@ -816,7 +855,7 @@ int heur_submit_batch(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *s
     if (!rc && e != cudaSuccess) rc = fail(CBDFS_EDEVICE, "evaluation: %s", cudaGetErrorString(e));
     if (d_y) dev_free(c, d_y, (size_t)n * C * 4 + 4);
     if (!rc) {
-        *minf_out = s.h_small[0];
+        *minf_key = s.h_small[0];
         if (s.h_small[1]) rc = fail(CBDFS_ETIMEDOUT, "a device wait ran out (code %d)", (int)s.h_small[1]);
     }
     {
@@ -825,6 +864,35 @@ int heur_submit_batch(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *s
     }
     c->slot_cv.notify_one();
     return rc;
+}
+
+int heur_submit_batch(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *states, const uint8_t *g,
+                      uint32_t bound, uint32_t n, uint8_t *h_out, uint32_t *mask_out, uint32_t *minf_out,
+                      float *y_out) {
+    if (!ctx || !minf_out || (n && (!states || !g || !h_out || !mask_out))) return fail(CBDFS_EINVAL, "null argument");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    int rc = check_eval_args(c, heur_id, domain, n);
+    if (rc) return rc;
+    int C = 0;
+    if (y_out && heur_id >= 0 && c->heur_kind[heur_id] == 0) {
+        const NetGPU &net = *c->nets[c->heur_index[heur_id]];
+        C = net.dims[net.L];
+    }
+    return submit_host(c, heur_id, domain, states, g, bound, n, h_out, mask_out, minf_out, C ? y_out : nullptr, C);
+}
+
+int heur_submit_batch_real(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *states, const uint8_t *g,
+                           float bound, uint32_t n, float *h_out, uint32_t *mask_out, float *minf_out) {
+    if (!ctx || !minf_out || (n && (!states || !g || !h_out || !mask_out))) return fail(CBDFS_EINVAL, "null argument");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    uint32_t key, mkey = 0xFFFFFFFFu;
+    int rc = check_eval_args(c, heur_id, domain, n, true);
+    if (rc || (rc = real_bound_key(bound, &key))) return rc;
+    rc = submit_host(c, heur_id, domain, states, g, key, n, nullptr, mask_out, &mkey, h_out, 1);
+    if (rc) return rc;
+    if (mkey == 0xFFFFFFFFu) *minf_out = INFINITY;
+    else memcpy(minf_out, &mkey, 4);
+    return CBDFS_OK;
 }
 
 int cbdfs_eval_profile(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_states,

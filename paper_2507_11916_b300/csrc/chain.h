@@ -43,12 +43,13 @@ struct ChainParams {
                                    // network (the separate last layer reads BF16); -1 none
     int C;                         // outputs of the last layer
     int head_kind, max_with_md;
+    float h_offset;                // CBDFS_HEAD_REAL: added to y
     const float *w_last, *b_last;  // [C][dims[nh]], [C]
     const uint8_t *g;
-    uint32_t bound;
-    uint8_t *h;
+    uint32_t bound;                // CBDFS_HEAD_REAL: the FP32 bound's bit pattern
+    uint8_t *h;                    // may be null for CBDFS_HEAD_REAL
     uint32_t *mask, *minf;
-    float *y;
+    float *y;                      // raw outputs; CBDFS_HEAD_REAL: the real h
     int *err;
     unsigned long long *trace;     // optional: [grid][trace_tiles][8] %globaltimer stamps
     int trace_tiles;

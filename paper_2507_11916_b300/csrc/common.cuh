@@ -55,6 +55,7 @@ void train_free(struct Ctx *c, TrainState *T);
 
 struct NetGPU {
     int domain = 0, L = 0, prec = 0, head = 0, max_with_md = 0;
+    float h_offset = 0.f;              // CBDFS_HEAD_REAL: added to y
     int dims[kMaxLayers + 1] = {};
     int k1pad = 0;                     // one-hot width padded to the MMA K block
     // tensor-core layers 0..L-2: low-precision weights [dims[l+1]][Kpad] (K-major)
@@ -147,6 +148,9 @@ int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
 
 // a slot's outputs, one allocation: h [max_batch_pad] bytes, then mask [max_batch_pad / 32]
 // words, then minf (one word)
+// a network with the real-valued head (FP32 bounds and f-costs)
+bool heur_is_real(const Ctx *c, int heur_id);
+
 inline size_t slot_out_bytes(const Ctx *c) { return (size_t)c->max_batch_pad + c->max_batch_pad / 8 + 4; }
 
 // per-domain facts
@@ -360,6 +364,22 @@ __device__ __forceinline__ bool rc_is_goal(uint64_t w0, uint64_t w1) {
     for (int k = 0; k < 12; ++k) g1 |= (uint64_t)(k * 2) << (5 * k);
     return w0 == g0 && w1 == g1;
 }
+
+// ---- the real-valued regression rule (CBDFS_HEAD_REAL) ----
+// h = max(y + offset, 0), max'ed with the Manhattan distance md (md < 0: none), 0 at the
+// goal.  f = g + h is an FP32 sum; bounds and least-f values travel as FP32 bit patterns,
+// which order like the values since f >= 0 (the integer heads' uint32 compares and
+// atomicMin then serve both).  NaN outputs give h = 0 (fmaxf drops NaN).
+__device__ __forceinline__ float real_h(float y, float offset, int md, bool goal) {
+    const float h = fmaxf(fmaxf(__fadd_rn(y, offset), 0.f), (float)md);
+    return goal ? 0.f : h;
+}
+__device__ __forceinline__ uint32_t real_f_key(uint32_t g, float h) {
+    return __float_as_uint(__fadd_rn((float)g, h));
+}
+// the uint8 h written beside a real h: its ceiling (an admissible integer h when h is, since
+// path costs are integers), clamped to 255
+__device__ __forceinline__ uint8_t real_h_u8(float h) { return (uint8_t)fminf(ceilf(h), 255.f); }
 
 }  // namespace dev
 }  // namespace cbdfs

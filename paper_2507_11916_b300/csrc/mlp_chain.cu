@@ -151,35 +151,43 @@ __device__ __forceinline__ void finish_row(const ChainParams &P, uint32_t row_g,
     uint32_t f = 0xFFFFFFFFu;
     bool pass = false;
     if (valid) {
-        int hv;
-        if (P.head_kind == CBDFS_HEAD_REGRESSION) {
-            hv = (int)fminf(fmaxf(rintf(yv[0]), 0.f), 255.f);
-        } else {
-            int best = 0;
-            float bv = yv[0];
-#pragma unroll
-            for (int c = 1; c < CMAX; ++c)
-                if (c < P.C && yv[c] > bv) { bv = yv[c]; best = c; }
-            hv = best;
-        }
         bool goal;
+        int md = -1;
         if (DOMAIN == CBDFS_DOM_RC3) {
             const ulonglong2 w = reinterpret_cast<const ulonglong2 *>(P.states)[row_g];
             goal = rc_is_goal(w.x, w.y);
         } else {
             constexpr int SIDE = DOMAIN == CBDFS_DOM_STP3 ? 3 : 4;
             const uint64_t s = P.states[row_g];
-            if (P.max_with_md) hv = max(hv, manhattan<SIDE>(s));
+            if (P.max_with_md) md = manhattan<SIDE>(s);
             goal = stp_is_goal<SIDE>(s);
         }
-        hv = goal ? 0 : min(hv, 255);
-        P.h[row_g] = (uint8_t)hv;
-        f = (uint32_t)P.g[row_g] + (uint32_t)hv;
-        pass = f <= P.bound;
-        if (P.y)
+        if (P.head_kind == CBDFS_HEAD_REAL) {
+            const float hr = real_h(yv[0], P.h_offset, md, goal);
+            if (P.h) P.h[row_g] = real_h_u8(hr);
+            if (P.y) P.y[row_g] = hr;
+            f = real_f_key(P.g[row_g], hr);
+        } else {
+            int hv;
+            if (P.head_kind == CBDFS_HEAD_REGRESSION) {
+                hv = (int)fminf(fmaxf(rintf(yv[0]), 0.f), 255.f);
+            } else {
+                int best = 0;
+                float bv = yv[0];
 #pragma unroll
-            for (int c = 0; c < CMAX; ++c)
-                if (c < P.C) P.y[(size_t)row_g * P.C + c] = yv[c];
+                for (int c = 1; c < CMAX; ++c)
+                    if (c < P.C && yv[c] > bv) { bv = yv[c]; best = c; }
+                hv = best;
+            }
+            hv = goal ? 0 : min(max(hv, md), 255);
+            P.h[row_g] = (uint8_t)hv;
+            f = (uint32_t)P.g[row_g] + (uint32_t)hv;
+            if (P.y)
+#pragma unroll
+                for (int c = 0; c < CMAX; ++c)
+                    if (c < P.C) P.y[(size_t)row_g * P.C + c] = yv[c];
+        }
+        pass = f <= P.bound;
     }
     const uint32_t bits = __ballot_sync(0xFFFFFFFFu, pass);
     const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, pass ? 0xFFFFFFFFu : f);

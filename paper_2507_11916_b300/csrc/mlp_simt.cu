@@ -132,7 +132,7 @@ template <typename TIn, int DOMAIN, int HEAD>
 __global__ void __launch_bounds__(128)
 k_head(const TIn *__restrict__ act, int K, int C, const float *__restrict__ W,
        const float *__restrict__ bL, const uint64_t *__restrict__ states,
-       const uint8_t *__restrict__ g, uint32_t bound, uint32_t n, int max_with_md,
+       const uint8_t *__restrict__ g, uint32_t bound, uint32_t n, int max_with_md, float offset,
        uint8_t *__restrict__ h_out, uint32_t *__restrict__ mask, uint32_t *__restrict__ minf,
        float *__restrict__ y_out) {
     extern __shared__ float ylog[];  // [4 warps][C]
@@ -164,32 +164,40 @@ k_head(const TIn *__restrict__ act, int K, int C, const float *__restrict__ W,
             if (lane == 0) yw[c] = part + __ldg(bL + c);
         }
         __syncwarp();
-        if (y_out)
+        if (y_out && HEAD != CBDFS_HEAD_REAL)
             for (int c = lane; c < C; c += 32) y_out[(size_t)m * C + c] = yw[c];
         if (lane == 0) {
-            int hv;
-            if (HEAD == CBDFS_HEAD_REGRESSION) {
-                float r = fminf(fmaxf(rintf(yw[0]), 0.f), 255.f);
-                hv = (int)r;
-            } else {
-                int best = 0;
-                float bv = yw[0];
-                for (int c = 1; c < C; ++c)
-                    if (yw[c] > bv) { bv = yw[c]; best = c; }
-                hv = best;
-            }
             bool goal;
+            int md = -1;
             if (DOMAIN == CBDFS_DOM_RC3) {
                 goal = rc_is_goal(states[2 * m], states[2 * m + 1]);
             } else {
                 constexpr int SIDE = DOMAIN == CBDFS_DOM_STP3 ? 3 : 4;
                 const uint64_t s = states[m];
-                if (max_with_md) hv = max(hv, manhattan<SIDE>(s));
+                if (max_with_md) md = manhattan<SIDE>(s);
                 goal = stp_is_goal<SIDE>(s);
             }
-            hv = goal ? 0 : min(hv, 255);
-            h_out[m] = (uint8_t)hv;
-            const uint32_t f = (uint32_t)g[m] + (uint32_t)hv;
+            uint32_t f;
+            if (HEAD == CBDFS_HEAD_REAL) {
+                const float hr = real_h(yw[0], offset, md, goal);
+                if (h_out) h_out[m] = real_h_u8(hr);
+                if (y_out) y_out[m] = hr;
+                f = real_f_key(g[m], hr);
+            } else {
+                int hv;
+                if (HEAD == CBDFS_HEAD_REGRESSION) {
+                    hv = (int)fminf(fmaxf(rintf(yw[0]), 0.f), 255.f);
+                } else {
+                    int best = 0;
+                    float bv = yw[0];
+                    for (int c = 1; c < C; ++c)
+                        if (yw[c] > bv) { bv = yw[c]; best = c; }
+                    hv = best;
+                }
+                hv = goal ? 0 : min(max(hv, md), 255);
+                h_out[m] = (uint8_t)hv;
+                f = (uint32_t)g[m] + (uint32_t)hv;
+            }
             pass[loc] = f <= bound;
             fval[loc] = f <= bound ? 0xFFFFFFFFu : f;
         }
@@ -219,7 +227,7 @@ template <typename TIn, int DOMAIN, int HEAD, int CPT>
 __global__ void __launch_bounds__(HT_THREADS)
 k_head_tiled(const TIn *__restrict__ act, int K, int C, const float *__restrict__ W,
              const float *__restrict__ bL, const uint64_t *__restrict__ states,
-             const uint8_t *__restrict__ g, uint32_t bound, uint32_t n, int max_with_md,
+             const uint8_t *__restrict__ g, uint32_t bound, uint32_t n, int max_with_md, float offset,
              uint8_t *__restrict__ h_out, uint32_t *__restrict__ mask, uint32_t *__restrict__ minf,
              float *__restrict__ y_out) {
     constexpr int CPAD = 16 * CPT;
@@ -305,12 +313,12 @@ k_head_tiled(const TIn *__restrict__ act, int K, int C, const float *__restrict_
             if (lane == 0) { pass[loc] = 0; fval[loc] = 0xFFFFFFFFu; }
             continue;
         }
-        if (y_out)
+        if (y_out && HEAD != CBDFS_HEAD_REAL)
             for (int c = lane; c < C; c += 32) y_out[(size_t)m * C + c] = Ys[loc][c];
-        int hv;
+        int hv = 0;
         if (HEAD == CBDFS_HEAD_REGRESSION) {
             hv = (int)fminf(fmaxf(rintf(Ys[loc][0]), 0.f), 255.f);
-        } else {
+        } else if (HEAD == CBDFS_HEAD_CLASSIFIER) {
             // argmax, lowest index on ties
             float bv = -INFINITY;
             int bi = 0x7FFFFFFF;
@@ -326,17 +334,26 @@ k_head_tiled(const TIn *__restrict__ act, int K, int C, const float *__restrict_
         }
         if (lane == 0) {
             bool goal;
+            int md = -1;
             if (DOMAIN == CBDFS_DOM_RC3) {
                 goal = rc_is_goal(states[2 * m], states[2 * m + 1]);
             } else {
                 constexpr int SIDE = DOMAIN == CBDFS_DOM_STP3 ? 3 : 4;
                 const uint64_t s = states[m];
-                if (max_with_md) hv = max(hv, manhattan<SIDE>(s));
+                if (max_with_md) md = manhattan<SIDE>(s);
                 goal = stp_is_goal<SIDE>(s);
             }
-            hv = goal ? 0 : min(hv, 255);
-            h_out[m] = (uint8_t)hv;
-            const uint32_t f = (uint32_t)g[m] + (uint32_t)hv;
+            uint32_t f;
+            if (HEAD == CBDFS_HEAD_REAL) {
+                const float hr = real_h(Ys[loc][0], offset, md, goal);
+                if (h_out) h_out[m] = real_h_u8(hr);
+                if (y_out) y_out[m] = hr;
+                f = real_f_key(g[m], hr);
+            } else {
+                hv = goal ? 0 : min(max(hv, md), 255);
+                h_out[m] = (uint8_t)hv;
+                f = (uint32_t)g[m] + (uint32_t)hv;
+            }
             pass[loc] = f <= bound;
             fval[loc] = f <= bound ? 0xFFFFFFFFu : f;
         }
@@ -355,38 +372,46 @@ k_head_tiled(const TIn *__restrict__ act, int K, int C, const float *__restrict_
 
 template <typename TIn, int DOMAIN, int HEAD>
 int head_tiled(const TIn *act, int K, int C, const float *W, const float *b, const uint64_t *states,
-               const uint8_t *g, uint32_t bound, uint32_t n, int md, uint8_t *h, uint32_t *mask,
-               uint32_t *minf, float *y, cudaStream_t st) {
+               const uint8_t *g, uint32_t bound, uint32_t n, int md, float off, uint8_t *h,
+               uint32_t *mask, uint32_t *minf, float *y, cudaStream_t st) {
     const unsigned blocks = (n + HT_BM - 1) / HT_BM;
-#define HT_LAUNCH(CPT) k_head_tiled<TIn, DOMAIN, HEAD, CPT><<<blocks, HT_THREADS, 0, st>>>(act, K, C, W, b, states, g, bound, n, md, h, mask, minf, y)
-    if (C <= 16) HT_LAUNCH(1);
-    else if (C <= 32) HT_LAUNCH(2);
-    else if (C <= 64) HT_LAUNCH(4);
-    else if (C <= 96) HT_LAUNCH(6);
-    else HT_LAUNCH(8);
+#define HT_LAUNCH(CPT) k_head_tiled<TIn, DOMAIN, HEAD, CPT><<<blocks, HT_THREADS, 0, st>>>(act, K, C, W, b, states, g, bound, n, md, off, h, mask, minf, y)
+    if (HEAD == CBDFS_HEAD_REAL || C <= 16) {  // a real-valued head has one output
+        HT_LAUNCH(1);
+    } else if constexpr (HEAD != CBDFS_HEAD_REAL) {
+        if (C <= 32) HT_LAUNCH(2);
+        else if (C <= 64) HT_LAUNCH(4);
+        else if (C <= 96) HT_LAUNCH(6);
+        else HT_LAUNCH(8);
+    }
 #undef HT_LAUNCH
+    CUDA_TRY(cudaGetLastError());
+    return CBDFS_OK;
+}
+
+template <typename TIn, int DOMAIN, int HEAD>
+int head_any(const TIn *act, int K, int C, const float *W, const float *b, const uint64_t *states,
+             const uint8_t *g, uint32_t bound, uint32_t n, int md, float off, uint8_t *h,
+             uint32_t *mask, uint32_t *minf, float *y, cudaStream_t st) {
+    if (C <= 128 && K % HT_BK == 0 && (size_t)act % 16 == 0 && (size_t)W % 16 == 0)
+        return head_tiled<TIn, DOMAIN, HEAD>(act, K, C, W, b, states, g, bound, n, md, off, h, mask, minf, y, st);
+    const unsigned blocks = (n + 31) / 32;
+    const size_t sm = 4 * C * sizeof(float);
+    k_head<TIn, DOMAIN, HEAD><<<blocks, 128, sm, st>>>(act, K, C, W, b, states, g, bound, n, md, off, h,
+                                                       mask, minf, y);
     CUDA_TRY(cudaGetLastError());
     return CBDFS_OK;
 }
 
 template <typename TIn, int DOMAIN>
 int head_dom(int head, const TIn *act, int K, int C, const float *W, const float *b,
-             const uint64_t *states, const uint8_t *g, uint32_t bound, uint32_t n, int md,
+             const uint64_t *states, const uint8_t *g, uint32_t bound, uint32_t n, int md, float off,
              uint8_t *h, uint32_t *mask, uint32_t *minf, float *y, cudaStream_t st) {
-    if (C <= 128 && K % HT_BK == 0 && (size_t)act % 16 == 0 && (size_t)W % 16 == 0)
-        return head == CBDFS_HEAD_REGRESSION
-                   ? head_tiled<TIn, DOMAIN, CBDFS_HEAD_REGRESSION>(act, K, C, W, b, states, g, bound, n, md, h, mask, minf, y, st)
-                   : head_tiled<TIn, DOMAIN, CBDFS_HEAD_CLASSIFIER>(act, K, C, W, b, states, g, bound, n, md, h, mask, minf, y, st);
-    const unsigned blocks = (n + 31) / 32;
-    const size_t sm = 4 * C * sizeof(float);
     if (head == CBDFS_HEAD_REGRESSION)
-        k_head<TIn, DOMAIN, CBDFS_HEAD_REGRESSION><<<blocks, 128, sm, st>>>(
-            act, K, C, W, b, states, g, bound, n, md, h, mask, minf, y);
-    else
-        k_head<TIn, DOMAIN, CBDFS_HEAD_CLASSIFIER><<<blocks, 128, sm, st>>>(
-            act, K, C, W, b, states, g, bound, n, md, h, mask, minf, y);
-    CUDA_TRY(cudaGetLastError());
-    return CBDFS_OK;
+        return head_any<TIn, DOMAIN, CBDFS_HEAD_REGRESSION>(act, K, C, W, b, states, g, bound, n, md, off, h, mask, minf, y, st);
+    if (head == CBDFS_HEAD_CLASSIFIER)
+        return head_any<TIn, DOMAIN, CBDFS_HEAD_CLASSIFIER>(act, K, C, W, b, states, g, bound, n, md, off, h, mask, minf, y, st);
+    return head_any<TIn, DOMAIN, CBDFS_HEAD_REAL>(act, K, C, W, b, states, g, bound, n, md, off, h, mask, minf, y, st);
 }
 
 }  // namespace
@@ -413,17 +438,18 @@ int sgemm_relu(const float *A, const float *W, const float *b, float *C, int M, 
 
 int head(bool bf16_in, int domain, int head_kind, const void *act, int K, int C, const float *W,
          const float *b, const uint64_t *states, const uint8_t *g, uint32_t bound, uint32_t n,
-         int max_with_md, uint8_t *h, uint32_t *mask, uint32_t *minf, float *y, cudaStream_t st) {
+         int max_with_md, float offset, uint8_t *h, uint32_t *mask, uint32_t *minf, float *y,
+         cudaStream_t st) {
     if (bf16_in) {
         auto a = static_cast<const __nv_bfloat16 *>(act);
-        if (domain == CBDFS_DOM_STP3) return head_dom<__nv_bfloat16, CBDFS_DOM_STP3>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, h, mask, minf, y, st);
-        if (domain == CBDFS_DOM_STP4) return head_dom<__nv_bfloat16, CBDFS_DOM_STP4>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, h, mask, minf, y, st);
-        return head_dom<__nv_bfloat16, CBDFS_DOM_RC3>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, h, mask, minf, y, st);
+        if (domain == CBDFS_DOM_STP3) return head_dom<__nv_bfloat16, CBDFS_DOM_STP3>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, offset, h, mask, minf, y, st);
+        if (domain == CBDFS_DOM_STP4) return head_dom<__nv_bfloat16, CBDFS_DOM_STP4>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, offset, h, mask, minf, y, st);
+        return head_dom<__nv_bfloat16, CBDFS_DOM_RC3>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, offset, h, mask, minf, y, st);
     }
     auto a = static_cast<const float *>(act);
-    if (domain == CBDFS_DOM_STP3) return head_dom<float, CBDFS_DOM_STP3>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, h, mask, minf, y, st);
-    if (domain == CBDFS_DOM_STP4) return head_dom<float, CBDFS_DOM_STP4>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, h, mask, minf, y, st);
-    return head_dom<float, CBDFS_DOM_RC3>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, h, mask, minf, y, st);
+    if (domain == CBDFS_DOM_STP3) return head_dom<float, CBDFS_DOM_STP3>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, offset, h, mask, minf, y, st);
+    if (domain == CBDFS_DOM_STP4) return head_dom<float, CBDFS_DOM_STP4>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, offset, h, mask, minf, y, st);
+    return head_dom<float, CBDFS_DOM_RC3>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, offset, h, mask, minf, y, st);
 }
 
 }  // namespace cbdfs

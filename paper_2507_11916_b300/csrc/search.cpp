@@ -15,7 +15,9 @@
 //     batch's least-f-above-bound.
 // So every completed iteration expands and generates exactly the nodes a serial CB-DFS
 // with the same h would; only the order differs.
+#include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <thread>
 
@@ -86,7 +88,7 @@ struct TreeNode {
     int parent;
     int8_t move;
     uint8_t g;
-    uint8_t h;                // pruning heuristic
+    float h;                  // pruning heuristic (an integer unless it is real-valued)
     int first_child, n_child;
 };
 
@@ -469,10 +471,27 @@ struct Worker {
 // ---------------------------------------------------------------------------------------
 // solve
 // ---------------------------------------------------------------------------------------
+// f-costs as the kernels' keys: an integer f, or an FP32 f's bit pattern for a real-valued
+// heuristic (f >= 0, so keys order like the values)
+inline uint32_t f_key(bool real, uint32_t g, float h) {
+    if (!real) return g + (uint32_t)h;
+    const float f = (float)g + h;
+    uint32_t k;
+    memcpy(&k, &f, 4);
+    return k;
+}
+inline float key_value(uint32_t k) {
+    float f;
+    memcpy(&f, &k, 4);
+    return f;
+}
+
 struct Solver {
     Ctx *c;
     Domain D;
     int heur, prune;
+    bool real = false;             // the pruning heuristic is real-valued (FP32 f-costs)
+    float *d_hreal = nullptr;      // device: real h of a batch of initial-tree states
     cbdfs_search_cfg cfg;
     std::vector<TreeNode> tree;
     std::vector<int> level_start;  // tree nodes of depth d: [level_start[d], level_start[d+1])
@@ -487,10 +506,15 @@ struct Solver {
     Solver(Ctx *c_, int dom) : c(c_), D(dom) {}
 
     // evaluate h (pruning heuristic) for a list of states synchronously on slot slots[0]
-    int eval_states(const std::vector<State> &st, std::vector<uint8_t> &h) {
+    int eval_states(const std::vector<State> &st, std::vector<float> &h) {
         Slot &sl = c->slots[slots[0]];
         const int w = D.words;
         h.resize(st.size());
+        std::vector<uint8_t> h8(st.size());
+        if (real && !d_hreal) {
+            int rc = dev_alloc(c, (void **)&d_hreal, sizeof(float) * c->max_batch_pad);
+            if (rc) return rc;
+        }
         std::vector<uint64_t> buf;
         std::vector<uint8_t> g;
         std::vector<uint32_t> mask;
@@ -511,14 +535,18 @@ struct Solver {
                 int rc = run_eval(c, sl, heur, D.dom, sl.d_states, sl.d_g, 255, n, sl.d_h, sl.d_mask, sl.d_minf, nullptr, s);
                 if (rc) return rc;
             }
-            int rc = run_eval(c, sl, prune, D.dom, sl.d_states, sl.d_g, 255, n, sl.d_h, sl.d_mask, sl.d_minf, nullptr, s);
+            int rc = run_eval(c, sl, prune, D.dom, sl.d_states, sl.d_g, 255, n, sl.d_h, sl.d_mask, sl.d_minf,
+                              real ? d_hreal : nullptr, s);
             if (rc) return rc;
-            CUDA_TRY(cudaMemcpyAsync(h.data() + o, sl.d_h, n, cudaMemcpyDeviceToHost, s));
+            if (real) CUDA_TRY(cudaMemcpyAsync(h.data() + o, d_hreal, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+            else CUDA_TRY(cudaMemcpyAsync(h8.data() + o, sl.d_h, n, cudaMemcpyDeviceToHost, s));
             CUDA_TRY(cudaMemcpyAsync(&minf, sl.d_minf, 4, cudaMemcpyDeviceToHost, s));
             CUDA_TRY(cudaStreamSynchronize(s));
             evaluated += n;
             nbatches++;
         }
+        if (!real)
+            for (size_t i = 0; i < st.size(); ++i) h[i] = (float)h8[i];
         return CBDFS_OK;
     }
 
@@ -564,10 +592,10 @@ struct Solver {
         for (int i = level_start[depth]; i < (int)tree.size(); ++i) tree[i].n_child = 0;
         std::vector<State> st(tree.size());
         for (size_t i = 0; i < tree.size(); ++i) st[i] = tree[i].s;
-        std::vector<uint8_t> h;
+        std::vector<float> h;
         int rc = eval_states(st, h);
         if (rc) return rc;
-        for (size_t i = 0; i < tree.size(); ++i) tree[i].h = D.is_goal(tree[i].s) ? 0 : h[i];
+        for (size_t i = 0; i < tree.size(); ++i) tree[i].h = D.is_goal(tree[i].s) ? 0.f : h[i];
         return CBDFS_OK;
     }
 
@@ -601,7 +629,7 @@ struct Solver {
             for (int i = level_start[d]; i < level_start[d + 1]; ++i) {
                 const TreeNode &t = tree[i];
                 if (t.parent >= 0 && !exp[t.parent]) continue;
-                const uint32_t f = (uint32_t)t.g + t.h;
+                const uint32_t f = f_key(real, t.g, t.h);
                 if (f > bound) {
                     minf = std::min(minf, f);
                     continue;
@@ -691,7 +719,10 @@ struct Solver {
             o.path.insert(o.path.end(), S.best_path.begin() + 1, S.best_path.end());
         }
         if (c->cancel.load()) return fail(CBDFS_ECANCELED, "canceled");
-        if (S.stop.load() && !S.found.load() && !S.cut.load()) {
+        // stopped by the deadline or the node limit (not by the expansion limit, nor by a goal
+        // in first-goal mode): an iteration cut short reports an error even after a goal,
+        // since a later part of it may hold a cheaper one
+        if (S.stop.load() && !S.cut.load() && !(S.found.load() && !S.complete)) {
             if (S.has_deadline && Clock::now() > S.deadline) return fail(CBDFS_ETIMEDOUT, "time limit reached");
             if (cfg.node_limit) return fail(CBDFS_ECANCELED, "node limit reached");
         }
@@ -704,7 +735,8 @@ struct Solver {
     void record(cbdfs_result *out, uint32_t bound, int64_t limit, const IterOut &o) {
         const int i = out->n_iters;
         if (i < CBDFS_MAX_ITERS) {
-            out->iter_bound[i] = bound;
+            out->iter_bound[i] = real ? 0 : bound;
+            out->iter_bound_real[i] = real ? (double)key_value(bound) : (double)bound;
             out->iter_expanded[i] = o.expanded;
             out->iter_generated[i] = o.generated;
             out->iter_limit[i] = limit;
@@ -725,7 +757,7 @@ struct Solver {
 
     // Algorithm 1: bound = h(root); CB-DFS; UpdateThreshold = least f above the bound.
     int ida(cbdfs_result *out) {
-        uint32_t bound = tree[0].h;
+        uint32_t bound = f_key(real, 0, tree[0].h);
         for (;;) {
             IterOut o;
             int rc = cbdfs(bound, -1, o);
@@ -745,7 +777,7 @@ struct Solver {
     int bts(cbdfs_result *out) {
         const int64_t c1 = cfg.bts_c1 > 0 ? cfg.bts_c1 : 2, c2 = cfg.bts_c2 > 0 ? cfg.bts_c2 : 8;
         int64_t N = cfg.bts_n0 ? (int64_t)cfg.bts_n0 : 10000;
-        int64_t nxt = (int64_t)tree[0].h + 1;
+        int64_t nxt = (int64_t)tree[0].h + 1;  // an integer h
         IterOut done;
         int code = 0;  // 1 found, 2 exhausted
         auto run = [&](int64_t b, int64_t limit, IterOut &o) -> int {
@@ -805,6 +837,80 @@ struct Solver {
         if (code == 2) return fail(CBDFS_ENOTFOUND, "no solution: the tree is exhausted");
         return finish(out, done);
     }
+
+    // BTS over real bounds (a real-valued heuristic): the schedule of bts() in FP32, except
+    // that the binary search between the last small bound lo and the first big one hi runs
+    // while some f-cost lies strictly between them (lo's least f above its bound is below
+    // hi) and probes max((lo+hi)/2, that f), so that every probe can change the tree.  With
+    // integer f-costs it accepts the bounds bts() accepts (the least big bound).
+    int bts_real(cbdfs_result *out) {
+        const int64_t c1 = cfg.bts_c1 > 0 ? cfg.bts_c1 : 2, c2 = cfg.bts_c2 > 0 ? cfg.bts_c2 : 8;
+        int64_t N = cfg.bts_n0 ? (int64_t)cfg.bts_n0 : 10000;
+        float nxt = tree[0].h + 1.0f;
+        IterOut done;
+        int code = 0;  // 1 found, 2 exhausted
+        auto run = [&](float b, int64_t limit, IterOut &o) -> int {
+            o = IterOut();
+            const uint32_t key = f_key(true, 0, b);
+            int rc = cbdfs(key, limit, o);
+            record(out, key, limit, o);
+            if (rc) return rc;
+            if (!o.cut && o.found) { done = o; code = 1; }
+            else if (!o.cut && o.minf == kNone) code = 2;
+            return CBDFS_OK;
+        };
+        auto big = [&](const IterOut &o) { return o.cut || o.expanded >= c1 * N; };
+        for (;;) {
+            const int64_t limit = c2 * N;
+            IterOut r;
+            int rc = run(nxt, limit, r);
+            if (rc) return rc;
+            if (code) break;
+            if (r.cut) {
+                if ((rc = run(nxt, -1, r))) return rc;
+                if (code) break;
+                N = std::max<int64_t>(r.expanded, 1);
+                nxt = key_value(r.minf);
+                continue;
+            }
+            if (r.expanded >= c1 * N) {
+                N = r.expanded;
+                nxt = key_value(r.minf);
+                continue;
+            }
+            float lo = nxt, lo_minf = key_value(r.minf), hi = 0.f;
+            IterOut hi_r;
+            bool have_hi = false;
+            for (int j = 0; j < 120 && !have_hi; ++j) {
+                const float b = nxt + std::ldexp(1.0f, j);
+                IterOut rr;
+                if ((rc = run(b, limit, rr))) return rc;
+                if (code) break;
+                if (big(rr)) { hi = b; hi_r = rr; have_hi = true; }
+                else { lo = b; lo_minf = key_value(rr.minf); }
+            }
+            if (code) break;
+            if (!have_hi) return fail(CBDFS_ENOTFOUND, "BTS: no bound below 2^120 reaches the node count");
+            while (lo_minf < hi) {
+                float mid = std::max((lo + hi) / 2.0f, lo_minf);
+                if (mid >= hi) mid = lo_minf;
+                IterOut rr;
+                if ((rc = run(mid, limit, rr))) return rc;
+                if (code) break;
+                if (big(rr)) { hi = mid; hi_r = rr; }
+                else { lo = mid; lo_minf = key_value(rr.minf); }
+            }
+            if (code) break;
+            if (hi_r.cut) {
+                if ((rc = run(hi, -1, hi_r))) return rc;
+                if (code) break;
+            }
+            N = std::max<int64_t>(hi_r.expanded, 1);
+            nxt = key_value(hi_r.minf);
+        }
+        if (code == 2) return fail(CBDFS_ENOTFOUND, "no solution: the tree is exhausted");
+        return finish(out, done);
+    }
 };
 
 }  // namespace
@@ -845,6 +951,7 @@ int cbdfs_solve(cbdfs_ctx *ctx, int domain, const uint64_t *start, int algo, int
     sv.cfg = cfg;
     sv.heur = heur_id;
     sv.prune = cfg.fixed_tree_heur != CBDFS_HEUR_NONE ? cfg.fixed_tree_heur : heur_id;
+    sv.real = heur_is_real(c, sv.prune);
     if (cfg.time_limit_s > 0)
         sv.deadline = t0 + std::chrono::microseconds((int64_t)(cfg.time_limit_s * 1e6));
     // take every free host slot (at least one; waits for one if all are busy)
@@ -877,7 +984,8 @@ int cbdfs_solve(cbdfs_ctx *ctx, int domain, const uint64_t *start, int algo, int
         sv.batches.push_back(std::move(b));
     }
     if (!rc) rc = sv.generate_work(sv.D.make(start));
-    if (!rc) rc = algo == CBDFS_ALGO_IDA ? sv.ida(out) : sv.bts(out);
+    if (!rc) rc = algo == CBDFS_ALGO_IDA ? sv.ida(out) : sv.real ? sv.bts_real(out) : sv.bts(out);
+    if (sv.d_hreal) dev_free(c, sv.d_hreal, sizeof(float) * c->max_batch_pad);
     for (auto &b : sv.batches) {
         cudaFreeHost(b->states);
         cudaFreeHost(b->g);
@@ -890,6 +998,7 @@ int cbdfs_solve(cbdfs_ctx *ctx, int domain, const uint64_t *start, int algo, int
         for (int i : sv.slots) c->slots[i].busy = false;
     }
     c->slot_cv.notify_all();
+    out->real_valued = sv.real;
     out->batches = sv.nbatches;
     out->evaluated = sv.evaluated;
     const double nb = (double)std::max<int64_t>(1, sv.search_batches);

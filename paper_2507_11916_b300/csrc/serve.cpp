@@ -368,6 +368,7 @@ int heur_request_submit(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t 
     if (heur_id >= (int)c->heur_kind.size() || heur_id < CBDFS_HEUR_MD ||
         (heur_id == CBDFS_HEUR_MD && domain == CBDFS_DOM_RC3))
         return fail(CBDFS_EINVAL, "heuristic id %d", heur_id);
+    if (heur_is_real(c, heur_id)) return fail(CBDFS_EINVAL, "heuristic %d is real-valued", heur_id);
     auto r = std::make_shared<Request>();
     r->heur = heur_id;
     r->domain = domain;
