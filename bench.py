@@ -252,6 +252,71 @@ def search_rates(P, ctx, hids, seconds, work_num=1024):
     return out
 
 
+def md_noise_net(seed=21):
+    """A 15-puzzle regression network with real outputs y = MD + u1 - u2 (dense 256-1024-1024-
+    512-1, Kaiming weights everywhere else): hidden unit 0 of the first layer sums the Manhattan
+    contribution of each (tile, cell) input, units 1 and 2 sum seeded weights uniform in
+    [0, 0.12) over the 16 inputs that are one (so u1, u2 lie in [0, 1.92]); the next layers pass
+    units 0-2 on and the last layer forms y.  With the offset -2.2, h = max(y - 2.2, 0) is
+    below MD (admissible) and takes many distinct fractional values -- the regime where IDA*'s
+    real thresholds creep up (section "Regression-Based Neural Heuristics", Table 2).  A
+    stand-in for the paper's trained cube regression model, which is not available."""
+    Ws, bs = W.net_weights([256, 1024, 1024, 512, 1], "kaiming", seed)
+    u = (W.splitmix64_array(W.seed_for(seed, 100), 512) >> np.uint64(11)).astype(np.float64) / 2.0 ** 53
+    Ws[0][0:3] = 0.0
+    for t in range(1, 16):
+        for c in range(16):
+            Ws[0][0, t * 16 + c] = abs(c // 4 - t // 4) + abs(c % 4 - t % 4)
+    Ws[0][1] = 0.12 * u[:256]
+    Ws[0][2] = 0.12 * u[256:]
+    for l in (1, 2):
+        Ws[l][0:3] = 0.0
+        for k in range(3):
+            Ws[l][k, k] = 1.0
+    for l in range(3):
+        bs[l][0:3] = 0.0
+    Ws[3][:] = 0.0
+    Ws[3][0, 0:3] = (1.0, 1.0, -1.0)
+    bs[3][:] = 0.0
+    return Ws, bs
+
+
+def regression_leg(P, args):
+    """Batch IDA* against Batch BTS with a real-valued regression heuristic (Table 2's
+    experiment on the 15-puzzle with the synthetic MD + noise network, BF16, offset -2.2):
+    per instance the cost, searches, expanded nodes and seconds of each; IDA* is stopped at
+    --regression-seconds and reported unsolved, as the paper reports Batch IDA* runs that
+    did not finish."""
+    ctx = P.cbdfs_create(0, max_batch=8192, n_slots=4)
+    try:
+        Ws, bs = md_noise_net()
+        hid = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, P.PREC_BF16, P.HEAD_REAL, 0, h_offset=-2.2)
+        threads = min(32, os.cpu_count() or 4)
+        starts = [(24, 7000), (24, 7001), (28, 7002), (30, 7001)]
+        cfg = dict(threads=threads, work_num=256, batch=8192, timeout_us=500)
+        rows = []
+        for moves, seed in starts:
+            s = P.cbdfs_apply_moves(P.DOM_STP4, W.stp_goal(4), W.stp_walk(4, moves, W.seed_for(W.TAG_C1, seed)))
+            row = {"walk": moves, "seed": seed, "md": P.cbdfs_manhattan(P.DOM_STP4, s)}
+            for name, algo in (("bts", P.ALGO_BTS), ("ida", P.ALGO_IDA)):
+                r = P.cbdfs_solve(ctx, P.DOM_STP4, s, algo, hid, partial_ok=True,
+                                  time_limit_s=args.regression_seconds, bts_n0=1000, **cfg)
+                solved = r["status"] == 0
+                row[name] = {"cost": r["cost"] if solved else None, "solved": solved,
+                             "searches": r["n_iters"], "expanded": r["expanded"],
+                             "seconds": r["seconds"], "expanded_per_s": r["expanded"] / max(r["seconds"], 1e-9),
+                             "avg_batch": r["evaluated"] / max(r["batches"], 1)}
+            rows.append(row)
+        both = [r for r in rows if r["ida"]["solved"] and r["bts"]["solved"]]
+        return {"network": "256-1024-1024-512-1 BF16, y = MD + u1 - u2 (synthetic), h = max(y - 2.2, 0)",
+                "instances": rows, "time_limit_s": args.regression_seconds, "threads": threads,
+                "equal_cost_where_both_solved": all(r["ida"]["cost"] == r["bts"]["cost"] for r in both),
+                "ida_unsolved": sum(not r["ida"]["solved"] for r in rows),
+                "bts_unsolved": sum(not r["bts"]["solved"] for r in rows)}
+    finally:
+        P.cbdfs_destroy(ctx)
+
+
 def train_leg(P, args):
     """The training configuration: 6-6-3 additive PDB built on the GPU, 10M walk states
     labelled by it, the 81-class network trained 5 epochs (batch 8192, Adam 1e-3); then the
@@ -740,6 +805,8 @@ def run_ours(args):
         line["kernel_micro"] = kernel_micro_leg(P, args)
     if rank == 0 and not args.no_pdb:
         line["pdb_gather"] = pdb_leg(P, args)
+    if rank == 0 and not args.no_regression:
+        line["regression_ida_vs_bts"] = regression_leg(P, args)
     if rank == 0 and not args.no_train:
         line["train"] = train_leg(P, args)
     if rank == 0 and not args.no_serve:
@@ -800,6 +867,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-pdb", action="store_true", help="skip the PDB gather leg")
     ap.add_argument("--no-nets", action="store_true", help="skip the per-network states/s leg")
+    ap.add_argument("--no-regression", action="store_true",
+                    help="skip the real-valued regression heuristic leg (IDA* against BTS)")
+    ap.add_argument("--regression-seconds", type=float, default=10.0)
     ap.add_argument("--pdb-states", type=int, default=1 << 22)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--search-seconds", type=float, default=3.0)
