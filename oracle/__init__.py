@@ -28,7 +28,9 @@ Section map (paper sections, equations and algorithms):
     reading (parity unpinned against the paper beyond the costs and the integer case).
   * network heuristic ............................ `mlp_forward`, `h_regression`,
     `h_classifier` (Experimental Setup: a classifier heuristic and a regression heuristic;
-    Background, Heuristics: classes are integer h values)
+    Background, Heuristics: classes are integer h values), `h_quantile` (Related Work: the
+    classification quantile of ordered classes, lowered for admissibility), `h_combo` (the
+    minimum over an ensemble; sums of such minima with MD, Experimental Setup)
   * training ..................................... `train_forward_backward`, `adam_step`
     (Experimental Setup: the models are trained from PDB values).  Not from the paper:
     float64 cross-entropy / MSE back-propagation and Adam as published by Kingma & Ba.
@@ -723,6 +725,53 @@ def bound_test_real(g, h, bound, dtype=np.float64):
     above = f[~ok]
     minf = float(above.min()) if above.size else float("inf")
     return words.astype(np.uint32), minf
+
+
+def h_quantile(logits, q, md=None, goal=None) -> np.ndarray:
+    """The classifier quantile (Related Work: ordered classes let the quantile of the
+    predicted class be lowered for admissibility): with p = softmax(logits), h = the smallest
+    class c with p_0 + ... + p_c >= q (the last class if no partial sum reaches q); optional
+    max with MD; the goal gets 0."""
+    y = np.asarray(logits, np.float64)
+    p = np.exp(y - y.max(axis=1, keepdims=True))
+    p /= p.sum(axis=1, keepdims=True)
+    cdf = np.cumsum(p, axis=1)
+    C = y.shape[1]
+    h = np.array([next((c for c in range(C) if cdf[i, c] >= q), C - 1) for i in range(len(y))], np.int64)
+    if md is not None:
+        h = np.maximum(h, np.asarray(md, np.int64))
+    h = np.minimum(h, 255)
+    if goal is not None:
+        h = np.where(goal, 0, h)
+    return h
+
+
+def h_combo(member_h, group_sizes, md=None, goal=None) -> np.ndarray:
+    """A composite heuristic (Related Work: the minimum over an ensemble keeps a learned
+    heuristic admissible; Experimental Setup: the 15-puzzle h_M adds ensembles trained on PDB
+    minus MD to MD): member_h[m] are the members' h arrays, group after group; h = [md] + the
+    sum over groups of the minimum over the group's members, clamped to 255; the goal gets 0."""
+    hs = [np.asarray(h, np.int64) for h in member_h]
+    total = np.zeros_like(hs[0]) if md is None else np.asarray(md, np.int64).copy()
+    m = 0
+    for k in group_sizes:
+        total = total + np.min(np.stack(hs[m:m + k]), axis=0)
+        m += k
+    total = np.minimum(total, 255)
+    if goal is not None:
+        total = np.where(goal, 0, total)
+    return total
+
+
+def quantile_margin(logits, q, width) -> np.ndarray:
+    """True where a partial sum of softmax(logits) lies within `width` (absolute, per row or
+    scalar) of q: a logit error of that size may move the quantile class."""
+    y = np.asarray(logits, np.float64)
+    p = np.exp(y - y.max(axis=1, keepdims=True))
+    p /= p.sum(axis=1, keepdims=True)
+    cdf = np.cumsum(p, axis=1)
+    w = np.broadcast_to(np.asarray(width, np.float64).reshape(-1, 1) if np.ndim(width) else width, cdf.shape)
+    return (np.abs(cdf - q) < w).any(axis=1)
 
 
 def regression_margin(y, width=1e-2) -> np.ndarray:
