@@ -48,7 +48,12 @@ typedef enum {
 
 typedef enum { CBDFS_DOM_STP3 = 0, CBDFS_DOM_STP4 = 1, CBDFS_DOM_RC3 = 2 } cbdfs_domain;
 typedef enum { CBDFS_PREC_FP32 = 0, CBDFS_PREC_BF16 = 1, CBDFS_PREC_FP8 = 2 } cbdfs_prec;
-typedef enum { CBDFS_HEAD_REGRESSION = 0, CBDFS_HEAD_CLASSIFIER = 1, CBDFS_HEAD_REAL = 2 } cbdfs_head;
+typedef enum {
+    CBDFS_HEAD_REGRESSION = 0,
+    CBDFS_HEAD_CLASSIFIER = 1,
+    CBDFS_HEAD_REAL = 2,
+    CBDFS_HEAD_QUANTILE = 3
+} cbdfs_head;
 typedef enum { CBDFS_ALGO_IDA = 0, CBDFS_ALGO_BTS = 1 } cbdfs_algo;
 
 /* Built-in heuristic ids (network and PDB ids from the load calls are >= 0). */
@@ -90,6 +95,11 @@ size_t cbdfs_mem_used(const cbdfs_ctx *ctx);
  *               when max_with_md != 0, clamped to 255;
  *   classifier: h = argmax over the outputs (lowest index on ties), max'ed with Manhattan
  *               distance when max_with_md != 0.
+ *   quantile:   the classifier quantile (Related Work: ordered classes let the quantile of
+ *               the predicted class be lowered for admissibility): with p = softmax(y) in
+ *               FP32, h = the smallest class c with p_0 + ... + p_c >= quantile (the last
+ *               class if rounding keeps the total below it), max'ed with Manhattan distance
+ *               when max_with_md != 0.
  * Real-valued h (section "Regression-Based Neural Heuristics"; Experimental Setup: the
  * regression model's predictions minus 2.2):
  *   real:       one output; h = max(y + h_offset, 0) in FP32, max'ed with Manhattan distance
@@ -108,6 +118,7 @@ typedef struct {
     int max_with_md;                /* STP only */
     const float *act_scales;        /* FP8 only: L-1 activation scales (host), else NULL */
     float h_offset;                 /* CBDFS_HEAD_REAL: added to y (the paper: -2.2); else 0 */
+    float quantile;                 /* CBDFS_HEAD_QUANTILE: q in (0, 1]; else 0 */
 } cbdfs_net_desc;
 
 /* Copy a network into device memory.  Weights are rounded there to the precision (FP32
@@ -144,6 +155,29 @@ int cbdfs_pdb_load(cbdfs_ctx *ctx, const cbdfs_pdb_desc *d, int *heur_id);
  * Errors: EINVAL (cap too small, bad tiles), ENOMEM, EDEVICE. */
 int pdb_build(cbdfs_ctx *ctx, int domain, const int *pattern_tiles, int k, uint8_t *table_out,
               size_t cap, size_t *entries);
+
+/* ---------------------------------------------------------------------------------------
+ * Composite heuristic (Related Work: the minimum over an ensemble of networks keeps a
+ * learned heuristic admissible; Experimental Setup: the 15-puzzle h_M adds to Manhattan
+ * distance two ensembles, each trained on one pattern's PDB minus Manhattan distance):
+ *   h = [MD if add_md] + sum over groups g of (min over the members of g of h_member),
+ * clamped to 255; the goal gets 0.  Members are loaded heuristic ids (networks with integer
+ * heads, PDBs, CBDFS_HEUR_MD / _ZERO) of the same domain: at most 4 groups of 1..8 members,
+ * 16 members in all.  Every member runs its own pipeline on the batch, then one kernel
+ * combines them and applies the bound test.  Not on the allocation-free entry
+ * (heur_eval_device_static).
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+    int domain;
+    int n_groups;
+    const int *group_size;          /* n_groups member counts */
+    const int *members;             /* the member ids, group after group */
+    int add_md;                     /* sliding-tile domains: add Manhattan distance */
+} cbdfs_combo_desc;
+
+/* *heur_id receives the composite's id.  Errors: EINVAL (members, sizes, domain; a server is
+ * running), ENOMEM, EDEVICE. */
+int cbdfs_combo_load(cbdfs_ctx *ctx, const cbdfs_combo_desc *d, int *heur_id);
 
 /* ---------------------------------------------------------------------------------------
  * Batched heuristic evaluation with the bound test (Algorithm 3: a node is expanded when

@@ -34,7 +34,7 @@ CBDFS_OK, CBDFS_EINVAL, CBDFS_ENOMEM, CBDFS_ETIMEDOUT = 0, -1, -2, -3
 CBDFS_EDEVICE, CBDFS_ECANCELED, CBDFS_ENOTFOUND = -4, -5, -6
 DOM_STP3, DOM_STP4, DOM_RC3 = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
-HEAD_REGRESSION, HEAD_CLASSIFIER, HEAD_REAL = 0, 1, 2
+HEAD_REGRESSION, HEAD_CLASSIFIER, HEAD_REAL, HEAD_QUANTILE = 0, 1, 2, 3
 LOSS_CE, LOSS_MSE = 0, 1
 ALGO_IDA, ALGO_BTS = 0, 1
 HEUR_ZERO, HEUR_MD, HEUR_NONE = -1, -2, -100
@@ -61,7 +61,14 @@ class NetDesc(ctypes.Structure):
                 ("weights", ctypes.POINTER(ctypes.POINTER(ctypes.c_float))),
                 ("biases", ctypes.POINTER(ctypes.POINTER(ctypes.c_float))),
                 ("prec", ctypes.c_int), ("head", ctypes.c_int), ("max_with_md", ctypes.c_int),
-                ("act_scales", ctypes.POINTER(ctypes.c_float)), ("h_offset", ctypes.c_float)]
+                ("act_scales", ctypes.POINTER(ctypes.c_float)), ("h_offset", ctypes.c_float),
+                ("quantile", ctypes.c_float)]
+
+
+class ComboDesc(ctypes.Structure):
+    _fields_ = [("domain", ctypes.c_int), ("n_groups", ctypes.c_int),
+                ("group_size", ctypes.POINTER(ctypes.c_int)), ("members", ctypes.POINTER(ctypes.c_int)),
+                ("add_md", ctypes.c_int)]
 
 
 class PdbDesc(ctypes.Structure):
@@ -130,6 +137,7 @@ _lib.cbdfs_mem_used.argtypes = [_vp]
 _lib.cbdfs_mem_used.restype = ctypes.c_size_t
 _lib.cbdfs_net_load.argtypes = [_vp, ctypes.POINTER(NetDesc), ctypes.POINTER(ctypes.c_int)]
 _lib.cbdfs_pdb_load.argtypes = [_vp, ctypes.POINTER(PdbDesc), ctypes.POINTER(ctypes.c_int)]
+_lib.cbdfs_combo_load.argtypes = [_vp, ctypes.POINTER(ComboDesc), ctypes.POINTER(ctypes.c_int)]
 _lib.pdb_build.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _vp,
                            ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
 _lib.heur_submit_batch.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint32,
@@ -176,7 +184,7 @@ _lib.cbdfs_cancel.restype = None
 
 # every symbol include/cbdfs.h declares
 EXPORTED = ["cbdfs_create", "cbdfs_destroy", "cbdfs_last_error", "cbdfs_mem_used", "cbdfs_net_load",
-            "cbdfs_pdb_load", "pdb_build", "heur_submit_batch", "heur_eval_device",
+            "cbdfs_pdb_load", "cbdfs_combo_load", "pdb_build", "heur_submit_batch", "heur_eval_device",
             "heur_submit_batch_real", "heur_eval_device_real", "heur_eval_device_static",
             "cbdfs_device_status", "cbdfs_eval_profile", "cbdfs_eval_trace", "net_train",
             "cbdfs_train_grad", "cbdfs_net_read", "cbdfs_gen_walk_states", "cbdfs_server_start",
@@ -219,7 +227,7 @@ def cbdfs_mem_used(ctx) -> int:
 
 
 def cbdfs_net_load(ctx, domain, weights, biases, prec=PREC_BF16, head=HEAD_REGRESSION,
-                   max_with_md=0, act_scales=None, h_offset=0.0) -> int:
+                   max_with_md=0, act_scales=None, h_offset=0.0, quantile=0.0) -> int:
     Ws = [np.ascontiguousarray(w, dtype=np.float32) for w in weights]
     bs = [np.ascontiguousarray(b, dtype=np.float32) for b in biases]
     dims = [Ws[0].shape[1]] + [w.shape[0] for w in Ws]
@@ -231,7 +239,7 @@ def cbdfs_net_load(ctx, domain, weights, biases, prec=PREC_BF16, head=HEAD_REGRE
         sc_arr = np.ascontiguousarray(act_scales, dtype=np.float32)
         sc = sc_arr.ctypes.data_as(FP)
     d = NetDesc(domain, len(Ws), (ctypes.c_int * len(dims))(*dims), wp, bp, prec, head,
-                max_with_md, sc, h_offset)
+                max_with_md, sc, h_offset, quantile)
     out = ctypes.c_int()
     _check(_lib.cbdfs_net_load(ctx, ctypes.byref(d), ctypes.byref(out)))
     return out.value
@@ -248,6 +256,18 @@ def cbdfs_pdb_load(ctx, domain, patterns, tables=None) -> int:
                 (ctypes.c_int * len(tiles))(*tiles), tabs)
     out = ctypes.c_int()
     _check(_lib.cbdfs_pdb_load(ctx, ctypes.byref(d), ctypes.byref(out)))
+    return out.value
+
+
+def cbdfs_combo_load(ctx, domain, groups, add_md=False) -> int:
+    """A composite heuristic: [MD] + sum over groups of the minimum over each group's member
+    heuristic ids (groups: a list of lists of ids)."""
+    sizes = [len(g) for g in groups]
+    members = [m for g in groups for m in g]
+    d = ComboDesc(domain, len(groups), (ctypes.c_int * len(sizes))(*sizes),
+                  (ctypes.c_int * max(1, len(members)))(*members), int(bool(add_md)))
+    out = ctypes.c_int()
+    _check(_lib.cbdfs_combo_load(ctx, ctypes.byref(d), ctypes.byref(out)))
     return out.value
 
 

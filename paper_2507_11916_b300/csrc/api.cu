@@ -35,6 +35,9 @@ struct PdbParams {
 int pdb_gather(int domain, const PdbParams &P, const uint64_t *states, uint32_t n, const uint8_t *g,
                uint32_t bound, uint8_t *h, uint32_t *mask, uint32_t *minf, cudaStream_t st);
 int pdb_build_device(Ctx *c, int side, const int *tiles, int k, uint8_t *table, cudaStream_t st);
+int combine(int domain, const ComboParams &C, const uint64_t *states, uint32_t n, const uint8_t *member_h,
+            size_t member_stride, const uint8_t *g, uint32_t bound, uint8_t *h, uint32_t *mask, uint32_t *minf,
+            cudaStream_t st);
 uint64_t npk(int n, int k);
 
 
@@ -347,7 +350,7 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     P.C = net.dims[L];
     P.head_kind = net.head;
     P.max_with_md = net.max_with_md;
-    P.h_offset = net.h_offset;
+    P.head_param = net.head_param();
     P.w_last = net.w32[L - 1];
     P.b_last = net.b32[L - 1];
     P.g = d_g;
@@ -369,7 +372,7 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     if (rc || (rc = mark(s, st)) || P.fused_head) return rc;
     // the last layer (FP32) over the stored BF16 activations of the last hidden layer
     rc = head(true, domain, net.head, s.act[(nh - 1) & 1], net.dims[nh], net.dims[L], net.w32[L - 1],
-              net.b32[L - 1], d_states, d_g, bound, n, net.max_with_md, net.h_offset, d_h, d_mask, d_minf,
+              net.b32[L - 1], d_states, d_g, bound, n, net.max_with_md, net.head_param(), d_h, d_mask, d_minf,
               d_y, st);
     return rc ? rc : mark(s, st);
 }
@@ -382,6 +385,23 @@ int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
     if (int r = mark(s, st)) return r;
     if (heur_id < 0) {
         int r = builtin(heur_id, domain, d_states, n, d_g, bound, d_h, d_mask, d_minf, st);
+        return r ? r : mark(s, st);
+    }
+    if (c->heur_kind[heur_id] == 2) {
+        // composite: every member into its row of the slot's member scratch (their own bound
+        // tests go to scratch too), then the combination with the bound test
+        const ComboGPU &cb = *c->combos[c->heur_index[heur_id]];
+        if (cb.domain != domain) return fail(CBDFS_EINVAL, "composite %d is for another domain", heur_id);
+        if (!s.combo) return fail(CBDFS_EINVAL, "composite heuristics need a context slot's scratch");
+        const size_t stride = c->max_batch_pad;
+        uint32_t *mmask = reinterpret_cast<uint32_t *>(s.combo + (size_t)kComboMaxTotal * stride);
+        uint32_t *mminf = mmask + stride / 32;
+        for (size_t m = 0; m < cb.members.size(); ++m) {
+            int r = run_eval(c, s, cb.members[m], domain, d_states, d_g, 255, n, s.combo + m * stride, mmask, mminf,
+                             nullptr, st);
+            if (r) return r;
+        }
+        int r = combine(domain, cb.P, d_states, n, s.combo, stride, d_g, bound, d_h, d_mask, d_minf, st);
         return r ? r : mark(s, st);
     }
     if (c->heur_kind[heur_id] == 1) {
@@ -416,7 +436,7 @@ int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
             std::swap(a, b);
         }
         rc = head(false, domain, net.head, a, net.dims[L - 1], net.dims[L], net.w32[L - 1], net.b32[L - 1],
-                  d_states, d_g, bound, n, net.max_with_md, net.h_offset, d_h, d_mask, d_minf, d_y, st);
+                  d_states, d_g, bound, n, net.max_with_md, net.head_param(), d_h, d_mask, d_minf, d_y, st);
         return rc ? rc : mark(s, st);
     }
     const bool fp8 = net.prec == CBDFS_PREC_FP8;
@@ -442,7 +462,7 @@ int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
         cur = out_buf;
     }
     rc = head(true, domain, net.head, s.act[cur], net.dims[L - 1], net.dims[L], net.w32[L - 1],
-              net.b32[L - 1], d_states, d_g, bound, n, net.max_with_md, net.h_offset, d_h, d_mask, d_minf,
+              net.b32[L - 1], d_states, d_g, bound, n, net.max_with_md, net.head_param(), d_h, d_mask, d_minf,
               d_y, st);
     return rc ? rc : mark(s, st);
 }
@@ -481,6 +501,7 @@ void cbdfs_destroy(cbdfs_ctx *ctx) {
         dev_free(c, s.counters, sizeof(int) * chain_counter_ints(c));
         dev_free(c, s.onehot, (size_t)c->max_batch_pad * 1024);
         dev_free(c, s.partial, s.partial_bytes);
+        dev_free(c, s.combo, combo_bytes(c));
         if (s.stream) cudaStreamDestroy(s.stream);
         if (s.done) cudaEventDestroy(s.done);
         if (s.h_small) cudaFreeHost(s.h_small);
@@ -559,9 +580,11 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
     if (d->dims[0] != dom_onehot(d->domain))
         return fail(CBDFS_EINVAL, "dims[0]=%d but the domain's one-hot width is %d", d->dims[0], dom_onehot(d->domain));
     if (d->prec < 0 || d->prec > 2) return fail(CBDFS_EINVAL, "precision %d", d->prec);
-    if (d->head != CBDFS_HEAD_REGRESSION && d->head != CBDFS_HEAD_CLASSIFIER && d->head != CBDFS_HEAD_REAL)
-        return fail(CBDFS_EINVAL, "head %d", d->head);
-    if (d->head != CBDFS_HEAD_CLASSIFIER && d->dims[L] != 1) return fail(CBDFS_EINVAL, "a regression head has one output");
+    if (d->head < CBDFS_HEAD_REGRESSION || d->head > CBDFS_HEAD_QUANTILE) return fail(CBDFS_EINVAL, "head %d", d->head);
+    if ((d->head == CBDFS_HEAD_REGRESSION || d->head == CBDFS_HEAD_REAL) && d->dims[L] != 1)
+        return fail(CBDFS_EINVAL, "a regression head has one output");
+    if (d->head == CBDFS_HEAD_QUANTILE ? !(d->quantile > 0.f && d->quantile <= 1.f) : d->quantile != 0.f)
+        return fail(CBDFS_EINVAL, "quantile %g (in (0, 1], and only for the quantile head)", d->quantile);
     if (!std::isfinite(d->h_offset) || (d->head != CBDFS_HEAD_REAL && d->h_offset != 0.f))
         return fail(CBDFS_EINVAL, "h_offset %g (finite, and only for the real-valued head)", d->h_offset);
     if (d->max_with_md && d->domain == CBDFS_DOM_RC3) return fail(CBDFS_EINVAL, "Manhattan distance needs a sliding-tile domain");
@@ -573,6 +596,7 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
     NetGPU &N = *net;
     N.domain = d->domain; N.L = L; N.prec = d->prec; N.head = d->head; N.max_with_md = d->max_with_md;
     N.h_offset = d->h_offset;
+    N.quantile = d->quantile;
     for (int l = 0; l <= L; ++l) N.dims[l] = d->dims[l];
     size_t maxw = 0;
     for (int l = 1; l < L; ++l) maxw = std::max(maxw, (size_t)d->dims[l]);
@@ -691,6 +715,52 @@ int cbdfs_pdb_load(cbdfs_ctx *ctx, const cbdfs_pdb_desc *d, int *heur_id) {
     c->pdbs.push_back(std::move(p));
     c->heur_kind.push_back(1);
     c->heur_index.push_back((int)c->pdbs.size() - 1);
+    *heur_id = (int)c->heur_kind.size() - 1;
+    return CBDFS_OK;
+}
+
+int cbdfs_combo_load(cbdfs_ctx *ctx, const cbdfs_combo_desc *d, int *heur_id) {
+    if (!ctx || !d || !heur_id || !d->group_size || !d->members) return fail(CBDFS_EINVAL, "null argument");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (c->server) return fail(CBDFS_EINVAL, "stop the server before loading a heuristic");
+    if (d->domain < 0 || d->domain > 2) return fail(CBDFS_EINVAL, "domain %d", d->domain);
+    if (d->n_groups < 1 || d->n_groups > kComboMaxGroups)
+        return fail(CBDFS_EINVAL, "n_groups %d outside 1..%d", d->n_groups, kComboMaxGroups);
+    if (d->add_md && d->domain == CBDFS_DOM_RC3) return fail(CBDFS_EINVAL, "Manhattan distance needs a sliding-tile domain");
+    auto cb = std::make_unique<ComboGPU>();
+    cb->domain = d->domain;
+    cb->P.n_groups = d->n_groups;
+    cb->P.add_md = d->add_md ? 1 : 0;
+    int total = 0;
+    for (int grp = 0; grp < d->n_groups; ++grp) {
+        const int k = d->group_size[grp];
+        if (k < 1 || k > kComboMaxMembers) return fail(CBDFS_EINVAL, "group size %d outside 1..%d", k, kComboMaxMembers);
+        cb->P.group_size[grp] = k;
+        for (int j = 0; j < k; ++j) {
+            const int id = d->members[total + j];
+            if (id >= (int)c->heur_kind.size() || id < CBDFS_HEUR_MD || (id == CBDFS_HEUR_MD && d->domain == CBDFS_DOM_RC3))
+                return fail(CBDFS_EINVAL, "member heuristic id %d", id);
+            if (id >= 0 && c->heur_kind[id] == 2) return fail(CBDFS_EINVAL, "member %d is itself a composite", id);
+            if (heur_is_real(c, id)) return fail(CBDFS_EINVAL, "member %d is real-valued", id);
+            const int dom = id < 0 ? d->domain
+                            : c->heur_kind[id] == 0 ? c->nets[c->heur_index[id]]->domain
+                                                    : c->pdbs[c->heur_index[id]]->domain;
+            if (dom != d->domain) return fail(CBDFS_EINVAL, "member %d is for another domain", id);
+            cb->members.push_back(id);
+        }
+        total += k;
+        if (total > kComboMaxTotal) return fail(CBDFS_EINVAL, "more than %d members", kComboMaxTotal);
+    }
+    CUDA_TRY(cudaSetDevice(c->device));
+    for (auto &s : c->slots)
+        if (!s.combo) {
+            int rc = dev_alloc(c, (void **)&s.combo, combo_bytes(c));
+            if (rc) return rc;
+            ++c->buf_gen;
+        }
+    c->combos.push_back(std::move(cb));
+    c->heur_kind.push_back(2);
+    c->heur_index.push_back((int)c->combos.size() - 1);
     *heur_id = (int)c->heur_kind.size() - 1;
     return CBDFS_OK;
 }

@@ -43,7 +43,7 @@ struct ChainParams {
                                    // network (the separate last layer reads BF16); -1 none
     int C;                         // outputs of the last layer
     int head_kind, max_with_md;
-    float h_offset;                // CBDFS_HEAD_REAL: added to y
+    float head_param;              // CBDFS_HEAD_REAL: the offset; CBDFS_HEAD_QUANTILE: q
     const float *w_last, *b_last;  // [C][dims[nh]], [C]
     const uint8_t *g;
     uint32_t bound;                // CBDFS_HEAD_REAL: the FP32 bound's bit pattern

@@ -56,6 +56,9 @@ void train_free(struct Ctx *c, TrainState *T);
 struct NetGPU {
     int domain = 0, L = 0, prec = 0, head = 0, max_with_md = 0;
     float h_offset = 0.f;              // CBDFS_HEAD_REAL: added to y
+    float quantile = 0.f;              // CBDFS_HEAD_QUANTILE: the CDF level
+    // the head's parameter as the final kernels take it (the offset, or the quantile)
+    float head_param() const { return head == CBDFS_HEAD_QUANTILE ? quantile : h_offset; }
     int dims[kMaxLayers + 1] = {};
     int k1pad = 0;                     // one-hot width padded to the MMA K block
     // tensor-core layers 0..L-2: low-precision weights [dims[l+1]][Kpad] (K-major)
@@ -82,6 +85,19 @@ struct PdbGPU {
     size_t bytes = 0;
 };
 
+// composite heuristic: [MD] + sum over groups of the minimum over each group's members
+constexpr int kComboMaxGroups = 4, kComboMaxMembers = 8, kComboMaxTotal = 16;
+struct ComboParams {
+    int n_groups;
+    int group_size[kComboMaxGroups];
+    int add_md;
+};
+struct ComboGPU {
+    int domain = 0;
+    ComboParams P{};
+    std::vector<int> members;          // heuristic ids, group by group
+};
+
 // one evaluation slot: a stream plus the scratch a batch needs
 struct Slot {
     cudaStream_t stream = nullptr;
@@ -101,6 +117,9 @@ struct Slot {
     float *partial = nullptr;          // head partials [n-tiles][rows][C]
     void *onehot = nullptr;            // one-hot input rows [max_batch_pad][1 KB]
     size_t partial_bytes = 0;
+    // composite heuristics: member h rows [kComboMaxTotal][max_batch_pad], then a member
+    // mask [max_batch_pad / 32] and minf word (written by the members, not read)
+    uint8_t *combo = nullptr;
     // when set, the fused chain stamps its tile timeline here (see cbdfs_eval_trace)
     unsigned long long *trace = nullptr;
     int trace_tiles = 0;
@@ -118,7 +137,8 @@ struct Ctx {
     int *d_err = nullptr;              // device error flag
     std::vector<std::unique_ptr<NetGPU>> nets;    // heur ids 0..: nets and PDBs interleaved
     std::vector<std::unique_ptr<PdbGPU>> pdbs;
-    std::vector<int> heur_kind;        // 0 = net, 1 = pdb
+    std::vector<std::unique_ptr<ComboGPU>> combos;
+    std::vector<int> heur_kind;        // 0 = net, 1 = pdb, 2 = composite
     std::vector<int> heur_index;
     std::vector<Slot> slots;
     std::mutex slot_mu;
@@ -150,6 +170,10 @@ int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
 // words, then minf (one word)
 // a network with the real-valued head (FP32 bounds and f-costs)
 bool heur_is_real(const Ctx *c, int heur_id);
+
+inline size_t combo_bytes(const Ctx *c) {
+    return (size_t)kComboMaxTotal * c->max_batch_pad + c->max_batch_pad / 8 + 4;
+}
 
 inline size_t slot_out_bytes(const Ctx *c) { return (size_t)c->max_batch_pad + c->max_batch_pad / 8 + 4; }
 
@@ -377,6 +401,25 @@ __device__ __forceinline__ float real_h(float y, float offset, int md, bool goal
 __device__ __forceinline__ uint32_t real_f_key(uint32_t g, float h) {
     return __float_as_uint(__fadd_rn((float)g, h));
 }
+// ---- the classifier quantile (CBDFS_HEAD_QUANTILE) ----
+// The smallest class c whose softmax cumulative probability reaches q, from the logits y(0..C)
+// in FP32: with m the largest logit and e_c = exp(y_c - m), the first c where e_0 + ... + e_c
+// >= q (e_0 + ... + e_{C-1}); C-1 if rounding keeps every partial sum below that.
+template <typename Y>
+__device__ __forceinline__ int quantile_class(const Y &y, int C, float q) {
+    float m = y(0);
+    for (int c = 1; c < C; ++c) m = fmaxf(m, y(c));
+    float S = 0.f;
+    for (int c = 0; c < C; ++c) S += expf(y(c) - m);
+    const float T = q * S;
+    float acc = 0.f;
+    for (int c = 0; c < C; ++c) {
+        acc += expf(y(c) - m);
+        if (acc >= T) return c;
+    }
+    return C - 1;
+}
+
 // the uint8 h written beside a real h: its ceiling (an admissible integer h when h is, since
 // path costs are integers), clamped to 255
 __device__ __forceinline__ uint8_t real_h_u8(float h) { return (uint8_t)fminf(ceilf(h), 255.f); }

@@ -163,7 +163,7 @@ __device__ __forceinline__ void finish_row(const ChainParams &P, uint32_t row_g,
             goal = stp_is_goal<SIDE>(s);
         }
         if (P.head_kind == CBDFS_HEAD_REAL) {
-            const float hr = real_h(yv[0], P.h_offset, md, goal);
+            const float hr = real_h(yv[0], P.head_param, md, goal);
             if (P.h) P.h[row_g] = real_h_u8(hr);
             if (P.y) P.y[row_g] = hr;
             f = real_f_key(P.g[row_g], hr);
@@ -171,6 +171,26 @@ __device__ __forceinline__ void finish_row(const ChainParams &P, uint32_t row_g,
             int hv;
             if (P.head_kind == CBDFS_HEAD_REGRESSION) {
                 hv = (int)fminf(fmaxf(rintf(yv[0]), 0.f), 255.f);
+            } else if (P.head_kind == CBDFS_HEAD_QUANTILE) {
+                // quantile_class's arithmetic, in the same order, over the register array
+                float mx = yv[0];
+#pragma unroll
+                for (int c = 1; c < CMAX; ++c)
+                    if (c < P.C) mx = fmaxf(mx, yv[c]);
+                float S = 0.f;
+#pragma unroll
+                for (int c = 0; c < CMAX; ++c)
+                    if (c < P.C) S += expf(yv[c] - mx);
+                const float T = P.head_param * S;
+                float acc = 0.f;
+                bool hit = false;
+                hv = P.C - 1;
+#pragma unroll
+                for (int c = 0; c < CMAX; ++c)
+                    if (c < P.C && !hit) {
+                        acc += expf(yv[c] - mx);
+                        if (acc >= T) { hv = c; hit = true; }
+                    }
             } else {
                 int best = 0;
                 float bv = yv[0];

@@ -132,7 +132,7 @@ template <typename TIn, int DOMAIN, int HEAD>
 __global__ void __launch_bounds__(128)
 k_head(const TIn *__restrict__ act, int K, int C, const float *__restrict__ W,
        const float *__restrict__ bL, const uint64_t *__restrict__ states,
-       const uint8_t *__restrict__ g, uint32_t bound, uint32_t n, int max_with_md, float offset,
+       const uint8_t *__restrict__ g, uint32_t bound, uint32_t n, int max_with_md, float hparam,
        uint8_t *__restrict__ h_out, uint32_t *__restrict__ mask, uint32_t *__restrict__ minf,
        float *__restrict__ y_out) {
     extern __shared__ float ylog[];  // [4 warps][C]
@@ -179,7 +179,7 @@ k_head(const TIn *__restrict__ act, int K, int C, const float *__restrict__ W,
             }
             uint32_t f;
             if (HEAD == CBDFS_HEAD_REAL) {
-                const float hr = real_h(yw[0], offset, md, goal);
+                const float hr = real_h(yw[0], hparam, md, goal);
                 if (h_out) h_out[m] = real_h_u8(hr);
                 if (y_out) y_out[m] = hr;
                 f = real_f_key(g[m], hr);
@@ -187,6 +187,8 @@ k_head(const TIn *__restrict__ act, int K, int C, const float *__restrict__ W,
                 int hv;
                 if (HEAD == CBDFS_HEAD_REGRESSION) {
                     hv = (int)fminf(fmaxf(rintf(yw[0]), 0.f), 255.f);
+                } else if (HEAD == CBDFS_HEAD_QUANTILE) {
+                    hv = quantile_class([&](int c) { return yw[c]; }, C, hparam);
                 } else {
                     int best = 0;
                     float bv = yw[0];
@@ -227,7 +229,7 @@ template <typename TIn, int DOMAIN, int HEAD, int CPT>
 __global__ void __launch_bounds__(HT_THREADS)
 k_head_tiled(const TIn *__restrict__ act, int K, int C, const float *__restrict__ W,
              const float *__restrict__ bL, const uint64_t *__restrict__ states,
-             const uint8_t *__restrict__ g, uint32_t bound, uint32_t n, int max_with_md, float offset,
+             const uint8_t *__restrict__ g, uint32_t bound, uint32_t n, int max_with_md, float hparam,
              uint8_t *__restrict__ h_out, uint32_t *__restrict__ mask, uint32_t *__restrict__ minf,
              float *__restrict__ y_out) {
     constexpr int CPAD = 16 * CPT;
@@ -333,6 +335,7 @@ k_head_tiled(const TIn *__restrict__ act, int K, int C, const float *__restrict_
             hv = bi;
         }
         if (lane == 0) {
+            if (HEAD == CBDFS_HEAD_QUANTILE) hv = quantile_class([&](int c) { return Ys[loc][c]; }, C, hparam);
             bool goal;
             int md = -1;
             if (DOMAIN == CBDFS_DOM_RC3) {
@@ -345,7 +348,7 @@ k_head_tiled(const TIn *__restrict__ act, int K, int C, const float *__restrict_
             }
             uint32_t f;
             if (HEAD == CBDFS_HEAD_REAL) {
-                const float hr = real_h(Ys[loc][0], offset, md, goal);
+                const float hr = real_h(Ys[loc][0], hparam, md, goal);
                 if (h_out) h_out[m] = real_h_u8(hr);
                 if (y_out) y_out[m] = hr;
                 f = real_f_key(g[m], hr);
@@ -411,6 +414,8 @@ int head_dom(int head, const TIn *act, int K, int C, const float *W, const float
         return head_any<TIn, DOMAIN, CBDFS_HEAD_REGRESSION>(act, K, C, W, b, states, g, bound, n, md, off, h, mask, minf, y, st);
     if (head == CBDFS_HEAD_CLASSIFIER)
         return head_any<TIn, DOMAIN, CBDFS_HEAD_CLASSIFIER>(act, K, C, W, b, states, g, bound, n, md, off, h, mask, minf, y, st);
+    if (head == CBDFS_HEAD_QUANTILE)
+        return head_any<TIn, DOMAIN, CBDFS_HEAD_QUANTILE>(act, K, C, W, b, states, g, bound, n, md, off, h, mask, minf, y, st);
     return head_any<TIn, DOMAIN, CBDFS_HEAD_REAL>(act, K, C, W, b, states, g, bound, n, md, off, h, mask, minf, y, st);
 }
 
@@ -438,18 +443,18 @@ int sgemm_relu(const float *A, const float *W, const float *b, float *C, int M, 
 
 int head(bool bf16_in, int domain, int head_kind, const void *act, int K, int C, const float *W,
          const float *b, const uint64_t *states, const uint8_t *g, uint32_t bound, uint32_t n,
-         int max_with_md, float offset, uint8_t *h, uint32_t *mask, uint32_t *minf, float *y,
+         int max_with_md, float hparam, uint8_t *h, uint32_t *mask, uint32_t *minf, float *y,
          cudaStream_t st) {
     if (bf16_in) {
         auto a = static_cast<const __nv_bfloat16 *>(act);
-        if (domain == CBDFS_DOM_STP3) return head_dom<__nv_bfloat16, CBDFS_DOM_STP3>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, offset, h, mask, minf, y, st);
-        if (domain == CBDFS_DOM_STP4) return head_dom<__nv_bfloat16, CBDFS_DOM_STP4>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, offset, h, mask, minf, y, st);
-        return head_dom<__nv_bfloat16, CBDFS_DOM_RC3>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, offset, h, mask, minf, y, st);
+        if (domain == CBDFS_DOM_STP3) return head_dom<__nv_bfloat16, CBDFS_DOM_STP3>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, hparam, h, mask, minf, y, st);
+        if (domain == CBDFS_DOM_STP4) return head_dom<__nv_bfloat16, CBDFS_DOM_STP4>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, hparam, h, mask, minf, y, st);
+        return head_dom<__nv_bfloat16, CBDFS_DOM_RC3>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, hparam, h, mask, minf, y, st);
     }
     auto a = static_cast<const float *>(act);
-    if (domain == CBDFS_DOM_STP3) return head_dom<float, CBDFS_DOM_STP3>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, offset, h, mask, minf, y, st);
-    if (domain == CBDFS_DOM_STP4) return head_dom<float, CBDFS_DOM_STP4>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, offset, h, mask, minf, y, st);
-    return head_dom<float, CBDFS_DOM_RC3>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, offset, h, mask, minf, y, st);
+    if (domain == CBDFS_DOM_STP3) return head_dom<float, CBDFS_DOM_STP3>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, hparam, h, mask, minf, y, st);
+    if (domain == CBDFS_DOM_STP4) return head_dom<float, CBDFS_DOM_STP4>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, hparam, h, mask, minf, y, st);
+    return head_dom<float, CBDFS_DOM_RC3>(head_kind, a, K, C, W, b, states, g, bound, n, max_with_md, hparam, h, mask, minf, y, st);
 }
 
 }  // namespace cbdfs

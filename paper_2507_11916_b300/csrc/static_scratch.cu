@@ -58,6 +58,7 @@ extern "C" int heur_eval_device_static(cbdfs_ctx *ctx, int heur_id, int domain,
     if (heur_id == CBDFS_HEUR_MD && domain == CBDFS_DOM_RC3)
         return fail(CBDFS_EINVAL, "Manhattan distance is defined for sliding-tile domains only");
     if (heur_is_real(c, heur_id)) return fail(CBDFS_EINVAL, "heuristic %d is real-valued", heur_id);
+    if (heur_id >= 0 && c->heur_kind[heur_id] == 2) return fail(CBDFS_EINVAL, "heuristic %d is a composite", heur_id);
     if (c->device < 0 || c->device >= kMaxDevices) return fail(CBDFS_EINVAL, "device %d", c->device);
     CUDA_TRY(cudaSetDevice(c->device));
     StaticDevice &D = g_static[c->device];
