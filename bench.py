@@ -522,12 +522,8 @@ def networks_leg(P, args):
             dm = torch.empty((B + 31) // 32, dtype=torch.int32, device=dev)
             dmin = torch.empty(1, dtype=torch.int32, device=dev)
             row = {"batch": B}
-            for prec in precs:
-                kw = {}
-                if prec == "fp8":
-                    kw["act_scales"] = calib_scales(Ws, bs, dom)
-                hid = P.cbdfs_net_load(ctx, dom, Ws, bs, {"fp32": P.PREC_FP32, "bf16": P.PREC_BF16, "fp8": P.PREC_FP8}[prec],
-                                       head, md, **kw)
+
+            def timed(hid):
                 with torch.cuda.stream(stream):
                     for _ in range(3):
                         P.heur_eval_device(ctx, hid, dom, ds, dg, 50, B, dh, dm, dmin, stream=stream)
@@ -545,12 +541,33 @@ def networks_leg(P, args):
                         gr.replay()
                         e1[k].record(stream)
                 stream.synchronize()
-                ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / K
-                dims = cfg["dims"]
-                flops = 2 * B * sum(dims[l] * dims[l + 1] for l in range(len(dims) - 1))
-                row[prec] = {"states_per_s": B / (ms / 1e3), "ms": ms, "tflops": flops / (ms / 1e3) / 1e12}
                 del gr
+                return sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / K
+
+            dims = cfg["dims"]
+            flops = 2 * B * sum(dims[l] * dims[l + 1] for l in range(len(dims) - 1))
+            for prec in precs:
+                kw = {}
+                if prec == "fp8":
+                    kw["act_scales"] = calib_scales(Ws, bs, dom)
+                hid = P.cbdfs_net_load(ctx, dom, Ws, bs, {"fp32": P.PREC_FP32, "bf16": P.PREC_BF16, "fp8": P.PREC_FP8}[prec],
+                                       head, md, **kw)
+                ms = timed(hid)
+                row[prec] = {"states_per_s": B / (ms / 1e3), "ms": ms, "tflops": flops / (ms / 1e3) / 1e12}
             out[name] = row
+            if cfg is W.NET_C3:
+                # the 15-puzzle h_M shape (Experimental Setup): MD + the minimum over an ensemble
+                # of two quantile classifiers + the minimum over a second pair (BF16, q = 0.05)
+                ids = []
+                for seed in (41, 42, 43, 44):
+                    Wq, bq = W.net_weights(dims=dims, init="kaiming", seed=seed)
+                    ids.append(P.cbdfs_net_load(ctx, dom, Wq, bq, P.PREC_BF16, P.HEAD_QUANTILE, 0, quantile=0.05))
+                cid = P.cbdfs_combo_load(ctx, dom, [ids[:2], ids[2:]], add_md=True)
+                ms = timed(cid)
+                out["15-puzzle composite: MD + min(2 x 81-class quantile) + min(2 x 81-class quantile)"] = {
+                    "batch": B, "bf16": {"states_per_s": B / (ms / 1e3), "ms": ms,
+                                         "tflops": 4 * flops / (ms / 1e3) / 1e12,
+                                         "members_run": "one after another on the stream, then the combine kernel"}}
         assert P.cbdfs_device_status(ctx) == 0
     finally:
         P.cbdfs_destroy(ctx)
