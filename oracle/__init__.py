@@ -109,6 +109,11 @@ def lib():
         L.or_pdb_ball.argtypes = [ctypes.c_int, ip, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                   ctypes.c_void_p, ctypes.c_void_p]
         L.or_pdb_ball.restype = ctypes.c_int64
+        L.or_rc_corner_index.argtypes = [u64p]
+        L.or_rc_corner_index.restype = ctypes.c_int64
+        L.or_rc_corner_ball.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+        L.or_rc_corner_ball.restype = ctypes.c_int64
+        L.or_rc_corner_pdb.argtypes = [ctypes.c_void_p]
         L.or_pdb_h.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ip, ip,
                                ctypes.c_void_p]
         L.or_cbdfs.argtypes = [ctypes.c_int, u64p, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
@@ -234,6 +239,33 @@ def pdb_ball(side: int, tiles, maxd: int, cap: int = 1 << 24):
     if m < 0:
         raise MemoryError("pdb_ball: more than cap states within the distance")
     return ranks[:m].copy(), vals[:m].copy()
+
+
+RC_CORNER_ENTRIES = 40320 * 2187  # 8! corner placements x 3^7 twists
+
+
+def rc_corner_index(state) -> int:
+    """The 8-corner PDB's index of a cube state (oracle.c `or_rc_corner_index`)."""
+    return int(lib().or_rc_corner_index(_words(state)))
+
+
+def rc_corner_ball(maxd: int, cap: int = 1 << 24):
+    """(indices, distances) of every corner configuration within maxd face turns of the
+    solved one, sorted by index: the 8-corner PDB's entries up to maxd."""
+    idx = np.empty(cap, np.int64)
+    val = np.empty(cap, np.uint8)
+    n = lib().or_rc_corner_ball(maxd, cap, idx.ctypes.data, val.ctypes.data)
+    if n < 0:
+        raise ValueError("ball larger than cap")
+    return idx[:n].copy(), val[:n].copy()
+
+
+def rc_corner_pdb() -> np.ndarray:
+    """The full 8-corner table (oracle.c `or_rc_corner_pdb`; 88 MB, about half a minute)."""
+    t = np.empty(RC_CORNER_ENTRIES, np.uint8)
+    if lib().or_rc_corner_pdb(t.ctypes.data) < 0:
+        raise MemoryError("corner PDB queue")
+    return t
 
 
 class PDB:

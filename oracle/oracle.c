@@ -599,6 +599,158 @@ int or_pdb_h(uint64_t s, int side, int npat, const int *k, const int *tiles,
 }
 
 /* ======================================================================================
+ * the cube's 8-corner pattern database (Experimental Setup: the 8-corner PDB is the cube's
+ * h_PDB).  Index of a corner configuration: p_c = the slot of corner cubie c, t_c its twist
+ * (packed word 0, field c = 3 p_c + t_c);
+ *   index = rank(p) * 3^7 + sum_{c<7} t_c 3^c,  rank(p) = sum_i (p_i - #{j<i: p_j<p_i}) (7-i)!
+ * ==================================================================================== */
+
+int64_t or_rc_corner_index(const uint64_t *w) {
+    int p[8], t[8];
+    for (int c = 0; c < 8; ++c) {
+        const int f = (int)((w[0] >> (5 * c)) & 31u);
+        p[c] = f / 3;
+        t[c] = f % 3;
+    }
+    int64_t rank = 0, fact = 5040; /* 7! */
+    for (int i = 0; i < 8; ++i) {
+        int less = 0;
+        for (int j = 0; j < i; ++j) less += p[j] < p[i];
+        rank += (int64_t)(p[i] - less) * fact;
+        if (i < 7) fact /= (7 - i);
+    }
+    int64_t tw = 0, pw = 1;
+    for (int c = 0; c < 7; ++c) {
+        tw += t[c] * pw;
+        pw *= 3;
+    }
+    return rank * 2187 + tw;
+}
+
+/* corner configuration <-> index; c_slot[c] / c_tw[c]: slot and twist of corner cubie c */
+static void corner_unindex(int64_t idx, int *c_slot, int *c_tw) {
+    int64_t r = idx / 2187, tr = idx % 2187, fact = 5040;
+    int used[8] = {0}, sum = 0;
+    for (int i = 0; i < 8; ++i) {
+        int d = (int)(r / fact);
+        r %= fact;
+        if (i < 7) fact /= (7 - i);
+        int s = 0;
+        for (;; ++s)
+            if (!used[s] && d-- == 0) break;
+        used[s] = 1;
+        c_slot[i] = s;
+    }
+    for (int c = 0; c < 7; ++c) {
+        c_tw[c] = (int)(tr % 3);
+        tr /= 3;
+        sum += c_tw[c];
+    }
+    c_tw[7] = (3 - sum % 3) % 3;
+}
+
+/* The full 8-corner table by breadth-first search from the solved corners (a queue of
+ * indices; each configuration is expanded once).  A face turn moves the cubie at slot
+ * RC_CP[f][i] to slot i, adding RC_CO[f][i] to its twist (one quarter; q quarters in a row).
+ * table: 88,179,840 bytes.  Returns the largest distance, or -1 if memory runs out. */
+int or_rc_corner_pdb(uint8_t *table) {
+    const int64_t E = (int64_t)40320 * 2187;
+    memset(table, 255, (size_t)E);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)E);
+    if (!queue) return -1;
+    int inv[6][8]; /* the slot a quarter turn of face f sends slot s to */
+    for (int f = 0; f < 6; ++f)
+        for (int i = 0; i < 8; ++i) inv[f][RC_CP[f][i]] = i;
+    int64_t head = 0, tail = 0;
+    table[0] = 0;
+    queue[tail++] = 0;
+    int maxd = 0;
+    while (head < tail) {
+        const int64_t u = queue[head++];
+        const int du = table[u];
+        int slot[8], tw[8];
+        corner_unindex(u, slot, tw);
+        for (int f = 0; f < 6; ++f) {
+            int ns[8], nt[8];
+            memcpy(ns, slot, sizeof ns);
+            memcpy(nt, tw, sizeof nt);
+            for (int q = 0; q < 3; ++q) {
+                for (int c = 0; c < 8; ++c) {
+                    const int to = inv[f][ns[c]];
+                    nt[c] = (nt[c] + RC_CO[f][to]) % 3;
+                    ns[c] = to;
+                }
+                uint64_t w[2] = {0, 0};
+                for (int c = 0; c < 8; ++c) w[0] |= (uint64_t)(ns[c] * 3 + nt[c]) << (5 * c);
+                const int64_t v = or_rc_corner_index(w);
+                if (table[v] == 255) {
+                    table[v] = (uint8_t)(du + 1);
+                    if (du + 1 > maxd) maxd = du + 1;
+                    queue[tail++] = (int32_t)v;
+                }
+            }
+        }
+    }
+    free(queue);
+    return maxd;
+}
+
+/* Every corner configuration within maxd face turns of the solved one, by breadth-first
+ * search over cube states (the corners of a turn's result depend only on the corners).
+ * Writes (index, distance) pairs sorted by index; returns their number, or -1 past `cap`. */
+int64_t or_rc_corner_ball(int maxd, int64_t cap, int64_t *out_index, uint8_t *out_val) {
+    uint64_t size = 1;
+    while (size < (uint64_t)cap * 2) size <<= 1;
+    hset h = {(uint64_t *)calloc(size, 8), (uint8_t *)malloc(size), size - 1, 0};
+    lvec cur = {0}, nxt = {0};
+    if (!h.key || !h.val) return -1;
+    uint64_t g[2];
+    rc_goal(g);
+    int fresh;
+    *hset_slot(&h, (uint64_t)or_rc_corner_index(g), &fresh) = 0;
+    lvec_push(&cur, (int64_t)g[0]);  /* the corner word is the whole BFS state */
+    int64_t result = 0;
+    for (int d = 0; d < maxd && cur.n > 0 && result >= 0; ++d) {
+        for (int64_t qi = 0; qi < cur.n && result >= 0; ++qi) {
+            uint64_t w[2] = {(uint64_t)cur.a[qi], g[1]}, o[2];
+            for (int m = 0; m < 18; ++m) {
+                or_rc_apply(w, m, o);
+                uint8_t *dv = hset_slot(&h, (uint64_t)or_rc_corner_index(o), &fresh);
+                if (h.used > cap) { result = -1; break; }
+                if (fresh) {
+                    *dv = (uint8_t)(d + 1);
+                    lvec_push(&nxt, (int64_t)o[0]);
+                }
+            }
+        }
+        lvec t = cur;
+        cur = nxt;
+        nxt = t;
+        nxt.n = 0;
+    }
+    if (result == 0) {
+        int64_t *pairs = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)(h.used ? h.used : 1));
+        for (uint64_t i = 0; i <= h.mask; ++i)
+            if (h.key[i]) {
+                pairs[2 * result] = (int64_t)(h.key[i] - 1);
+                pairs[2 * result + 1] = h.val[i];
+                ++result;
+            }
+        qsort(pairs, (size_t)result, 2 * sizeof(int64_t), cmp_pair);
+        for (int64_t i = 0; i < result; ++i) {
+            out_index[i] = pairs[2 * i];
+            out_val[i] = (uint8_t)pairs[2 * i + 1];
+        }
+        free(pairs);
+    }
+    free(cur.a);
+    free(nxt.a);
+    free(h.key);
+    free(h.val);
+    return result;
+}
+
+/* ======================================================================================
  * one cost-bounded depth-first search
  * ==================================================================================== */
 

@@ -74,3 +74,51 @@ def test_pdb_ball_is_the_table_near_the_goal(orc, side, tiles, maxd):
     idx = np.nonzero(T <= maxd)[0]
     assert np.array_equal(ranks, idx)
     assert np.array_equal(vals, T[idx])
+
+
+# ---- the cube's 8-corner PDB ---------------------------------------------------------------
+
+def test_rc_corner_ball_matches_the_full_table_levels(orc):
+    # two independent oracle computations: the ball walks full cube states with or_rc_apply;
+    # the stored histogram comes from the full table's own corner-only search
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "rc_corner_pdb.json")))
+    assert gold["entries"] == orc.RC_CORNER_ENTRIES == 40320 * 2187 == sum(gold["histogram"])
+    idx, val = orc.rc_corner_ball(5)
+    assert [int((val == d).sum()) for d in range(6)] == gold["histogram"][:6]
+    assert len(np.unique(idx)) == len(idx) and idx.min() == 0 and idx.max() < orc.RC_CORNER_ENTRIES
+    # sampled entries within the ball agree with the stored table sample
+    si, sv = np.array(gold["sample_index"]), np.array(gold["sample_value"])
+    pos = np.searchsorted(idx, si)
+    inside = (pos < len(idx)) & (idx[np.minimum(pos, len(idx) - 1)] == si)
+    assert np.array_equal(val[pos[inside]], sv[inside])
+    assert (sv[~inside] > 5).all()
+
+
+def test_rc_corner_distance_is_admissible_and_consistent(orc):
+    idx, val = orc.rc_corner_ball(5)
+
+    def look(s):
+        i = orc.rc_corner_index(s)
+        p = np.searchsorted(idx, i)
+        return int(val[p]) if p < len(idx) and idx[p] == i else None
+
+    assert look(orc.rc_goal()) == 0
+    for k in range(40):
+        n = 1 + k % 4
+        s = orc.rc_apply_seq(W.rc_scramble(n, 900 + k))
+        h = look(s)
+        assert h is not None and h <= n
+        for m in range(18):
+            h2 = look(orc.rc_apply(s, m))
+            assert h2 is not None and abs(h2 - h) <= 1
+
+
+def test_rc_corner_index_ignores_edges_and_separates_corners(orc):
+    s = orc.rc_apply_seq(W.rc_scramble(6, 4242))
+    g = orc.rc_goal()
+    assert orc.rc_corner_index((s[0], g[1])) == orc.rc_corner_index(s)
+    idx = {orc.rc_corner_index(orc.rc_apply_seq(W.rc_scramble(7, 5000 + k))) for k in range(300)}
+    words = {orc.rc_apply_seq(W.rc_scramble(7, 5000 + k))[0] for k in range(300)}
+    assert len(idx) == len(words)
