@@ -134,9 +134,13 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id);
  * tiles (in list order) among all k-permutations of the N cells:
  *   rank = sum_i d_i * (N-1-i)!/(N-k)!,  d_i = cell_i - #{j < i : cell_j < cell_i}.
  * h = sum over patterns of table_q[rank_q].
+ * The cube (CBDFS_DOM_RC3; Experimental Setup: the 8-corner PDB) takes one pattern, the
+ * corner cubies 0..7 in order: with p_c the slot and t_c the twist of corner cubie c,
+ *   index = rank(p) * 3^7 + sum_{c<7} t_c 3^c,  rank(p) = sum_i (p_i - #{j<i: p_j<p_i}) (7-i)!,
+ * 8! * 3^7 = 88,179,840 entries.
  * ------------------------------------------------------------------------------------- */
 typedef struct {
-    int domain;                     /* CBDFS_DOM_STP3 or CBDFS_DOM_STP4 */
+    int domain;                     /* any cbdfs_domain (the cube: the corner pattern only) */
     int n_patterns;                 /* 1..4 */
     const int *k;                   /* tiles per pattern */
     const int *tiles;               /* concatenated tile lists */
@@ -151,7 +155,9 @@ int cbdfs_pdb_load(cbdfs_ctx *ctx, const cbdfs_pdb_desc *d, int *heur_id);
 /* Build one pattern's table on the GPU by breadth-first search over the abstract space
  * (pattern-tile cells plus the blank cell; a blank move that displaces a pattern tile costs
  * 1, any other costs 0; the entry is the least distance over blank cells).  table_out
- * (host, cap bytes) receives N!/(N-k)! entries; *entries receives that count.
+ * (host, cap bytes) receives N!/(N-k)! entries; *entries receives that count.  For the cube
+ * (pattern_tiles = 0..7, k = 8): the 8-corner table, by breadth-first search over corner
+ * configurations under the 18 face turns (88,179,840 entries, largest distance 11).
  * Errors: EINVAL (cap too small, bad tiles), ENOMEM, EDEVICE. */
 int pdb_build(cbdfs_ctx *ctx, int domain, const int *pattern_tiles, int k, uint8_t *table_out,
               size_t cap, size_t *entries);
@@ -204,7 +210,8 @@ int heur_submit_batch(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *s
                       const uint8_t *g, uint32_t bound, uint32_t n, uint8_t *h_out,
                       uint32_t *mask_out, uint32_t *minf_out, float *y_out);
 
-/* Device buffers, enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream);
+/* Device buffers, enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream).
+ * Cube states (two words each) must start on a 16-byte boundary (EINVAL otherwise);
  * returns without waiting.  All device-buffer calls on one context share one set of
  * activation scratch, and the library orders each call after the previous one on the GPU.
  * The call may be captured into a CUDA graph (the library then leaves the ordering to the

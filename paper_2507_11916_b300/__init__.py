@@ -272,10 +272,14 @@ def cbdfs_combo_load(ctx, domain, groups, add_md=False) -> int:
 
 
 def pdb_build(ctx, domain, tiles) -> np.ndarray:
-    n = 9 if domain == DOM_STP3 else 16
-    P = 1
-    for i in range(len(tiles)):
-        P *= n - i
+    """One pattern's table built on the GPU (the cube: tiles 0..7, the 8-corner table)."""
+    if domain == DOM_RC3:
+        P = 40320 * 2187
+    else:
+        n = 9 if domain == DOM_STP3 else 16
+        P = 1
+        for i in range(len(tiles)):
+            P *= n - i
     table = np.empty(P, dtype=np.uint8)
     entries = ctypes.c_size_t()
     _check(_lib.pdb_build(ctx, domain, (ctypes.c_int * len(tiles))(*tiles), len(tiles),

@@ -25,16 +25,13 @@ int head(bool bf16_in, int domain, int head_kind, const void *act, int K, int C,
          const float *b, const uint64_t *states, const uint8_t *g, uint32_t bound, uint32_t n,
          int max_with_md, float offset, uint8_t *h, uint32_t *mask, uint32_t *minf, float *y,
          cudaStream_t st);
-struct PdbParams {
-    int n_patterns;
-    int k[4];
-    int tiles[4][8];
-    uint32_t weight[4][8];
-    const uint8_t *table[4];
-};
 int pdb_gather(int domain, const PdbParams &P, const uint64_t *states, uint32_t n, const uint8_t *g,
                uint32_t bound, uint8_t *h, uint32_t *mask, uint32_t *minf, cudaStream_t st);
 int pdb_build_device(Ctx *c, int side, const int *tiles, int k, uint8_t *table, cudaStream_t st);
+size_t rc_corner_entries();
+int rc_corner_gather(const uint8_t *table, const uint64_t *states, uint32_t n, const uint8_t *g, uint32_t bound,
+                     uint8_t *h, uint32_t *mask, uint32_t *minf, cudaStream_t st);
+int rc_corner_build_device(Ctx *c, uint8_t *table, cudaStream_t st);
 int combine(int domain, const ComboParams &C, const uint64_t *states, uint32_t n, const uint8_t *member_h,
             size_t member_stride, const uint8_t *g, uint32_t bound, uint8_t *h, uint32_t *mask, uint32_t *minf,
             cudaStream_t st);
@@ -382,6 +379,9 @@ int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
              cudaStream_t st) {
     CUDA_TRY(cudaMemsetAsync(d_minf, 0xFF, sizeof(uint32_t), st));
     if (n == 0) return CBDFS_OK;
+    // the kernels read a cube state as one 16-byte load
+    if (domain == CBDFS_DOM_RC3 && (reinterpret_cast<uintptr_t>(d_states) & 15u))
+        return fail(CBDFS_EINVAL, "cube states must start on a 16-byte boundary");
     if (int r = mark(s, st)) return r;
     if (heur_id < 0) {
         int r = builtin(heur_id, domain, d_states, n, d_g, bound, d_h, d_mask, d_minf, st);
@@ -407,12 +407,17 @@ int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
     if (c->heur_kind[heur_id] == 1) {
         const PdbGPU &p = *c->pdbs[c->heur_index[heur_id]];
         if (p.domain != domain) return fail(CBDFS_EINVAL, "PDB %d is for another domain", heur_id);
+        if (domain == CBDFS_DOM_RC3) {
+            int r = rc_corner_gather(p.table[0], d_states, n, d_g, bound, d_h, d_mask, d_minf, st);
+            return r ? r : mark(s, st);
+        }
         PdbParams P{};
         P.n_patterns = p.n_patterns;
         const int N = p.side * p.side;
         for (int q = 0; q < p.n_patterns; ++q) {
             P.k[q] = p.k[q];
             P.table[q] = p.table[q];
+            P.entries[q] = (uint32_t)p.entries[q];
             for (int i = 0; i < p.k[q]; ++i) {
                 P.tiles[q][i] = p.tiles[q][i];
                 P.weight[q][i] = (uint32_t)npk(N - 1 - i, p.k[q] - 1 - i);
@@ -676,14 +681,43 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
     return CBDFS_OK;
 }
 
+// the cube's one pattern: the eight corner cubies 0..7 in order (the 8-corner PDB)
+static int check_rc_corner_pattern(int n_patterns, const int *k, const int *tiles) {
+    if (n_patterns != 1 || k[0] != 8) return fail(CBDFS_EINVAL, "the cube's PDB is one pattern of the 8 corners");
+    for (int i = 0; i < 8; ++i)
+        if (tiles[i] != i) return fail(CBDFS_EINVAL, "the cube's corner pattern lists cubies 0..7 in order");
+    return CBDFS_OK;
+}
+
 int cbdfs_pdb_load(cbdfs_ctx *ctx, const cbdfs_pdb_desc *d, int *heur_id) {
     if (!ctx || !d || !heur_id || !d->k || !d->tiles) return fail(CBDFS_EINVAL, "null argument");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (c->server) return fail(CBDFS_EINVAL, "stop the server before loading a heuristic");
     CUDA_TRY(cudaSetDevice(c->device));
-    if (d->domain != CBDFS_DOM_STP3 && d->domain != CBDFS_DOM_STP4)
-        return fail(CBDFS_EINVAL, "pattern databases are for sliding-tile domains");
+    if (d->domain < 0 || d->domain > 2) return fail(CBDFS_EINVAL, "domain %d", d->domain);
     if (d->n_patterns < 1 || d->n_patterns > 4) return fail(CBDFS_EINVAL, "n_patterns %d outside 1..4", d->n_patterns);
+    if (d->domain == CBDFS_DOM_RC3) {
+        int rc = check_rc_corner_pattern(d->n_patterns, d->k, d->tiles);
+        if (rc) return rc;
+        auto p = std::make_unique<PdbGPU>();
+        p->domain = d->domain;
+        p->n_patterns = 1;
+        p->k[0] = 8;
+        for (int i = 0; i < 8; ++i) p->tiles[0][i] = i;
+        p->entries[0] = rc_corner_entries();
+        if ((rc = dev_alloc(c, (void **)&p->table[0], p->entries[0]))) return rc;
+        p->bytes = p->entries[0];
+        if (d->tables && d->tables[0]) {
+            CUDA_TRY(cudaMemcpy(p->table[0], d->tables[0], p->entries[0], cudaMemcpyHostToDevice));
+        } else if ((rc = rc_corner_build_device(c, p->table[0], c->slots[0].stream))) {
+            return rc;
+        }
+        c->pdbs.push_back(std::move(p));
+        c->heur_kind.push_back(1);
+        c->heur_index.push_back((int)c->pdbs.size() - 1);
+        *heur_id = (int)c->heur_kind.size() - 1;
+        return CBDFS_OK;
+    }
     auto p = std::make_unique<PdbGPU>();
     p->domain = d->domain;
     p->side = dom_side(d->domain);
@@ -768,9 +802,23 @@ int cbdfs_combo_load(cbdfs_ctx *ctx, const cbdfs_combo_desc *d, int *heur_id) {
 int pdb_build(cbdfs_ctx *ctx, int domain, const int *pattern_tiles, int k, uint8_t *table_out,
               size_t cap, size_t *entries) {
     if (!ctx || !pattern_tiles || !table_out || !entries) return fail(CBDFS_EINVAL, "null argument");
-    if (domain != CBDFS_DOM_STP3 && domain != CBDFS_DOM_STP4) return fail(CBDFS_EINVAL, "domain %d", domain);
+    if (domain < 0 || domain > 2) return fail(CBDFS_EINVAL, "domain %d", domain);
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     CUDA_TRY(cudaSetDevice(c->device));
+    if (domain == CBDFS_DOM_RC3) {
+        int rc = check_rc_corner_pattern(1, &k, pattern_tiles);
+        if (rc) return rc;
+        const size_t E = rc_corner_entries();
+        *entries = E;
+        if (cap < E) return fail(CBDFS_EINVAL, "table buffer holds %zu bytes, %zu needed", cap, E);
+        uint8_t *d_tab = nullptr;
+        if ((rc = dev_alloc(c, (void **)&d_tab, E))) return rc;
+        rc = rc_corner_build_device(c, d_tab, c->slots[0].stream);
+        if (!rc && cudaMemcpy(table_out, d_tab, E, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = fail(CBDFS_EDEVICE, "table download");
+        dev_free(c, d_tab, E);
+        return rc;
+    }
     const int side = dom_side(domain), N = side * side;
     if (k < 1 || k > 8) return fail(CBDFS_EINVAL, "pattern size %d outside 1..8", k);
     uint32_t used = 0;
@@ -894,7 +942,8 @@ static int submit_host(Ctx *c, int heur_id, int domain, const uint64_t *states, 
     // staging with copies.
     void *zs = nullptr, *zg = nullptr, *zh = nullptr, *zm = nullptr, *zy = nullptr;
     const bool zero_copy = n && host_mapped(states, &zs) && host_mapped(g, &zg) && host_mapped(mask_out, &zm) &&
-                           (!h8 || host_mapped(h8, &zh)) && (!yf || host_mapped(yf, &zy));
+                           (!h8 || host_mapped(h8, &zh)) && (!yf || host_mapped(yf, &zy)) &&
+                           (domain != CBDFS_DOM_RC3 || !(reinterpret_cast<uintptr_t>(zs) & 15u));
     float *d_y = nullptr;
     if (!zero_copy && yf && n) rc = dev_alloc(c, (void **)&d_y, (size_t)n * C * 4 + 4);
     if (zero_copy) {

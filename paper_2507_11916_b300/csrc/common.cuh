@@ -85,6 +85,16 @@ struct PdbGPU {
     size_t bytes = 0;
 };
 
+// the additive PDB gather's parameters (pdb.cu): per pattern its tiles, rank weights and table
+struct PdbParams {
+    int n_patterns;
+    int k[4];
+    int tiles[4][8];
+    uint32_t weight[4][8];   // (N-1-i)! / (N-k)!
+    uint32_t entries[4];     // table sizes N!/(N-k)!
+    const uint8_t *table[4];
+};
+
 // composite heuristic: [MD] + sum over groups of the minimum over each group's members
 constexpr int kComboMaxGroups = 4, kComboMaxMembers = 8, kComboMaxTotal = 16;
 struct ComboParams {

@@ -91,6 +91,11 @@ inline void rc_apply(uint64_t *w, int m) {
 
 }  // namespace
 
+void rc_corner_moves(uint8_t dst[18][8], uint8_t add[18][8]) {
+    memcpy(dst, kMoves.cdst, sizeof(kMoves.cdst));
+    memcpy(add, kMoves.cadd, sizeof(kMoves.cadd));
+}
+
 Domain::Domain(int d) : dom(d) {
     goal[0] = goal[1] = 0;
     if (d == CBDFS_DOM_RC3) {

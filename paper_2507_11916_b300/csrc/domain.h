@@ -30,4 +30,8 @@ struct Domain {
     int manhattan(uint64_t w0) const;
 };
 
+// The cube's corner moves: for move m and a cubie on slot s, its new slot dst[m][s] and the
+// twist add[m][s] it gains (mod 3).
+void rc_corner_moves(uint8_t dst[18][8], uint8_t add[18][8]);
+
 }  // namespace cbdfs

@@ -20,14 +20,6 @@
 
 namespace cbdfs {
 
-struct PdbParams {
-    int n_patterns;
-    int k[4];
-    int tiles[4][8];
-    uint32_t weight[4][8];   // (N-1-i)! / (N-k)!
-    const uint8_t *table[4];
-};
-
 namespace {
 
 using namespace dev;
@@ -70,7 +62,10 @@ k_pdb_gather(const uint64_t *__restrict__ states, uint32_t n, const PdbParams P,
     }
     uint32_t v[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = (q < P.n_patterns) ? __ldg(P.table[q] + rank[q]) : 0u;
+    // a malformed state (a repeated tile) can rank past its table: clamp, so that such input
+    // gives a meaningless h but no out-of-bounds read
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = (q < P.n_patterns) ? __ldg(P.table[q] + min(rank[q], P.entries[q] - 1u)) : 0u;
     uint32_t hv = v[0] + v[1] + v[2] + v[3];
     hv = (s == goal) ? 0u : min(hv, 255u);
     uint32_t f = 0xFFFFFFFFu;
