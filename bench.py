@@ -252,6 +252,61 @@ def search_rates(P, ctx, hids, seconds, work_num=1024):
     return out
 
 
+def cube_search_leg(P, args):
+    """The cube's fixed-tree evaluation (section "Fixed-Tree Evaluation"): Batch IDA* pruned
+    by the 8-corner PDB (built on the GPU here) while the 480-2048-2048-1024-21 classifier is
+    evaluated on every generated node, in BF16, FP8 and FP32.  The tree is the same for every
+    precision, so costs and per-iteration counts must agree; nodes/s compares the evaluation
+    paths.  Also the PDB alone (the plain-heuristic search) on the same instances."""
+    ctx = P.cbdfs_create(0, max_batch=8192, n_slots=4)
+    try:
+        t0 = time.perf_counter()
+        pid = P.cbdfs_pdb_load(ctx, P.DOM_RC3, [list(range(8))])
+        build_s = time.perf_counter() - t0
+        Ws, bs = W.net_weights(**W.NET_C2)
+        hids = {"bf16": P.cbdfs_net_load(ctx, P.DOM_RC3, Ws, bs, P.PREC_BF16, P.HEAD_CLASSIFIER, 0),
+                "fp8": P.cbdfs_net_load(ctx, P.DOM_RC3, Ws, bs, P.PREC_FP8, P.HEAD_CLASSIFIER, 0,
+                                        act_scales=calib_scales(Ws, bs, P.DOM_RC3)),
+                "fp32": P.cbdfs_net_load(ctx, P.DOM_RC3, Ws, bs, P.PREC_FP32, P.HEAD_CLASSIFIER, 0)}
+        starts = [W.rc_scramble(9, W.seed_for(W.TAG_C2, 100 + i)) for i in range(4)]
+        starts = [P.cbdfs_apply_moves(P.DOM_RC3, W.rc_goal(), m) for m in starts]
+        threads = min(32, os.cpu_count() or 4)
+        cfg = dict(threads=threads, work_num=256, batch=4096, timeout_us=500)
+        out = {"instances": "4 seeded 9-turn cube scrambles", "threads": threads, "batch": 4096,
+               "corner_pdb_build_s": build_s}
+
+        def run(hid, fixed):
+            costs, iters, exp, secs, nb, ev = [], [], 0, 0.0, 0, 0
+            for s in starts:
+                r = P.cbdfs_solve(ctx, P.DOM_RC3, s, P.ALGO_IDA, hid, partial_ok=True, time_limit_s=args.search_seconds * 4,
+                                  fixed_tree_heur=pid if fixed else P.HEUR_NONE, **cfg)
+                ok = r["status"] == 0
+                costs.append(r["cost"] if ok else None)
+                iters.append([tuple(it) for it in (r["iters"] if ok else r["iters"][:-1])])
+                exp += r["expanded"]
+                secs += r["seconds"]
+                nb += r["batches"]
+                ev += r["evaluated"]
+            return {"costs": costs, "expanded_per_s": exp / secs, "expanded": exp, "seconds": secs,
+                    "avg_batch": ev / max(nb, 1)}, iters
+
+        res, its = {}, {}
+        for name, hid in hids.items():
+            res[name], its[name] = run(hid, True)
+        res["pdb_only"], its["pdb_only"] = run(pid, False)
+        names = list(res)
+        res["equal_cost"] = all(res[n]["costs"] == res["pdb_only"]["costs"] for n in names)
+        res["equal_counts"] = all(
+            its[n][i][:m] == its["pdb_only"][i][:m] for i in range(len(starts)) for n in names
+            for m in [min(len(its[n][i]), len(its["pdb_only"][i]))])
+        for n in ("bf16", "fp8"):
+            res[f"{n}_over_fp32_nodes"] = res[n]["expanded_per_s"] / max(res["fp32"]["expanded_per_s"], 1e-9)
+        out["fixed_tree"] = res
+        return out
+    finally:
+        P.cbdfs_destroy(ctx)
+
+
 def md_noise_net(seed=21):
     """A 15-puzzle regression network with real outputs y = MD + u1 - u2 (dense 256-1024-1024-
     512-1, Kaiming weights everywhere else): hidden unit 0 of the first layer sums the Manhattan
@@ -822,6 +877,8 @@ def run_ours(args):
         line["kernel_micro"] = kernel_micro_leg(P, args)
     if rank == 0 and not args.no_pdb:
         line["pdb_gather"] = pdb_leg(P, args)
+    if rank == 0 and not args.no_search:
+        line["cube_search"] = cube_search_leg(P, args)
     if rank == 0 and not args.no_regression:
         line["regression_ida_vs_bts"] = regression_leg(P, args)
     if rank == 0 and not args.no_train:
