@@ -26,6 +26,9 @@ Section map (paper sections, equations and algorithms):
     real h, real f-costs and thresholds; Experimental Setup: the regression model's
     predictions minus 2.2).  `bts_real`'s binary search over real bounds is this oracle's
     reading (parity unpinned against the paper beyond the costs and the integer case).
+  * DIV-compressed PDBs ........................... `pdb_div`, `pdb_div_h` (Background: DIV
+    groups k adjacent entries by dividing the index by k and keeps the smallest; PDB
+    Comparison: h_DIV of the network's size is the plain-heuristic comparator)
   * network heuristic ............................ `mlp_forward`, `h_regression`,
     `h_classifier` (Experimental Setup: a classifier heuristic and a regression heuristic;
     Background, Heuristics: classes are integer h values), `h_quantile` (Related Work: the
@@ -285,6 +288,30 @@ class PDB:
 
     def hs(self, states) -> np.ndarray:
         return np.array([self.h(int(s)) for s in states], dtype=np.int64)
+
+
+def pdb_div(table, k: int) -> np.ndarray:
+    """DIV compression (Background: k adjacent entries are grouped by dividing the index by
+    k, and each group keeps its smallest entry so that the heuristic stays admissible):
+    entry j of the result = min(table[j*k], ..., table[j*k + k - 1]) over the entries that
+    exist; ceil(len / k) entries."""
+    t = np.asarray(table, np.uint8)
+    m = -(-len(t) // k)
+    pad = np.full(m * k, 255, np.uint8)
+    pad[:len(t)] = t
+    return pad.reshape(m, k).min(axis=1)
+
+
+def pdb_div_h(side, patterns, div_tables, k, state) -> int:
+    """h of an additive PDB whose tables are DIV-compressed by k: sum over patterns of
+    div_table[rank // k]; the goal gets 0."""
+    n = side * side
+    if int(state) == stp_goal(side):
+        return 0
+    where = {}
+    for p in range(n):
+        where[(int(state) >> (4 * p)) & 15] = p
+    return int(sum(int(t[pdb_rank([where[x] for x in pat], n) // k]) for pat, t in zip(patterns, div_tables)))
 
 
 # ---------------------------------------------------------------------------------------

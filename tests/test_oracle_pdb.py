@@ -122,3 +122,38 @@ def test_rc_corner_index_ignores_edges_and_separates_corners(orc):
     idx = {orc.rc_corner_index(orc.rc_apply_seq(W.rc_scramble(7, 5000 + k))) for k in range(300)}
     words = {orc.rc_apply_seq(W.rc_scramble(7, 5000 + k))[0] for k in range(300)}
     assert len(idx) == len(words)
+
+
+# ---- DIV compression -----------------------------------------------------------------------
+
+def test_div_by_hand_and_identity(orc):
+    t = np.array([5, 3, 9, 9, 1, 4, 7], np.uint8)
+    assert list(orc.pdb_div(t, 2)) == [3, 9, 1, 7]   # the last group holds one entry
+    assert list(orc.pdb_div(t, 3)) == [3, 1, 7]
+    assert np.array_equal(orc.pdb_div(t, 1), t)
+    assert list(orc.pdb_div(t, 7)) == [1]
+
+
+def test_div_is_a_lower_bound_attained_in_each_group(orc):
+    t = orc.pdb_build(3, [1, 2, 3, 4])
+    for k in (2, 5, 16):
+        d = orc.pdb_div(t, k)
+        assert len(d) == -(-len(t) // k)
+        assert (d[np.arange(len(t)) // k] <= t).all()
+        # every group's value is one of its own entries
+        for j in range(0, len(d), 97):
+            assert d[j] in t[j * k:(j + 1) * k]
+
+
+def test_div_heuristic_is_admissible_and_weaker(orc):
+    pats = [[1, 2, 3, 4], [5, 6, 7, 8]]
+    tabs = [orc.pdb_build(3, p) for p in pats]
+    full = orc.PDB(3, pats, tabs)
+    dist, _, _ = orc.stp3_bfs()
+    for k in (1, 4, 30):
+        dt = [orc.pdb_div(t, k) for t in tabs]
+        for s in W.random_stp_states(3, 200, 77 + k):
+            hd = orc.pdb_div_h(3, pats, dt, k, s)
+            assert hd <= full.h(int(s)) <= dist[orc.perm_rank([(int(s) >> (4 * p)) & 15 for p in range(9)])]
+            if k == 1:
+                assert hd == full.h(int(s))
