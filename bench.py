@@ -409,23 +409,35 @@ def train_leg(P, args):
         out["held_out"] = {"states": 65536, "inadmissible_vs_pdb": float(np.mean(h_nn > h_pdb)),
                            "exact": float(np.mean(h_nn == h_pdb)),
                            "mean_abs_err": float(np.mean(np.abs(h_nn - h_pdb)))}
+        # h_DIV of the network's size (PDB Comparison: the plain-heuristic comparator): the 6-6-3
+        # tables DIV-compressed until they fit the network's bytes (BF16 hidden layers, FP32 last)
+        net_bytes = sum(dims[l] * dims[l + 1] * 2 for l in range(len(dims) - 2)) + dims[-2] * dims[-1] * 4 \
+            + sum(dims[1:]) * 4
+        table_bytes = sum(len(t) for t in tabs)
+        k_div = -(-table_bytes // net_bytes)
+        pdb_div = P.cbdfs_pdb_load(ctx, P.DOM_STP4, pats, tabs, div=k_div)
+        out["div"] = {"network_bytes": net_bytes, "tables_bytes": table_bytes, "k": k_div,
+                      "div_tables_bytes": sum(-(-len(t) // k_div) for t in tabs)}
         # IDA* on the 200-move starts: per completed bound, nodes with max(NN, MD) vs the PDB
+        # and vs its DIV compression of the network's size
         cmp = []
         threads = min(32, os.cpu_count() or 4)
         for i in range(2):
             s = P.cbdfs_apply_moves(P.DOM_STP4, W.stp_goal(4), W.stp_walk(4, 200, W.seed_for(W.TAG_C1, i)))
             res = {}
-            for name, h in (("network", hid), ("pdb", pdb)):
+            for name, h in (("network", hid), ("pdb", pdb), ("pdb_div", pdb_div)):
                 r = P.cbdfs_solve(ctx, P.DOM_STP4, s, P.ALGO_IDA, h, partial_ok=True, threads=threads,
                                   work_num=64, batch=8192, timeout_us=500, time_limit_s=args.search_seconds)
                 done = r["iters"] if r["status"] == 0 else r["iters"][:-1]
                 res[name] = {"cost": r["cost"] if r["status"] == 0 else None,
                              "iters": {int(b): int(e) for b, e, _ in done}, "seconds": r["seconds"]}
-            common = sorted(set(res["network"]["iters"]) & set(res["pdb"]["iters"]))
+            common = sorted(set(res["network"]["iters"]) & set(res["pdb"]["iters"]) & set(res["pdb_div"]["iters"]))
             cmp.append({"start": i, "network_cost": res["network"]["cost"], "pdb_cost": res["pdb"]["cost"],
-                        "bounds_compared": common,
+                        "pdb_div_cost": res["pdb_div"]["cost"], "bounds_compared": common,
                         "expanded_network": sum(res["network"]["iters"][b] for b in common),
-                        "expanded_pdb": sum(res["pdb"]["iters"][b] for b in common)})
+                        "expanded_pdb": sum(res["pdb"]["iters"][b] for b in common),
+                        "expanded_pdb_div": sum(res["pdb_div"]["iters"][b] for b in common),
+                        "seconds": {k: v["seconds"] for k, v in res.items()}})
         out["ida_vs_pdb"] = cmp
     finally:
         P.cbdfs_destroy(ctx)
@@ -891,6 +903,46 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def sweep(P, args):
+    """The host-side hyperparameters (Hyperparameter Analysis: workNum, batch size and the
+    batch timeout): Batch IDA* with the 15-puzzle BF16 network (h = max(rint(y), 0, MD)) over a
+    grid of work_num x batch x timeout_us, on the same four 50-move walks, each search stopped
+    at --search-seconds.  Prints one JSON line: per grid point the expanded nodes/s, the mean
+    batch size and the batch fill / flight / submit times."""
+    ctx = P.cbdfs_create(0, max_batch=8192, n_slots=4)
+    try:
+        Ws, bs = W.net_weights(**W.NET_C1)
+        hid = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, P.PREC_BF16, P.HEAD_REGRESSION, 1)
+        starts = [P.cbdfs_apply_moves(P.DOM_STP4, W.stp_goal(4), W.stp_walk(4, 50, W.seed_for(W.TAG_C1, i)))
+                  for i in range(4)]
+        threads = min(32, os.cpu_count() or 4)
+        rows = []
+        for work_num in (16, 64, 256, 1024):
+            for batch in (512, 2048, 8192):
+                for timeout_us in (100, 500, 4000):
+                    exp, secs, nb, ev, fill, flight, sub = 0, 0.0, 0, 0, 0.0, 0.0, 0.0
+                    for s in starts:
+                        r = P.cbdfs_solve(ctx, P.DOM_STP4, s, P.ALGO_IDA, hid, partial_ok=True, threads=threads,
+                                          work_num=work_num, batch=batch, timeout_us=timeout_us,
+                                          time_limit_s=args.search_seconds)
+                        exp += r["expanded"]
+                        secs += r["seconds"]
+                        nb += r["batches"]
+                        ev += r["evaluated"]
+                        fill += r["batch_fill_us"] * r["batches"]
+                        flight += r["batch_flight_us"] * r["batches"]
+                        sub += r["submit_us"] * r["batches"]
+                    rows.append({"work_num": work_num, "batch": batch, "timeout_us": timeout_us,
+                                 "expanded_per_s": exp / secs, "avg_batch": ev / max(nb, 1),
+                                 "batch_fill_us": fill / max(nb, 1), "batch_flight_us": flight / max(nb, 1),
+                                 "submit_us": sub / max(nb, 1)})
+        best = max(rows, key=lambda r: r["expanded_per_s"])
+        print(json.dumps({"sweep": rows, "threads": threads, "best": best,
+                          "instances": "4 seeded 50-move 15-puzzle walks, BF16 256-1024-1024-512-1"}))
+    finally:
+        P.cbdfs_destroy(ctx)
+
+
 def profile_case(P, args):
     """A small case for ncu: four launches of one kernel, each after a 512 MB L2 flush, on the
     default stream; the third is the one a capture with `-s 2 -c 1` takes.
@@ -954,8 +1006,13 @@ def main():
     ap.add_argument("--profile-case", choices=["chain", "pdb78"],
                     help="run four launches of one kernel for an ncu capture and exit")
     ap.add_argument("--profile-states", type=int, default=BATCH)
+    ap.add_argument("--sweep", action="store_true",
+                    help="run the work_num x batch x timeout grid of the search and exit")
     args = ap.parse_args()
-    if args.profile_case:
+    if args.sweep:
+        import paper_2507_11916_b300 as P
+        sweep(P, args)
+    elif args.profile_case:
         import paper_2507_11916_b300 as P
         profile_case(P, args)
     elif args.impl == "reference":

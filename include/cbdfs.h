@@ -146,6 +146,9 @@ typedef struct {
     const int *tiles;               /* concatenated tile lists */
     const uint8_t *const *tables;   /* host tables, N!/(N-k)! entries each; NULL: build them
                                        on the GPU with pdb_build */
+    int div;                        /* 0 or 1: as given; k >= 2: DIV-compressed on the device
+                                       (Background, PDB compression: entry j keeps the least of
+                                       the k entries j*k .. j*k+k-1; h reads entry rank / k) */
 } cbdfs_pdb_desc;
 
 /* Register an additive PDB (copying the tables to the device, or building them there).

@@ -74,7 +74,7 @@ class ComboDesc(ctypes.Structure):
 class PdbDesc(ctypes.Structure):
     _fields_ = [("domain", ctypes.c_int), ("n_patterns", ctypes.c_int),
                 ("k", ctypes.POINTER(ctypes.c_int)), ("tiles", ctypes.POINTER(ctypes.c_int)),
-                ("tables", ctypes.POINTER(ctypes.c_void_p))]
+                ("tables", ctypes.POINTER(ctypes.c_void_p)), ("div", ctypes.c_int)]
 
 
 class SearchCfg(ctypes.Structure):
@@ -245,7 +245,7 @@ def cbdfs_net_load(ctx, domain, weights, biases, prec=PREC_BF16, head=HEAD_REGRE
     return out.value
 
 
-def cbdfs_pdb_load(ctx, domain, patterns, tables=None) -> int:
+def cbdfs_pdb_load(ctx, domain, patterns, tables=None, div=1) -> int:
     ks = [len(p) for p in patterns]
     tiles = [t for p in patterns for t in p]
     tabs = None
@@ -253,7 +253,7 @@ def cbdfs_pdb_load(ctx, domain, patterns, tables=None) -> int:
         tables = [np.ascontiguousarray(t, dtype=np.uint8) for t in tables]
         tabs = (ctypes.c_void_p * len(tables))(*(t.ctypes.data for t in tables))
     d = PdbDesc(domain, len(patterns), (ctypes.c_int * len(ks))(*ks),
-                (ctypes.c_int * len(tiles))(*tiles), tabs)
+                (ctypes.c_int * len(tiles))(*tiles), tabs, int(div))
     out = ctypes.c_int()
     _check(_lib.cbdfs_pdb_load(ctx, ctypes.byref(d), ctypes.byref(out)))
     return out.value

@@ -29,8 +29,9 @@ int pdb_gather(int domain, const PdbParams &P, const uint64_t *states, uint32_t 
                uint32_t bound, uint8_t *h, uint32_t *mask, uint32_t *minf, cudaStream_t st);
 int pdb_build_device(Ctx *c, int side, const int *tiles, int k, uint8_t *table, cudaStream_t st);
 size_t rc_corner_entries();
-int rc_corner_gather(const uint8_t *table, const uint64_t *states, uint32_t n, const uint8_t *g, uint32_t bound,
-                     uint8_t *h, uint32_t *mask, uint32_t *minf, cudaStream_t st);
+int rc_corner_gather(const uint8_t *table, uint32_t div, const uint64_t *states, uint32_t n, const uint8_t *g,
+                     uint32_t bound, uint8_t *h, uint32_t *mask, uint32_t *minf, cudaStream_t st);
+int pdb_div_compress(const uint8_t *src, uint64_t n, uint32_t k, uint8_t *dst, cudaStream_t st);
 int rc_corner_build_device(Ctx *c, uint8_t *table, cudaStream_t st);
 int combine(int domain, const ComboParams &C, const uint64_t *states, uint32_t n, const uint8_t *member_h,
             size_t member_stride, const uint8_t *g, uint32_t bound, uint8_t *h, uint32_t *mask, uint32_t *minf,
@@ -408,7 +409,7 @@ int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
         const PdbGPU &p = *c->pdbs[c->heur_index[heur_id]];
         if (p.domain != domain) return fail(CBDFS_EINVAL, "PDB %d is for another domain", heur_id);
         if (domain == CBDFS_DOM_RC3) {
-            int r = rc_corner_gather(p.table[0], d_states, n, d_g, bound, d_h, d_mask, d_minf, st);
+            int r = rc_corner_gather(p.table[0], p.div, d_states, n, d_g, bound, d_h, d_mask, d_minf, st);
             return r ? r : mark(s, st);
         }
         PdbParams P{};
@@ -418,6 +419,7 @@ int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
             P.k[q] = p.k[q];
             P.table[q] = p.table[q];
             P.entries[q] = (uint32_t)p.entries[q];
+            P.div = p.div;
             for (int i = 0; i < p.k[q]; ++i) {
                 P.tiles[q][i] = p.tiles[q][i];
                 P.weight[q][i] = (uint32_t)npk(N - 1 - i, p.k[q] - 1 - i);
@@ -681,6 +683,22 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
     return CBDFS_OK;
 }
 
+// Replace the full table *t (n entries, on the device) by its DIV compression by k.
+static int div_compress_table(Ctx *c, uint8_t **t, size_t n, uint32_t k, size_t *entries, cudaStream_t st) {
+    const size_t m = (n + k - 1) / k;
+    uint8_t *d = nullptr;
+    int rc = dev_alloc(c, (void **)&d, m);
+    if (rc) return rc;
+    if ((rc = pdb_div_compress(*t, n, k, d, st)) || cudaStreamSynchronize(st) != cudaSuccess) {
+        dev_free(c, d, m);
+        return rc ? rc : fail(CBDFS_EDEVICE, "DIV compression");
+    }
+    dev_free(c, *t, n);
+    *t = d;
+    *entries = m;
+    return CBDFS_OK;
+}
+
 // the cube's one pattern: the eight corner cubies 0..7 in order (the 8-corner PDB)
 static int check_rc_corner_pattern(int n_patterns, const int *k, const int *tiles) {
     if (n_patterns != 1 || k[0] != 8) return fail(CBDFS_EINVAL, "the cube's PDB is one pattern of the 8 corners");
@@ -696,6 +714,8 @@ int cbdfs_pdb_load(cbdfs_ctx *ctx, const cbdfs_pdb_desc *d, int *heur_id) {
     CUDA_TRY(cudaSetDevice(c->device));
     if (d->domain < 0 || d->domain > 2) return fail(CBDFS_EINVAL, "domain %d", d->domain);
     if (d->n_patterns < 1 || d->n_patterns > 4) return fail(CBDFS_EINVAL, "n_patterns %d outside 1..4", d->n_patterns);
+    if (d->div < 0) return fail(CBDFS_EINVAL, "div %d", d->div);
+    const uint32_t div = d->div > 1 ? (uint32_t)d->div : 1u;
     if (d->domain == CBDFS_DOM_RC3) {
         int rc = check_rc_corner_pattern(d->n_patterns, d->k, d->tiles);
         if (rc) return rc;
@@ -711,6 +731,12 @@ int cbdfs_pdb_load(cbdfs_ctx *ctx, const cbdfs_pdb_desc *d, int *heur_id) {
             CUDA_TRY(cudaMemcpy(p->table[0], d->tables[0], p->entries[0], cudaMemcpyHostToDevice));
         } else if ((rc = rc_corner_build_device(c, p->table[0], c->slots[0].stream))) {
             return rc;
+        }
+        if (div > 1) {
+            if ((rc = div_compress_table(c, &p->table[0], p->entries[0], div, &p->entries[0], c->slots[0].stream)))
+                return rc;
+            p->bytes = p->entries[0];
+            p->div = div;
         }
         c->pdbs.push_back(std::move(p));
         c->heur_kind.push_back(1);
@@ -745,7 +771,14 @@ int cbdfs_pdb_load(cbdfs_ctx *ctx, const cbdfs_pdb_desc *d, int *heur_id) {
             rc = pdb_build_device(c, p->side, p->tiles[q], p->k[q], p->table[q], c->slots[0].stream);
             if (rc) return rc;
         }
+        if (div > 1) {
+            p->bytes -= p->entries[q];
+            if ((rc = div_compress_table(c, &p->table[q], p->entries[q], div, &p->entries[q], c->slots[0].stream)))
+                return rc;
+            p->bytes += p->entries[q];
+        }
     }
+    p->div = div;
     c->pdbs.push_back(std::move(p));
     c->heur_kind.push_back(1);
     c->heur_index.push_back((int)c->pdbs.size() - 1);

@@ -81,7 +81,8 @@ struct PdbGPU {
     int domain = 0, side = 0, n_patterns = 0;
     int k[4] = {}, tiles[4][16] = {};
     uint8_t *table[4] = {};
-    size_t entries[4] = {};
+    size_t entries[4] = {};            // stored entries (after DIV compression)
+    uint32_t div = 1;                  // DIV compression: entry = min over div adjacent ranks
     size_t bytes = 0;
 };
 
@@ -91,7 +92,8 @@ struct PdbParams {
     int k[4];
     int tiles[4][8];
     uint32_t weight[4][8];   // (N-1-i)! / (N-k)!
-    uint32_t entries[4];     // table sizes N!/(N-k)!
+    uint32_t entries[4];     // table sizes: N!/(N-k)!, or ceil of that / div
+    uint32_t div;            // DIV compression of every table (1: none)
     const uint8_t *table[4];
 };
 

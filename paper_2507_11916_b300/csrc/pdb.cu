@@ -65,7 +65,7 @@ k_pdb_gather(const uint64_t *__restrict__ states, uint32_t n, const PdbParams P,
     // a malformed state (a repeated tile) can rank past its table: clamp, so that such input
     // gives a meaningless h but no out-of-bounds read
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = (q < P.n_patterns) ? __ldg(P.table[q] + min(rank[q], P.entries[q] - 1u)) : 0u;
+    for (int q = 0; q < 4; ++q) v[q] = (q < P.n_patterns) ? __ldg(P.table[q] + min(rank[q] / P.div, P.entries[q] - 1u)) : 0u;
     uint32_t hv = v[0] + v[1] + v[2] + v[3];
     hv = (s == goal) ? 0u : min(hv, 255u);
     uint32_t f = 0xFFFFFFFFu;
@@ -87,6 +87,17 @@ k_pdb_gather(const uint64_t *__restrict__ states, uint32_t n, const PdbParams P,
         const uint32_t m = __reduce_min_sync(0xFFFFFFFFu, lane < (int)(blockDim.x >> 5) ? warp_min[lane] : 0xFFFFFFFFu);
         if (lane == 0 && m != 0xFFFFFFFFu) atomicMin(minf, m);
     }
+}
+
+// DIV compression: entry j = the least of the k entries j*k .. j*k+k-1 that exist
+__global__ void __launch_bounds__(256) k_div_compress(const uint8_t *__restrict__ src, uint64_t n, uint32_t k,
+                                                     uint8_t *__restrict__ dst, uint64_t m) {
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const uint64_t lo = j * k, hi = lo + k < n ? lo + k : n;
+    uint32_t best = 255;
+    for (uint64_t i = lo; i < hi; ++i) best = min(best, (uint32_t)__ldg(src + i));
+    dst[j] = (uint8_t)best;
 }
 
 // ---- builder ---------------------------------------------------------------------------
@@ -225,6 +236,13 @@ int pdb_gather(int domain, const PdbParams &P, const uint64_t *states, uint32_t 
         k_pdb_gather<3><<<blocks, 256, 0, st>>>(states, n, P, g, bound, h, mask, minf);
     else
         k_pdb_gather<4><<<blocks, 256, 0, st>>>(states, n, P, g, bound, h, mask, minf);
+    CUDA_TRY(cudaGetLastError());
+    return CBDFS_OK;
+}
+
+int pdb_div_compress(const uint8_t *src, uint64_t n, uint32_t k, uint8_t *dst, cudaStream_t st) {
+    const uint64_t m = (n + k - 1) / k;
+    k_div_compress<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(src, n, k, dst, m);
     CUDA_TRY(cudaGetLastError());
     return CBDFS_OK;
 }

@@ -10,7 +10,8 @@
 // k_corner_level: one thread per index; an entry at distance d applies the 18 face turns to
 // its configuration and marks every unseen result d+1 (writers of one entry in one level all
 // write d+1, so the race is benign).  Levels run until one marks nothing.
-// k_corner_gather: one state per lane; the table byte, the goal rule and the bound test
+// k_corner_gather: one state per lane; the table byte (at index / div for a DIV-compressed
+// table), the goal rule and the bound test
 // (ballot mask word, warp and block minimum of f above the bound, one atomicMin per block).
 #include "common.cuh"
 #include "domain.h"
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(256) k_corner_level(uint8_t *table, int d, int
 }
 
 __global__ void __launch_bounds__(256)
-k_corner_gather(const uint64_t *__restrict__ states, uint32_t n, const uint8_t *__restrict__ table,
+k_corner_gather(const uint64_t *__restrict__ states, uint32_t n, const uint8_t *__restrict__ table, uint32_t div,
                 const uint8_t *__restrict__ g, uint32_t bound, uint8_t *__restrict__ h_out,
                 uint32_t *__restrict__ mask, uint32_t *__restrict__ minf) {
     __shared__ uint32_t warp_min[8];
@@ -106,7 +107,7 @@ k_corner_gather(const uint64_t *__restrict__ states, uint32_t n, const uint8_t *
         }
         // a malformed word (a field above 23, or two cubies on one slot) would index past the
         // table: clamp, so that such input gives a meaningless h but no out-of-bounds read
-        uint32_t hv = __ldg(table + min(corner_index(p, t), kCornerEntries - 1u));
+        uint32_t hv = __ldg(table + min(corner_index(p, t), kCornerEntries - 1u) / div);
         hv = rc_is_goal(w.x, w.y) ? 0u : hv;
         h_out[i] = (uint8_t)hv;
         f = (uint32_t)g[i] + hv;
@@ -129,10 +130,11 @@ k_corner_gather(const uint64_t *__restrict__ states, uint32_t n, const uint8_t *
 
 size_t rc_corner_entries() { return kCornerEntries; }
 
-int rc_corner_gather(const uint8_t *table, const uint64_t *states, uint32_t n, const uint8_t *g, uint32_t bound,
-                     uint8_t *h, uint32_t *mask, uint32_t *minf, cudaStream_t st) {
+// div: the table's DIV compression (1: none)
+int rc_corner_gather(const uint8_t *table, uint32_t div, const uint64_t *states, uint32_t n, const uint8_t *g,
+                     uint32_t bound, uint8_t *h, uint32_t *mask, uint32_t *minf, cudaStream_t st) {
     if (n == 0) return CBDFS_OK;
-    k_corner_gather<<<(n + 255) / 256, 256, 0, st>>>(states, n, table, g, bound, h, mask, minf);
+    k_corner_gather<<<(n + 255) / 256, 256, 0, st>>>(states, n, table, div, g, bound, h, mask, minf);
     CUDA_TRY(cudaGetLastError());
     return CBDFS_OK;
 }
