@@ -731,6 +731,20 @@ def fp8_scales(P, ctx, Ws, bs):
     return np.array(sc, np.float32)
 
 
+def job_rate(ms, units, dist=None, device="cpu"):
+    """Whole-job throughput over replicas (weak scaling, one process per GPU): the slowest
+    rank's time and every rank's units.  Returns (units/s over all ranks, max ms)."""
+    if dist is not None:
+        import torch
+        t = torch.tensor([ms, units], dtype=torch.float64, device=device)
+        m = t[:1].clone()
+        u = t[1:].clone()
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms, units = float(m.item()), float(u.item())
+    return units / (ms / 1e3), ms
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -799,11 +813,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    value, ms = job_rate(ms, B * args.steps, dist, dev)
     clk = clocks.stop()
-    value = world * B * args.steps / (ms / 1e3)
     # the graph replays the same pipeline: check its result against a host-buffer call
     h_ref, mask_ref, minf_ref = P.heur_submit_batch(ctx, hid, P.DOM_STP4, states, g, BOUND)
     assert np.array_equal(dh.cpu().numpy(), h_ref), "graph replay result differs"
