@@ -190,7 +190,7 @@ def run_reference(args):
         "e2e": {"value": v, "unit": "states/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
-def search_rates(P, ctx, hids, seconds, work_num=1024):
+def search_rates(P, ctx, hids, seconds, work_num=256):
     """IDA* nodes/s with the network heuristic in each precision at equal solution cost.
 
     fixed_tree: Manhattan distance prunes and the network is evaluated on every generated node
@@ -268,11 +268,11 @@ def cube_search_leg(P, args):
                 "fp8": P.cbdfs_net_load(ctx, P.DOM_RC3, Ws, bs, P.PREC_FP8, P.HEAD_CLASSIFIER, 0,
                                         act_scales=calib_scales(Ws, bs, P.DOM_RC3)),
                 "fp32": P.cbdfs_net_load(ctx, P.DOM_RC3, Ws, bs, P.PREC_FP32, P.HEAD_CLASSIFIER, 0)}
-        starts = [W.rc_scramble(9, W.seed_for(W.TAG_C2, 100 + i)) for i in range(4)]
+        starts = [W.rc_scramble(10, W.seed_for(W.TAG_C2, 100 + i)) for i in range(4)]
         starts = [P.cbdfs_apply_moves(P.DOM_RC3, W.rc_goal(), m) for m in starts]
         threads = min(32, os.cpu_count() or 4)
         cfg = dict(threads=threads, work_num=256, batch=4096, timeout_us=500)
-        out = {"instances": "4 seeded 9-turn cube scrambles", "threads": threads, "batch": 4096,
+        out = {"instances": "4 seeded 10-turn cube scrambles", "threads": threads, "batch": 4096,
                "corner_pdb_build_s": build_s}
 
         def run(hid, fixed):

@@ -38,13 +38,18 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 // shared batches
 // ---------------------------------------------------------------------------------------
 struct Batch {
-    // pinned host arrays; h, mask and minf lie in `out` in the slot's device layout
-    // (slot_out_bytes), so that one copy returns them
+    // page-locked host arrays; h, mask and minf lie in `out` in the slot's layout
+    // (slot_out_bytes): the kernels write h and the mask there, minf comes back by one copy
     uint64_t *states = nullptr;
     uint8_t *g = nullptr, *h = nullptr, *out = nullptr;
     uint32_t *mask = nullptr, *minf = nullptr;
     uint8_t *h2 = nullptr;  // fixed-tree mode: the evaluated (not pruning) heuristic
-    uint32_t *mask2 = nullptr, *minf2 = nullptr;
+    // the same page-locked buffers as the kernels address them (mapped host memory: the
+    // kernels read the states and write h and the mask over the bus, no staging copies)
+    const uint64_t *d_states = nullptr;
+    const uint8_t *d_g = nullptr;
+    uint8_t *d_h = nullptr, *d_h2 = nullptr;
+    uint32_t *d_mask = nullptr;
     uint32_t n = 0;                       // states in the batch
     std::atomic<uint32_t> done_gen{0};    // == gen once results are readable
     uint32_t gen = 0;                     // bumped each time the buffer is reopened
@@ -164,23 +169,20 @@ int submit(Shared &S, Batch &b) {
     b.slot = si;
     Slot &sl = c->slots[si];
     cudaStream_t st = sl.stream;
-    const int w = S.D->words;
     const uint32_t n = b.n;
     int rc = CBDFS_OK;
-    if (n && (cudaMemcpyAsync(sl.d_states, b.states, (size_t)n * 8 * w, cudaMemcpyHostToDevice, st) ||
-              cudaMemcpyAsync(sl.d_g, b.g, n, cudaMemcpyHostToDevice, st)))
-        return fail(CBDFS_EDEVICE, "batch upload");
     if (S.prune_heur != S.heur) {
         // fixed-tree mode: evaluate the network on every state, prune with the other one
-        rc = run_eval(c, sl, S.heur, S.D->dom, sl.d_states, sl.d_g, S.bound, n, sl.d_h, sl.d_mask,
+        rc = run_eval(c, sl, S.heur, S.D->dom, b.d_states, b.d_g, S.bound, n, b.d_h2, sl.d_mask,
                       sl.d_minf, nullptr, st);
         if (rc) return rc;
-        if (n && cudaMemcpyAsync(b.h2, sl.d_h, n, cudaMemcpyDeviceToHost, st)) return fail(CBDFS_EDEVICE, "download");
     }
-    rc = run_eval(c, sl, S.prune_heur, S.D->dom, sl.d_states, sl.d_g, S.bound, n, sl.d_h, sl.d_mask,
+    rc = run_eval(c, sl, S.prune_heur, S.D->dom, b.d_states, b.d_g, S.bound, n, b.d_h, b.d_mask,
                   sl.d_minf, nullptr, st);
     if (rc) return rc;
-    if (cudaMemcpyAsync(b.out, sl.d_h, slot_out_bytes(c), cudaMemcpyDeviceToHost, st) || cudaEventRecord(b.ev, st))
+    // h and the mask are already in the batch's host buffers; the least f above the bound is
+    // the one word read back
+    if (cudaMemcpyAsync(b.minf, sl.d_minf, 4, cudaMemcpyDeviceToHost, st) || cudaEventRecord(b.ev, st))
         return fail(CBDFS_EDEVICE, "result download");
     b.state = 2;
     S.nbatches++;
@@ -972,14 +974,24 @@ int cbdfs_solve(cbdfs_ctx *ctx, int domain, const uint64_t *start, int algo, int
     for (size_t i = 0; i < 2 * sv.slots.size() && !rc; ++i) {
         auto b = std::make_unique<Batch>();
         const size_t cap = cfg.batch;
-        if (cudaMallocHost(&b->states, cap * 8 * w) || cudaMallocHost(&b->g, cap) ||
-            cudaMallocHost(&b->out, slot_out_bytes(c)) || cudaMallocHost(&b->h2, cap) ||
+        const unsigned fl = cudaHostAllocMapped | cudaHostAllocPortable;
+        if (cudaHostAlloc(&b->states, cap * 8 * w, fl) || cudaHostAlloc(&b->g, cap, fl) ||
+            cudaHostAlloc(&b->out, slot_out_bytes(c), fl) || cudaHostAlloc(&b->h2, cap, fl) ||
             cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming))
             rc = fail(CBDFS_ENOMEM, "pinned batch buffers");
-        if (b->out) {
+        if (!rc) {
             b->h = b->out;
             b->mask = reinterpret_cast<uint32_t *>(b->out + c->max_batch_pad);
             b->minf = b->mask + c->max_batch_pad / 32;
+            void *ds = nullptr, *dg = nullptr, *dout = nullptr, *dh2 = nullptr;
+            if (cudaHostGetDevicePointer(&ds, b->states, 0) || cudaHostGetDevicePointer(&dg, b->g, 0) ||
+                cudaHostGetDevicePointer(&dout, b->out, 0) || cudaHostGetDevicePointer(&dh2, b->h2, 0))
+                rc = fail(CBDFS_EDEVICE, "mapped batch buffers");
+            b->d_states = static_cast<const uint64_t *>(ds);
+            b->d_g = static_cast<const uint8_t *>(dg);
+            b->d_h = static_cast<uint8_t *>(dout);
+            b->d_mask = reinterpret_cast<uint32_t *>(b->d_h + c->max_batch_pad);
+            b->d_h2 = static_cast<uint8_t *>(dh2);
         }
         sv.batches.push_back(std::move(b));
     }
