@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstring>
 #include <random>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -38,12 +39,14 @@ using namespace dev;
 
 constexpr int kThreads = 192;
 constexpr int kDwRows = 512;   // rows of one split of the last layer's dW
-constexpr int kSumRows = 256;  // rows of one chunk of a column sum
+constexpr int kSumRows = 64;   // rows of one chunk of a column sum
 constexpr int kStageA = kBM * 128;
 
 // ---------------------------------------------------------------------------------------
 // TN GEMM on tcgen05: C[M][N] = A[M][K] B[N][K]^T, both BF16 K-major, FP32 accumulate.
 // EPI 1: C FP32.  EPI 2: C BF16 = acc * (mask[m][n] > 0) (mask BF16 [M][N]).
+// Split K (gridDim.z > 1, EPI 1): CTA z contracts k-blocks [z KB/S, (z+1) KB/S) into its own
+// partial out + z M N; k_sum_splits then adds the partials in split order.
 // ---------------------------------------------------------------------------------------
 template <int BN, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -52,7 +55,9 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     constexpr int kStageB = BN * 128;
-    const int KB = K / 64;
+    const int kb0 = (int)((long long)(K / 64) * blockIdx.z / gridDim.z);
+    const int KB = (int)((long long)(K / 64) * (blockIdx.z + 1) / gridDim.z) - kb0;
+    if (EPI == 1) out = static_cast<float *>(out) + (size_t)blockIdx.z * gridDim.y * kBM * N;
     uint8_t *A = smem;
     uint8_t *B = smem + stages * kStageA;
     uint64_t *bars = reinterpret_cast<uint64_t *>(B + stages * kStageB);
@@ -83,8 +88,8 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 const int s = kb % stages, u = kb / stages;
                 if (kb >= stages && !mbar_wait(smem_u32(&empty[s]), (u - 1) & 1, err, DEVERR_STAGE_EMPTY)) break;
                 mbar_arrive_expect_tx(smem_u32(&full[s]), kStageA + kStageB);
-                tma_load_2d(smem_u32(A + s * kStageA), &tmA, smem_u32(&full[s]), kb * 64, m0);
-                tma_load_2d(smem_u32(B + s * kStageB), &tmB, smem_u32(&full[s]), kb * 64, n0);
+                tma_load_2d(smem_u32(A + s * kStageA), &tmA, smem_u32(&full[s]), (kb0 + kb) * 64, m0);
+                tma_load_2d(smem_u32(B + s * kStageB), &tmB, smem_u32(&full[s]), (kb0 + kb) * 64, n0);
                 ++issued;
             }
             // bounded drain of this thread's loads before the CTA can exit
@@ -155,16 +160,27 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     }
 }
 
+__global__ void k_sum_splits(const float *__restrict__ part, int S, int len, float *__restrict__ out);
+
+// splits > 1 (EPI 1 only): the partials go to `part` (splits x M x N floats), then their sum
+// in split order to `out`
 template <int BN, int EPI>
 int gemm_tn(const CUtensorMap &tmA, const CUtensorMap &tmB, int M, int N, int K, void *out,
-            const __nv_bfloat16 *mask, int *err, cudaStream_t st) {
+            const __nv_bfloat16 *mask, int *err, cudaStream_t st, int splits = 1, float *part = nullptr) {
     constexpr int kStageB = BN * 128;
     const int stages = 4;
     const size_t smem = 1024 + 256 + (size_t)stages * (kStageA + kStageB);
     auto kern = k_gemm_tn<BN, EPI>;
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<dim3(N / BN, M / kBM), kThreads, smem, st>>>(tmA, tmB, K, N, out, mask, stages, err);
+    const bool split = EPI == 1 && splits > 1 && part;
+    kern<<<dim3(N / BN, M / kBM, split ? splits : 1), kThreads, smem, st>>>(tmA, tmB, K, N, split ? part : out,
+                                                                           mask, stages, err);
     CUDA_TRY(cudaGetLastError());
+    if (split) {
+        const int len = M * N;
+        k_sum_splits<<<(len + 255) / 256, 256, 0, st>>>(part, splits, len, static_cast<float *>(out));
+        CUDA_TRY(cudaGetLastError());
+    }
     return CBDFS_OK;
 }
 
@@ -172,13 +188,25 @@ int gemm_tn(const CUtensorMap &tmA, const CUtensorMap &tmB, int M, int N, int K,
 // small kernels
 // ---------------------------------------------------------------------------------------
 
-// BF16 transpose: in [R][C] -> out [C][R], 32 x 32 tiles through shared memory
-__global__ void k_transpose(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ out, int R, int C) {
-    __shared__ __nv_bfloat16 t[32][33];
-    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-    for (int i = threadIdx.y; i < 32; i += 8) t[i][threadIdx.x] = in[(size_t)(r0 + i) * C + c0 + threadIdx.x];
+// BF16 transpose: in [R][C] -> out [C][R] (R, C multiples of 64), 64 x 64 tiles through shared
+// memory, moved as element pairs: a warp reads and writes 128 contiguous bytes, and the padded
+// rows (65 elements) keep the column reads on distinct banks.  Block (32, 8).
+__global__ void __launch_bounds__(256) k_transpose(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ out,
+                                                   int R, int C) {
+    __shared__ __nv_bfloat16 t[64][65];
+    const int c0 = blockIdx.x * 64, r0 = blockIdx.y * 64, tx = threadIdx.x;
+    for (int i = threadIdx.y; i < 64; i += 8) {
+        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(in + (size_t)(r0 + i) * C + c0 + 2 * tx);
+        t[i][2 * tx] = v.x;
+        t[i][2 * tx + 1] = v.y;
+    }
     __syncthreads();
-    for (int i = threadIdx.y; i < 32; i += 8) out[(size_t)(c0 + i) * R + r0 + threadIdx.x] = t[threadIdx.x][i];
+    for (int j = threadIdx.y; j < 64; j += 8) {
+        __nv_bfloat162 v;
+        v.x = t[2 * tx][j];
+        v.y = t[2 * tx + 1][j];
+        *reinterpret_cast<__nv_bfloat162 *>(out + (size_t)(c0 + j) * R + r0 + 2 * tx) = v;
+    }
 }
 
 // transposed one-hot X^T [K1pad][Bp] (BF16) of the packed states; rows >= n are zero
@@ -312,6 +340,22 @@ __global__ void k_colsum_part(const T *__restrict__ X, int n, int J, int chunk, 
     for (int m = mb; m < me; ++m) s += tof(X[(size_t)m * J + j]);
     part[(size_t)r * J + j] = s;
 }
+// the same for BF16 with J even: a thread sums a column pair (one 4-byte load per row), rows
+// in the same order, so every column's sum is the scalar kernel's
+__global__ void k_colsum_part2(const __nv_bfloat16 *__restrict__ X, int n, int J, int chunk, float *__restrict__ part) {
+    const int j = 2 * (blockIdx.x * blockDim.x + threadIdx.x), r = blockIdx.y;
+    if (j >= J) return;
+    const int mb = r * chunk, me = min(n, mb + chunk);
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll 8
+    for (int m = mb; m < me; ++m) {
+        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(X + (size_t)m * J + j));
+        s0 += v.x;
+        s1 += v.y;
+    }
+    part[(size_t)r * J + j] = s0;
+    part[(size_t)r * J + j + 1] = s1;
+}
 
 // sum of per-row losses (one block, fixed order), divided by n
 __global__ void k_mean(const float *__restrict__ v, int n, float *__restrict__ out) {
@@ -425,12 +469,20 @@ struct TrainState {
     float *logits = nullptr, *dzl = nullptr, *row_loss = nullptr, *loss = nullptr;
     float *red = nullptr;                                  // split / row-chunk partial sums
     size_t red_floats = 0;
+    float *dw_part = nullptr;                              // split-K partials of the hidden dW
     uint64_t *states = nullptr;
     uint8_t *labels = nullptr;
     int64_t step = 0;
     std::vector<std::pair<void *, size_t>> allocs;
     std::map<long long, CUtensorMap> maps;
 };
+
+// Row splits of a hidden layer's dW = dZ^T A (O x I outputs, Bp rows contracted): enough
+// that the output tiles times the splits come near the SM count, at most one k-block each.
+static int dw_splits(const Ctx *c, int O, int I, int Bp) {
+    const int tiles = (I / (I % 256 == 0 ? 256 : 128)) * (O / kBM);
+    return std::max(1, std::min(Bp / 64, c->num_sms / std::max(tiles, 1)));
+}
 
 static int talloc(Ctx *c, TrainState &T, void **p, size_t bytes) {
     int rc = dev_alloc(c, p, bytes);
@@ -501,6 +553,13 @@ static int train_setup(Ctx *c, NetGPU &net, int B, const float *const *host_w, c
             T->red_floats = std::max((size_t)((Bp + kDwRows - 1) / kDwRows) * C * KL,
                                      (size_t)((Bp + kSumRows - 1) / kSumRows) * std::max(maxw, (size_t)C));
             if (!rc) rc = talloc(c, *T, (void **)&T->red, T->red_floats * 4);
+            size_t part = 0;  // the hidden layers' dW in row splits (dw_splits)
+            for (int l = 0; l < L - 1; ++l) {
+                const int O = net.dims[l + 1], I = l == 0 ? (int)k1 : net.dims[l];
+                const int S = dw_splits(c, O, I, Bp);
+                if (S > 1) part = std::max(part, (size_t)S * O * I);
+            }
+            if (!rc && part) rc = talloc(c, *T, (void **)&T->dw_part, part * 4);
         }
         if (!rc) rc = talloc(c, *T, (void **)&T->loss, 4);
         if (!rc) rc = talloc(c, *T, (void **)&T->states, (size_t)Bp * 16);
@@ -547,7 +606,12 @@ template <typename T>
 static int colsum(TrainState &S, const T *X, int n, int J, float *out, cudaStream_t st) {
     const int R = (n + kSumRows - 1) / kSumRows;
     if ((size_t)R * J > S.red_floats) return fail(CBDFS_EINVAL, "column-sum scratch");
-    k_colsum_part<T><<<dim3((J + 255) / 256, R), 256, 0, st>>>(X, n, J, kSumRows, S.red);
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+        if (J % 2 == 0) k_colsum_part2<<<dim3((J / 2 + 255) / 256, R), 256, 0, st>>>(X, n, J, kSumRows, S.red);
+        else k_colsum_part<T><<<dim3((J + 255) / 256, R), 256, 0, st>>>(X, n, J, kSumRows, S.red);
+    } else {
+        k_colsum_part<T><<<dim3((J + 255) / 256, R), 256, 0, st>>>(X, n, J, kSumRows, S.red);
+    }
     k_sum_splits<<<(J + 255) / 256, 256, 0, st>>>(S.red, R, J, out);
     CUDA_TRY(cudaGetLastError());
     return CBDFS_OK;
@@ -588,22 +652,23 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
     for (int l = L - 2; l >= 0; --l) {
         const int O = net.dims[l + 1], I = l == 0 ? net.k1pad : net.dims[l];
         // dW_l = dZ_l^T A_{l-1}: transpose both to K-major over the batch
-        k_transpose<<<dim3(O / 32, Bp / 32), dim3(32, 8), 0, st>>>(T.dz[l], T.t_dz, Bp, O);
+        k_transpose<<<dim3(O / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.dz[l], T.t_dz, Bp, O);
         if (l == 0) {
             CUDA_TRY(cudaMemsetAsync(T.t_a, 0, (size_t)I * Bp * 2, st));
             if (net.domain == CBDFS_DOM_STP3) k_onehot_t<CBDFS_DOM_STP3><<<(Bp + 255) / 256, 256, 0, st>>>(T.states, n, Bp, T.t_a);
             else if (net.domain == CBDFS_DOM_STP4) k_onehot_t<CBDFS_DOM_STP4><<<(Bp + 255) / 256, 256, 0, st>>>(T.states, n, Bp, T.t_a);
             else k_onehot_t<CBDFS_DOM_RC3><<<(Bp + 255) / 256, 256, 0, st>>>(T.states, n, Bp, T.t_a);
         } else {
-            k_transpose<<<dim3(I / 32, Bp / 32), dim3(32, 8), 0, st>>>(T.act[l - 1], T.t_a, Bp, I);
+            k_transpose<<<dim3(I / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.act[l - 1], T.t_a, Bp, I);
         }
         // the output width is the (padded) input width; padding columns of the one-hot are
         // zero, so their gradient is exactly zero
         const CUtensorMap *ma = bmap(T, T.t_dz, Bp, O, kBM);
         const CUtensorMap *mb = bmap(T, T.t_a, Bp, I, I % 256 == 0 ? 256 : 128);
         if (!ma || !mb) return CBDFS_EDEVICE;
-        rc = (I % 256 == 0) ? gemm_tn<256, 1>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st)
-                            : gemm_tn<128, 1>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st);
+        const int S = T.dw_part ? dw_splits(c, O, I, Bp) : 1;
+        rc = (I % 256 == 0) ? gemm_tn<256, 1>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st, S, T.dw_part)
+                            : gemm_tn<128, 1>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st, S, T.dw_part);
         if (rc) return rc;
         if (int r = colsum(T, T.dz[l], n, O, T.gb[l], st)) return r;
         if (l > 0) {
