@@ -368,10 +368,34 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     P.done_index = chain_counter_ints(c) - 1;
     int rc = chain_launch(domain, fp8, bn, maps, P, grid, st);
     if (rc || (rc = mark(s, st)) || P.fused_head) return rc;
-    // the last layer (FP32) over the stored BF16 activations of the last hidden layer
-    rc = head(true, domain, net.head, s.act[(nh - 1) & 1], net.dims[nh], net.dims[L], net.w32[L - 1],
-              net.b32[L - 1], d_states, d_g, bound, n, net.max_with_md, net.head_param(), d_h, d_mask, d_minf,
-              d_y, st);
+    // the last layer over the stored BF16 activations of the last hidden layer: on the tensor
+    // cores (split FP32 weights) for a prepared classifier head, else FP32 on the CUDA cores
+    if (net.head_cpad) {
+        const CUtensorMap *ma = act_map(s, c, (nh - 1) & 1, net.dims[nh], 2);
+        if (!ma) return CBDFS_EDEVICE;
+        HeadTcParams H{};
+        H.K = net.dims[nh];
+        H.C = net.dims[L];
+        H.cpad = net.head_cpad;
+        H.head_kind = net.head;
+        H.quantile = net.quantile;
+        H.max_with_md = net.max_with_md;
+        H.n = n;
+        H.states = d_states;
+        H.g = d_g;
+        H.bound = bound;
+        H.b_last = net.b32[L - 1];
+        H.h = d_h;
+        H.mask = d_mask;
+        H.minf = d_minf;
+        H.y = d_y;
+        H.err = c->d_err;
+        rc = head_tc(domain, *ma, net.tm_wsplit, H, rows_pad, st);
+    } else {
+        rc = head(true, domain, net.head, s.act[(nh - 1) & 1], net.dims[nh], net.dims[L], net.w32[L - 1],
+                  net.b32[L - 1], d_states, d_g, bound, n, net.max_with_md, net.head_param(), d_h, d_mask, d_minf,
+                  d_y, st);
+    }
     return rc ? rc : mark(s, st);
 }
 
@@ -521,6 +545,7 @@ void cbdfs_destroy(cbdfs_ctx *ctx) {
             if (n->w32[l]) cudaFree(n->w32[l]);
             if (n->b32[l]) cudaFree(n->b32[l]);
         }
+        if (n->w_split) cudaFree(n->w_split);
     }
     for (auto &p : c->pdbs)
         for (int q = 0; q < 4; ++q)
@@ -673,6 +698,32 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
                                    fp8 ? 1 : 2, (uint64_t)Kp, (uint64_t)O, kblk, kChainBNSmall)))
                 return rc;
         }
+    }
+    // the tensor-core head: a classifier of 33..128 outputs behind BF16 / E4M3 hidden layers
+    // (the fused chain stores the last hidden layer in BF16 for it); W = W1 + W2 + W3 in BF16,
+    // each part the rounding of what the previous ones leave (24 bits of mantissa in all)
+    const int C = d->dims[L], KL = d->dims[L - 1];
+    if (d->prec != CBDFS_PREC_FP32 && (d->head == CBDFS_HEAD_CLASSIFIER || d->head == CBDFS_HEAD_QUANTILE) &&
+        C > kMaxHeadC && C <= kHeadTcMaxC && KL % 64 == 0) {
+        const int cpad = (C + 15) / 16 * 16;
+        std::vector<uint16_t> sp((size_t)3 * cpad * KL, 0);
+        for (int c = 0; c < C; ++c)
+            for (int k = 0; k < KL; ++k) {
+                float r = d->weights[L - 1][(size_t)c * KL + k];
+                for (int part = 0; part < 3; ++part) {
+                    const uint16_t b16 = f32_to_bf16_rne(r);
+                    sp[((size_t)part * cpad + c) * KL + k] = b16;
+                    float back;
+                    const uint32_t u = (uint32_t)b16 << 16;
+                    memcpy(&back, &u, 4);
+                    r -= back;  // exact: r and its BF16 rounding are within a factor of two
+                }
+            }
+        if ((rc = upload(&N.w_split, sp.data(), sp.size() * 2))) return rc;
+        if ((rc = make_tmap_2d(&N.tm_wsplit, N.w_split, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (uint64_t)KL,
+                               (uint64_t)3 * cpad, 64, cpad)))
+            return rc;
+        N.head_cpad = cpad;
     }
     if ((size_t)d->dims[L] * 4 * 4 > 48 * 1024) return fail(CBDFS_EINVAL, "output width too large");
     if (chain_ok(N) && (rc = ensure_chain(c, chain_partial_floats(N)))) return rc;

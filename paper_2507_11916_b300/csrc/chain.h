@@ -55,6 +55,28 @@ struct ChainParams {
     int trace_tiles;
 };
 
+// the last layer of a classifier network (33..128 outputs) on the tensor cores (head_tc.cu)
+constexpr int kHeadTcMaxC = 128;
+struct HeadTcParams {
+    int K;             // input width, a multiple of 64
+    int C, cpad;       // outputs, and their padding to a multiple of 16 (<= 128)
+    int head_kind;     // CBDFS_HEAD_CLASSIFIER or CBDFS_HEAD_QUANTILE
+    float quantile;
+    int max_with_md;
+    uint32_t n;
+    const uint64_t *states;
+    const uint8_t *g;
+    uint32_t bound;
+    const float *b_last;
+    uint8_t *h;
+    uint32_t *mask, *minf;
+    float *y;          // optional [n][C] logits
+    int *err;
+};
+
+int head_tc(int domain, const CUtensorMap &tmA, const CUtensorMap &tmW, const HeadTcParams &P, uint32_t rows_pad,
+            cudaStream_t st);
+
 // bn: kChainBN, or kChainBNSmall (maps.w with 64-row boxes)
 int chain_launch(int domain, bool fp8, int bn, const ChainMaps &maps, const ChainParams &P, int grid,
                  cudaStream_t st);

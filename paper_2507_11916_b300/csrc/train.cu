@@ -320,6 +320,22 @@ k_fgemm(const TA *__restrict__ A, long sam, long sak, const TB *__restrict__ B, 
         }
 }
 
+// the last layer's FP32 weights w[C][K] as three BF16 parts out[part][cpad][K] (W = W1 + W2 + W3,
+// each part the round-to-nearest-even BF16 of what the previous parts leave), for the
+// tensor-core head
+__global__ void k_split3(const float *__restrict__ w, int C, int K, int cpad, __nv_bfloat16 *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C * K) return;
+    const int c = i / K, k = i % K;
+    float r = w[i];
+#pragma unroll
+    for (int part = 0; part < 3; ++part) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(r);
+        out[((size_t)part * cpad + c) * K + k] = b;
+        r -= __bfloat162float(b);
+    }
+}
+
 // out[i] = sum over z of part[z][i] (+ bias), in split order
 __global__ void k_sum_splits(const float *__restrict__ part, int S, int len, float *__restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -700,6 +716,11 @@ static int train_update(Ctx *c, NetGPU &net, const cbdfs_train_cfg &tc, cudaStre
                                                 tc.eps, c1, c2, nullptr, 0, nullptr);
         if (l == net.L - 1) {  // the inference head reads the FP32 last layer
             CUDA_TRY(cudaMemcpyAsync(net.w32[l], T.w[l], (size_t)O * I * 4, cudaMemcpyDeviceToDevice, st));
+            if (net.w_split) {  // and the tensor-core head its three BF16 parts
+                k_split3<<<(O * I + 255) / 256, 256, 0, st>>>(T.w[l], O, I, net.head_cpad,
+                                                               static_cast<__nv_bfloat16 *>(net.w_split));
+                CUDA_TRY(cudaGetLastError());
+            }
         }
         CUDA_TRY(cudaMemcpyAsync(net.b32[l], T.b[l], (size_t)O * 4, cudaMemcpyDeviceToDevice, st));
     }

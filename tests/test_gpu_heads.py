@@ -173,3 +173,29 @@ def test_ida_with_a_composite_matches_oracle(P, ctx, orc, pdb8):
                           timeout_us=200, time_limit_s=60.0)
         assert r["cost"] == want["cost"] == dist[orc.perm_rank([(s >> (4 * p)) & 15 for p in range(9)])]
         assert [tuple(map(int, t)) for t in r["iters"]] == [tuple(t) for t in want["iters"]]
+
+
+@pytest.mark.parametrize("C", [81, 40, 128])
+def test_tensor_core_head_is_fp32_accurate(P, ctx, orc, C):
+    # 256 -> 256 -> C with an identity hidden layer: the stored BF16 activations are the one-hot
+    # rows exactly, so y_c = b_c + the sum of W2[c, i] over the 16 active inputs, in float64.  The
+    # head's three BF16 parts of W2 leave only the FP32 accumulation's rounding, a few 2^-24 of
+    # the summed magnitudes (a plain BF16 last layer would be off by ~1e-3 relative)
+    rng = np.random.default_rng(C)
+    W1 = np.eye(256, dtype=np.float32)
+    b1 = np.zeros(256, np.float32)
+    W2 = rng.normal(size=(C, 256)).astype(np.float32)
+    b2 = rng.normal(size=C).astype(np.float32)
+    hid = P.cbdfs_net_load(ctx, P.DOM_STP4, [W1, W2], [b1, b2], PREC["bf16"], P.HEAD_CLASSIFIER, 0)
+    n = 3000
+    s = W.random_stp_states(4, n, 1800 + C)
+    g = np.zeros(n, np.uint8)
+    h, mask, minf, y = P.heur_submit_batch(ctx, hid, P.DOM_STP4, s, g, 255, want_y=True, n_out=C)
+    X = orc.one_hot(orc.DOM_STP4, s)
+    terms = X[:, None, :] * W2.astype(np.float64)[None, :, :]
+    y64 = terms.sum(axis=2) + b2.astype(np.float64)
+    scale = np.abs(terms).sum(axis=2) + np.abs(b2)
+    err = np.abs(y.astype(np.float64) - y64) / scale
+    assert err.max() < 2e-6, err.max()
+    want = orc.h_classifier(y.astype(np.float64), None, orc.is_goal_states(orc.DOM_STP4, s))
+    assert np.array_equal(h, np.minimum(want, 255))

@@ -298,8 +298,8 @@ def test_c3_classifier_81(P, ctx, orc, prec, n):
 
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
 def test_c3_chain_matches_per_layer_kernels(P, ctx, orc, prec):
-    """Chain + separate head against the per-layer kernels + the same head: both store the last
-    hidden layer in BF16 after the same tensor-core arithmetic, so results are identical."""
+    """Chain + separate head against the per-layer kernels + the CUDA-core head: both store the
+    last hidden layer in BF16 after the same tensor-core arithmetic."""
     import torch
     Ws, bs = W.net_weights(**W.NET_C3)
     sc = fp8_act_scales(orc, 1, Ws, bs, W.random_stp_states(4, 4096, 13)) if prec == "fp8" else None
@@ -318,6 +318,13 @@ def test_c3_chain_matches_per_layer_kernels(P, ctx, orc, prec):
         fn(ctx, hid, P.DOM_STP4, ds, dg, 70, n, dh, dm, dmin, stream=torch.cuda.current_stream())
         torch.cuda.synchronize()
         outs.append((dh.cpu().numpy(), dm.cpu().numpy(), int(dmin.cpu()[0])))
-    assert np.array_equal(outs[0][0], outs[1][0])
-    assert np.array_equal(outs[0][1], outs[1][1]) and outs[0][2] == outs[1][2]
+    # the last layer: the chain's tensor-core head (split FP32 weights) and the per-layer path's
+    # CUDA-core FP32 head round their accumulations in different orders, so h may differ only
+    # where the two largest logits lie within 1e-4 of each other
+    y64, _, _ = oracle_net(orc, P.DOM_STP4, Ws, bs, prec, s, "classifier", True, sc)
+    tie = orc.classifier_margin(y64, 1e-4)
+    assert np.array_equal(outs[0][0][~tie], outs[1][0][~tie])
+    for h, mask, minf in outs:  # each path's bound test is that of its own h
+        wm, wf = orc.bound_test(g, h, 70)
+        assert np.array_equal(mask.view(np.uint32), wm) and (minf & 0xFFFFFFFF) == wf
     assert P.cbdfs_device_status(ctx) == 0
