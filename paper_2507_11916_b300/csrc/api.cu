@@ -311,7 +311,7 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     const int bn = P.mblocks <= kChainSmallMBlocks && 4 * rows_pad <= c->max_batch_pad ? kChainBNSmall : kChainBN;
     int max_tiles = 0;
     P.tile_start[0] = 0;
-    P.fused_head = net.dims[L] <= kMaxHeadC;
+    P.fused_head = net.dims[L] <= kMaxHeadC && !net.head_cpad;
     P.bf16_store_layer = !P.fused_head && fp8 ? nh - 1 : -1;
     for (int l = 0; l < nh; ++l) {
         maps.w[l] = bn == kChainBNSmall ? net.tm_w64[l] : net.tm_w[l];
@@ -704,7 +704,7 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
     // each part the rounding of what the previous ones leave (24 bits of mantissa in all)
     const int C = d->dims[L], KL = d->dims[L - 1];
     if (d->prec != CBDFS_PREC_FP32 && (d->head == CBDFS_HEAD_CLASSIFIER || d->head == CBDFS_HEAD_QUANTILE) &&
-        C > kMaxHeadC && C <= kHeadTcMaxC && KL % 64 == 0) {
+        C > kHeadTcMinC && C <= kHeadTcMaxC && KL % 64 == 0) {
         const int cpad = (C + 15) / 16 * 16;
         std::vector<uint16_t> sp((size_t)3 * cpad * KL, 0);
         for (int c = 0; c < C; ++c)

@@ -55,8 +55,8 @@ struct ChainParams {
     int trace_tiles;
 };
 
-// the last layer of a classifier network (33..128 outputs) on the tensor cores (head_tc.cu)
-constexpr int kHeadTcMaxC = 128;
+// the last layer of a classifier network (17..128 outputs) on the tensor cores (head_tc.cu)
+constexpr int kHeadTcMinC = 16, kHeadTcMaxC = 128;
 struct HeadTcParams {
     int K;             // input width, a multiple of 64
     int C, cpad;       // outputs, and their padding to a multiple of 16 (<= 128)
