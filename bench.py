@@ -863,12 +863,16 @@ def run_ours(args):
     pin_s = torch.from_numpy(states.view(np.int64)).pin_memory()
     pin_g = torch.from_numpy(g).pin_memory()
     s_np, g_np = pin_s.numpy().view(np.uint64), pin_g.numpy()
+    # the results land in page-locked arrays too, so the kernels read and write in place
+    pin_h = torch.empty(B, dtype=torch.uint8).pin_memory().numpy()
+    pin_m = torch.empty((B + 31) // 32, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
     Ke = max(10, min(args.steps, 500))
     for _ in range(3):
-        P.heur_submit_batch(ctx, hid, P.DOM_STP4, s_np, g_np, BOUND)
+        P.heur_submit_batch(ctx, hid, P.DOM_STP4, s_np, g_np, BOUND, out=(pin_h, pin_m))
+    assert np.array_equal(pin_h, h_ref) and np.array_equal(pin_m, mask_ref)
     t0 = time.perf_counter()
     for _ in range(Ke):
-        P.heur_submit_batch(ctx, hid, P.DOM_STP4, s_np, g_np, BOUND)
+        P.heur_submit_batch(ctx, hid, P.DOM_STP4, s_np, g_np, BOUND, out=(pin_h, pin_m))
     e2e = B * Ke / (time.perf_counter() - t0)
     if dist:
         t = torch.tensor([e2e], device=dev, dtype=torch.float64)

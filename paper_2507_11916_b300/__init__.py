@@ -287,13 +287,21 @@ def pdb_build(ctx, domain, tiles) -> np.ndarray:
     return table[:entries.value]
 
 
-def heur_submit_batch(ctx, heur_id, domain, states, g, bound, want_y=False, n_out=1):
-    """Host arrays in, host arrays out: (h uint8[n], mask uint32[ceil(n/32)], minf[, y])."""
+def heur_submit_batch(ctx, heur_id, domain, states, g, bound, want_y=False, n_out=1, out=None):
+    """Host arrays in, host arrays out: (h uint8[n], mask uint32[ceil(n/32)], minf[, y]).
+    out=(h, mask): caller-owned output arrays (contiguous uint8[n], uint32[ceil(n/32)]); with
+    page-locked states, g, h and mask the kernels read and write them in place."""
     states = np.ascontiguousarray(states, dtype=np.uint64)
     g = np.ascontiguousarray(g, dtype=np.uint8)
     n = len(g)
-    h = np.empty(n, dtype=np.uint8)
-    mask = np.empty((n + 31) // 32, dtype=np.uint32)
+    if out is not None:
+        h, mask = out
+        if h.dtype != np.uint8 or mask.dtype != np.uint32 or len(h) < n or len(mask) < (n + 31) // 32 \
+                or not (h.flags.c_contiguous and mask.flags.c_contiguous):
+            raise ValueError("out: contiguous uint8[n] and uint32[ceil(n/32)] arrays")
+    else:
+        h = np.empty(n, dtype=np.uint8)
+        mask = np.empty((n + 31) // 32, dtype=np.uint32)
     minf = np.empty(1, dtype=np.uint32)
     y = np.empty((n, n_out), dtype=np.float32) if want_y else None
     _check(_lib.heur_submit_batch(ctx, heur_id, domain, _ptr(states), _ptr(g), bound, n,

@@ -328,3 +328,31 @@ def test_c3_chain_matches_per_layer_kernels(P, ctx, orc, prec):
         wm, wf = orc.bound_test(g, h, 70)
         assert np.array_equal(mask.view(np.uint32), wm) and (minf & 0xFFFFFFFF) == wf
     assert P.cbdfs_device_status(ctx) == 0
+
+
+def test_page_locked_buffers_read_and_written_in_place(P, ctx, orc):
+    # the host-buffer call with page-locked states, g, h and mask (the kernels read and write
+    # them over the bus) gives what the staged call gives, for a network and for the cube
+    import torch
+    Ws, bs = W.net_weights(**W.NET_C1)
+    hid = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, PREC["bf16"], P.HEAD_REGRESSION, 1)
+    for n in (1, 1000, 8192):
+        s = W.random_stp_states(4, n, 6600 + n)
+        g = _g(n, 6700 + n, 60)
+        want = P.heur_submit_batch(ctx, hid, P.DOM_STP4, s, g, 50)
+        ps = torch.from_numpy(s.view(np.int64)).pin_memory().numpy().view(np.uint64)
+        pg = torch.from_numpy(g).pin_memory().numpy()
+        ph = torch.zeros(n, dtype=torch.uint8).pin_memory().numpy()
+        pm = torch.zeros((n + 31) // 32, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+        h, mask, minf = P.heur_submit_batch(ctx, hid, P.DOM_STP4, ps, pg, 50, out=(ph, pm))
+        assert h is ph and np.array_equal(ph, want[0]) and np.array_equal(pm, want[1]) and minf == want[2]
+    pids = P.cbdfs_pdb_load(ctx, P.DOM_RC3, [list(range(8))])
+    rs = W.random_rc_states(500, 6800).reshape(-1)
+    rg = _g(500, 6801, 14)
+    want = P.heur_submit_batch(ctx, pids, P.DOM_RC3, rs, rg, 12)
+    prs = torch.from_numpy(rs.view(np.int64)).pin_memory().numpy().view(np.uint64)
+    ph = torch.zeros(500, dtype=torch.uint8).pin_memory().numpy()
+    pm = torch.zeros(16, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+    h, mask, minf = P.heur_submit_batch(ctx, pids, P.DOM_RC3, prs, torch.from_numpy(rg).pin_memory().numpy(), 12,
+                                        out=(ph, pm))
+    assert np.array_equal(ph, want[0]) and np.array_equal(pm, want[1]) and minf == want[2]
