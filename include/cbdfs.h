@@ -62,6 +62,8 @@ typedef enum { CBDFS_ALGO_IDA = 0, CBDFS_ALGO_BTS = 1 } cbdfs_algo;
 #define CBDFS_HEUR_NONE (-100)  /* "no heuristic" (cbdfs_search_cfg.fixed_tree_heur: off) */
 
 typedef struct cbdfs_ctx cbdfs_ctx;
+/* identifies an asynchronous batch (heur_submit_batch_async) or a served request */
+typedef struct { uint64_t id; } cbdfs_ticket;
 
 typedef struct {
     int device;             /* CUDA device ordinal */
@@ -225,6 +227,22 @@ int heur_eval_device(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_
                      const uint8_t *d_g, uint32_t bound, uint32_t n, uint8_t *d_h,
                      uint32_t *d_mask, uint32_t *d_minf, float *d_y, void *stream);
 
+/* Asynchronous form (no y_out): holds a free slot, enqueues the batch on its stream and returns
+ * with *t at once; the results are in h_out, mask_out and minf_out when heur_wait(t) has
+ * returned CBDFS_OK, and no buffer may change before.  Fully asynchronous when the buffers are
+ * page-locked (the kernels then read and write them in place); pageable ones are copied, and a
+ * copy to pageable memory waits for the batch.  Each batch holds one of the context's host
+ * slots until it is waited on: a submit that finds none free blocks until another thread's
+ * wait releases one.  Thread-safe.  Errors: those of heur_submit_batch. */
+int heur_submit_batch_async(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *states,
+                            const uint8_t *g, uint32_t bound, uint32_t n, uint8_t *h_out,
+                            uint32_t *mask_out, uint32_t *minf_out, cbdfs_ticket *t);
+
+/* Wait up to timeout_us (0: without limit) for an asynchronous batch.  CBDFS_ETIMEDOUT if it is
+ * still running (the ticket stays valid); otherwise the batch's status, and the ticket and its
+ * slot are released.  EINVAL for an unknown or collected ticket. */
+int heur_wait(cbdfs_ctx *ctx, cbdfs_ticket t, uint64_t timeout_us);
+
 /* Real-valued heuristic (a network loaded with CBDFS_HEAD_REAL), host buffers: the bound
  * test with f = g + h in FP32 (Algorithm 3's expansion test with real f-costs).
  *   bound    a finite or infinite FP32 bound >= 0 (negative or NaN: EINVAL)
@@ -300,7 +318,6 @@ int cbdfs_device_status(cbdfs_ctx *ctx);
  * alone (rows are independent); its mask and least f above its own bound are formed at
  * completion.  Caller buffers must stay valid until heur_request_wait returns.
  * ------------------------------------------------------------------------------------- */
-typedef struct { uint64_t id; } cbdfs_ticket;
 
 typedef struct {
     int max_inflight;       /* launches on the device at once (slots taken); 0 = all free slots */

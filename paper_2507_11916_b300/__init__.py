@@ -144,6 +144,9 @@ _lib.heur_submit_batch.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ct
                                    ctypes.c_uint32, _vp, _vp, _vp, _vp]
 _lib.heur_eval_device.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint32,
                                   ctypes.c_uint32, _vp, _vp, _vp, _vp, _vp]
+_lib.heur_submit_batch_async.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_uint32,
+                                         ctypes.c_uint32, _vp, _vp, _vp, ctypes.POINTER(Ticket)]
+_lib.heur_wait.argtypes = [_vp, Ticket, ctypes.c_uint64]
 _lib.heur_submit_batch_real.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_float,
                                         ctypes.c_uint32, _vp, _vp, _vp]
 _lib.heur_eval_device_real.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_float,
@@ -186,6 +189,7 @@ _lib.cbdfs_cancel.restype = None
 EXPORTED = ["cbdfs_create", "cbdfs_destroy", "cbdfs_last_error", "cbdfs_mem_used", "cbdfs_net_load",
             "cbdfs_pdb_load", "cbdfs_combo_load", "pdb_build", "heur_submit_batch", "heur_eval_device",
             "heur_submit_batch_real", "heur_eval_device_real", "heur_eval_device_static",
+            "heur_submit_batch_async", "heur_wait",
             "cbdfs_device_status", "cbdfs_eval_profile", "cbdfs_eval_trace", "net_train",
             "cbdfs_train_grad", "cbdfs_net_read", "cbdfs_gen_walk_states", "cbdfs_server_start",
             "cbdfs_server_stop", "heur_request_submit", "heur_request_wait", "cbdfs_server_get_stats", "cbdfs_apply_moves", "cbdfs_manhattan", "cbdfs_solve",
@@ -307,6 +311,36 @@ def heur_submit_batch(ctx, heur_id, domain, states, g, bound, want_y=False, n_ou
     _check(_lib.heur_submit_batch(ctx, heur_id, domain, _ptr(states), _ptr(g), bound, n,
                                   _ptr(h), _ptr(mask), _ptr(minf), _ptr(y)))
     return (h, mask, int(minf[0]), y) if want_y else (h, mask, int(minf[0]))
+
+
+class AsyncBatch:
+    """An asynchronous batch: wait() returns (h, mask, minf) once the results are in."""
+
+    def __init__(self, ctx, ticket, keep, h, mask, minf):
+        self.ctx, self.ticket, self._keep = ctx, ticket, keep
+        self.h, self.mask, self._minf = h, mask, minf
+
+    def wait(self, timeout_us=0):
+        _check(_lib.heur_wait(self.ctx, self.ticket, timeout_us))
+        return self.h, self.mask, int(self._minf[0])
+
+
+def heur_submit_batch_async(ctx, heur_id, domain, states, g, bound, out=None) -> AsyncBatch:
+    """heur_submit_batch without waiting: the arrays (and out=(h, mask), caller-owned) are kept
+    alive by the returned object until its wait()."""
+    states = np.ascontiguousarray(states, dtype=np.uint64)
+    g = np.ascontiguousarray(g, dtype=np.uint8)
+    n = len(g)
+    if out is not None:
+        h, mask = out
+    else:
+        h = np.empty(n, dtype=np.uint8)
+        mask = np.empty((n + 31) // 32, dtype=np.uint32)
+    minf = np.empty(1, dtype=np.uint32)
+    t = Ticket()
+    _check(_lib.heur_submit_batch_async(ctx, heur_id, domain, _ptr(states), _ptr(g), bound, n, _ptr(h),
+                                        _ptr(mask), _ptr(minf), ctypes.byref(t)))
+    return AsyncBatch(ctx, t, (states, g), h, mask, minf)
 
 
 def heur_submit_batch_real(ctx, heur_id, domain, states, g, bound):

@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <chrono>
 #include <cstring>
+#include <thread>
 
 #include "chain.h"
 
@@ -1001,9 +1003,11 @@ static bool host_mapped(const void *p, void **dev) {
 // One host-buffer batch on a free slot (slots 1..).  h8: uint8 h (null for a real-valued
 // head); yf: C floats per row (the raw outputs, or for a real-valued head its h, C = 1), or
 // null.  *minf_key receives the least f above the bound as the kernels' key.
+// ticket_out != null: return once the batch is enqueued (the slot stays held; heur_wait finishes
+// the call and releases it)
 static int submit_host(Ctx *c, int heur_id, int domain, const uint64_t *states, const uint8_t *g,
                        uint32_t bound, uint32_t n, uint8_t *h8, uint32_t *mask_out, uint32_t *minf_key,
-                       float *yf, int C) {
+                       float *yf, int C, uint64_t *ticket_out = nullptr) {
     CUDA_TRY(cudaSetDevice(c->device));
     int si;
     {
@@ -1054,6 +1058,16 @@ static int submit_host(Ctx *c, int heur_id, int domain, const uint64_t *states, 
     if (!rc && (cudaMemcpyAsync(s.h_small, s.d_minf, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                 cudaMemcpyAsync(s.h_small + 1, c->d_err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess))
         rc = fail(CBDFS_EDEVICE, "result download");
+    if (ticket_out && !rc && !d_y) {
+        if (cudaEventRecord(s.done, st) != cudaSuccess) {
+            rc = fail(CBDFS_EDEVICE, "event record");
+        } else {
+            std::lock_guard<std::mutex> lk(c->pending_mu);
+            *ticket_out = c->next_ticket++;
+            c->pending[*ticket_out] = Ctx::Pending{si, minf_key};
+            return CBDFS_OK;
+        }
+    }
     cudaError_t e = cudaStreamSynchronize(st);
     if (!rc && e != cudaSuccess) rc = fail(CBDFS_EDEVICE, "evaluation: %s", cudaGetErrorString(e));
     if (d_y) dev_free(c, d_y, (size_t)n * C * 4 + 4);
@@ -1082,6 +1096,55 @@ int heur_submit_batch(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *s
         C = net.dims[net.L];
     }
     return submit_host(c, heur_id, domain, states, g, bound, n, h_out, mask_out, minf_out, C ? y_out : nullptr, C);
+}
+
+int heur_submit_batch_async(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *states, const uint8_t *g,
+                            uint32_t bound, uint32_t n, uint8_t *h_out, uint32_t *mask_out, uint32_t *minf_out,
+                            cbdfs_ticket *t) {
+    if (!ctx || !minf_out || !t || (n && (!states || !g || !h_out || !mask_out))) return fail(CBDFS_EINVAL, "null argument");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    int rc = check_eval_args(c, heur_id, domain, n);
+    if (rc) return rc;
+    uint64_t id = 0;
+    rc = submit_host(c, heur_id, domain, states, g, bound, n, h_out, mask_out, minf_out, nullptr, 0, &id);
+    t->id = id;
+    return rc;
+}
+
+int heur_wait(cbdfs_ctx *ctx, cbdfs_ticket t, uint64_t timeout_us) {
+    if (!ctx) return fail(CBDFS_EINVAL, "null argument");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    Ctx::Pending p;
+    {
+        std::lock_guard<std::mutex> lk(c->pending_mu);
+        auto it = c->pending.find(t.id);
+        if (it == c->pending.end()) return fail(CBDFS_EINVAL, "unknown or collected ticket %llu", (unsigned long long)t.id);
+        p = it->second;
+    }
+    CUDA_TRY(cudaSetDevice(c->device));
+    Slot &s = c->slots[p.slot];
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaError_t q;
+    while ((q = cudaEventQuery(s.done)) == cudaErrorNotReady) {
+        if (timeout_us && std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(timeout_us))
+            return fail(CBDFS_ETIMEDOUT, "ticket %llu still running", (unsigned long long)t.id);
+        std::this_thread::yield();
+    }
+    int rc = q == cudaSuccess ? CBDFS_OK : fail(CBDFS_EDEVICE, "evaluation: %s", cudaGetErrorString(q));
+    if (!rc) {
+        *p.minf_out = s.h_small[0];
+        if (s.h_small[1]) rc = fail(CBDFS_ETIMEDOUT, "a device wait ran out (code %d)", (int)s.h_small[1]);
+    }
+    {
+        std::lock_guard<std::mutex> lk(c->pending_mu);
+        c->pending.erase(t.id);
+    }
+    {
+        std::lock_guard<std::mutex> lk(c->slot_mu);
+        s.busy = false;
+    }
+    c->slot_cv.notify_one();
+    return rc;
 }
 
 int heur_submit_batch_real(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *states, const uint8_t *g,

@@ -166,6 +166,14 @@ struct Ctx {
     size_t partial_floats = 0;         // per-row head partials the chain scratch holds
     int num_sms = 0;
     uint64_t buf_gen = 0;              // bumped whenever slot scratch moves (captured graphs hold its pointers)
+    // heur_submit_batch_async: tickets of batches still holding their slot
+    struct Pending {
+        int slot;
+        uint32_t *minf_out;
+    };
+    std::mutex pending_mu;
+    std::map<uint64_t, Pending> pending;
+    uint64_t next_ticket = 1;
     Server *server = nullptr;
 };
 

@@ -356,3 +356,34 @@ def test_page_locked_buffers_read_and_written_in_place(P, ctx, orc):
     h, mask, minf = P.heur_submit_batch(ctx, pids, P.DOM_RC3, prs, torch.from_numpy(rg).pin_memory().numpy(), 12,
                                         out=(ph, pm))
     assert np.array_equal(ph, want[0]) and np.array_equal(pm, want[1]) and minf == want[2]
+
+
+def test_async_batches_and_wait(P, orc):
+    # three batches in flight on three host slots, waited on in reverse order; each is what the
+    # synchronous call gives.  A collected ticket is unknown afterwards.
+    import torch
+    ctx = P.cbdfs_create(0, max_batch=8192, n_slots=4)
+    try:
+        Ws, bs = W.net_weights(**W.NET_C1)
+        hid = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, PREC["bf16"], P.HEAD_REGRESSION, 1)
+        jobs = []
+        for k, (heur, n) in enumerate(((hid, 8192), (P.HEUR_MD, 3000), (hid, 129))):
+            s = W.random_stp_states(4, n, 7100 + k)
+            g = _g(n, 7200 + k, 60)
+            want = P.heur_submit_batch(ctx, heur, P.DOM_STP4, s, g, 50)
+            ps = torch.from_numpy(s.view(np.int64)).pin_memory().numpy().view(np.uint64)
+            pg = torch.from_numpy(g).pin_memory().numpy()
+            out = (torch.zeros(n, dtype=torch.uint8).pin_memory().numpy(),
+                   torch.zeros((n + 31) // 32, dtype=torch.int32).pin_memory().numpy().view(np.uint32))
+            jobs.append((P.heur_submit_batch_async(ctx, heur, P.DOM_STP4, ps, pg, 50, out=out), want))
+        for job, want in reversed(jobs):
+            try:
+                h, mask, minf = job.wait(timeout_us=1)   # may still be running: the ticket stays
+            except P.CbdfsError as e:
+                assert e.status == P.CBDFS_ETIMEDOUT
+                h, mask, minf = job.wait()
+            assert np.array_equal(h, want[0]) and np.array_equal(mask, want[1]) and minf == want[2]
+        with pytest.raises(P.CbdfsError):
+            jobs[0][0].wait()
+    finally:
+        P.cbdfs_destroy(ctx)
