@@ -174,9 +174,12 @@ int pdb_build(cbdfs_ctx *ctx, int domain, const int *pattern_tiles, int k, uint8
  *   h = [MD if add_md] + sum over groups g of (min over the members of g of h_member),
  * clamped to 255; the goal gets 0.  Members are loaded heuristic ids (networks with integer
  * heads, PDBs, CBDFS_HEUR_MD / _ZERO) of the same domain: at most 4 groups of 1..8 members,
- * 16 members in all.  Every member runs its own pipeline on the batch, then one kernel
- * combines them and applies the bound test.  Not on the allocation-free entry
- * (heur_eval_device_static).
+ * 16 members in all.  A group of two or more BF16 networks of one shape whose head runs on
+ * the tensor cores (classifier or quantile, 17..128 outputs) is evaluated as one grouped
+ * network (the ensemble as a grouped GEMM: one fused launch for the hidden layers, one for the
+ * heads); the load copies those members' weights, so train members before combining them.
+ * Other members run their own pipelines one after another; then one kernel combines them and
+ * applies the bound test.  Not on the allocation-free entry (heur_eval_device_static).
  * ------------------------------------------------------------------------------------- */
 typedef struct {
     int domain;

@@ -47,6 +47,16 @@ uint64_t npk(int n, int k);
 // ints of a slot's chain counters: (layers + 2) per row block, and the finished-CTA count
 static int chain_counter_ints(const Ctx *c) { return (kMaxLayers + 2) * (c->max_batch_pad / kBM) + 1; }
 
+// a network's device buffers (at context teardown)
+static void free_net_buffers(NetGPU &n) {
+    for (int l = 0; l < kMaxLayers; ++l) {
+        if (n.w_lp[l]) cudaFree(n.w_lp[l]);
+        if (n.w32[l]) cudaFree(n.w32[l]);
+        if (n.b32[l]) cudaFree(n.b32[l]);
+    }
+    if (n.w_split) cudaFree(n.w_split);
+}
+
 static bool chain_ok(const NetGPU &net) {
     if (net.prec == CBDFS_PREC_FP32) return false;
     for (int l = 1; l < net.L; ++l)
@@ -333,8 +343,9 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
         } else {
             maps.o[l] = net.tm_w[0];  // unused
         }
-        P.kdim[l] = l == 0 ? net.k1pad : net.dims[l];
+        P.kdim[l] = l == 0 ? net.k1pad : net.dims[l] / net.groups;
         P.nt[l] = net.dims[l + 1] / bn;
+        P.group_nt[l] = l > 0 && net.groups > 1 ? P.nt[l] / net.groups : 0;
         P.tile_start[l + 1] = P.tile_start[l] + P.nt[l] * P.mblocks;
         max_tiles = std::max(max_tiles, P.nt[l] * P.mblocks);
         P.bias[l] = net.b32[l];
@@ -376,7 +387,9 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
         const CUtensorMap *ma = act_map(s, c, (nh - 1) & 1, net.dims[nh], 2);
         if (!ma) return CBDFS_EDEVICE;
         HeadTcParams H{};
-        H.K = net.dims[nh];
+        H.K = net.dims[nh] / net.groups;
+        H.groups = net.groups;
+        H.h_stride = c->max_batch_pad;
         H.C = net.dims[L];
         H.cpad = net.head_cpad;
         H.head_kind = net.head;
@@ -423,10 +436,18 @@ int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
         const size_t stride = c->max_batch_pad;
         uint32_t *mmask = reinterpret_cast<uint32_t *>(s.combo + (size_t)kComboMaxTotal * stride);
         uint32_t *mminf = mmask + stride / 32;
-        for (size_t m = 0; m < cb.members.size(); ++m) {
-            int r = run_eval(c, s, cb.members[m], domain, d_states, d_g, 255, n, s.combo + m * stride, mmask, mminf,
-                             nullptr, st);
-            if (r) return r;
+        for (int grp = 0, m = 0; grp < cb.P.n_groups; m += cb.P.group_size[grp++]) {
+            if (cb.fused[grp]) {  // the group's networks as one grouped network: h rows m, m+1, ...
+                int r = run_chain(c, s, *cb.fused[grp], domain, d_states, d_g, 255, n, s.combo + (size_t)m * stride,
+                                  mmask, mminf, nullptr, st);
+                if (r) return r;
+                continue;
+            }
+            for (int j = 0; j < cb.P.group_size[grp]; ++j) {
+                int r = run_eval(c, s, cb.members[m + j], domain, d_states, d_g, 255, n, s.combo + (size_t)(m + j) * stride,
+                                 mmask, mminf, nullptr, st);
+                if (r) return r;
+            }
         }
         int r = combine(domain, cb.P, d_states, n, s.combo, stride, d_g, bound, d_h, d_mask, d_minf, st);
         return r ? r : mark(s, st);
@@ -552,6 +573,9 @@ void cbdfs_destroy(cbdfs_ctx *ctx) {
     for (auto &p : c->pdbs)
         for (int q = 0; q < 4; ++q)
             if (p->table[q]) cudaFree(p->table[q]);
+    for (auto &cb : c->combos)
+        for (auto &f : cb->fused)
+            if (f) free_net_buffers(*f);
     if (c->d_err) cudaFree(c->d_err);
     delete c;
 }
@@ -839,6 +863,69 @@ int cbdfs_pdb_load(cbdfs_ctx *ctx, const cbdfs_pdb_desc *d, int *heur_id) {
     return CBDFS_OK;
 }
 
+// A group's networks as one grouped network, when they are two or more BF16 networks of one
+// shape with the tensor-core head: weights and biases stacked by member (device copies).
+// Returns with *out null when the group does not qualify.
+static int fuse_group(Ctx *c, const int *ids, int k, std::unique_ptr<NetGPU> *out) {
+    out->reset();
+    if (k < 2) return CBDFS_OK;
+    for (int j = 0; j < k; ++j)
+        if (ids[j] < 0 || c->heur_kind[ids[j]] != 0) return CBDFS_OK;
+    const NetGPU &a = *c->nets[c->heur_index[ids[0]]];
+    if (a.prec != CBDFS_PREC_BF16 || !a.head_cpad || !chain_ok(a)) return CBDFS_OK;
+    for (int j = 1; j < k; ++j) {
+        const NetGPU &b = *c->nets[c->heur_index[ids[j]]];
+        if (b.domain != a.domain || b.L != a.L || b.prec != a.prec || b.head != a.head || b.quantile != a.quantile ||
+            b.max_with_md != a.max_with_md || b.head_cpad != a.head_cpad || b.k1pad != a.k1pad)
+            return CBDFS_OK;
+        for (int l = 0; l <= a.L; ++l)
+            if (b.dims[l] != a.dims[l]) return CBDFS_OK;
+    }
+    auto f = std::make_unique<NetGPU>();
+    NetGPU &F = *f;
+    const int L = a.L, E = k;
+    F.domain = a.domain; F.L = L; F.prec = a.prec; F.head = a.head; F.quantile = a.quantile;
+    F.max_with_md = a.max_with_md; F.k1pad = a.k1pad; F.head_cpad = a.head_cpad; F.groups = E;
+    F.dims[0] = a.dims[0];
+    for (int l = 1; l < L; ++l) F.dims[l] = E * a.dims[l];
+    F.dims[L] = a.dims[L];
+    auto stack = [&](void **dst, size_t each, auto member_ptr) -> int {
+        int rc = dev_alloc(c, dst, each * E);
+        if (rc) return rc;
+        F.bytes += each * E;
+        for (int j = 0; j < E; ++j)
+            CUDA_TRY(cudaMemcpy(static_cast<uint8_t *>(*dst) + each * j, member_ptr(*c->nets[c->heur_index[ids[j]]]),
+                                each, cudaMemcpyDeviceToDevice));
+        return CBDFS_OK;
+    };
+    int rc;
+    size_t maxw = 0;
+    for (int l = 0; l < L - 1; ++l) {
+        const int O = a.dims[l + 1], Kp = l == 0 ? a.k1pad : a.dims[l];
+        if ((rc = stack(&F.w_lp[l], (size_t)O * Kp * 2, [&](const NetGPU &n) { return n.w_lp[l]; }))) return rc;
+        if ((rc = stack((void **)&F.b32[l], (size_t)O * 4, [&](const NetGPU &n) { return (const void *)n.b32[l]; })))
+            return rc;
+        F.w_scale[l] = F.a_scale[l] = 1.f;
+        F.bn[l] = a.bn[l];
+        if ((rc = make_tmap_2d(&F.tm_w[l], F.w_lp[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (uint64_t)Kp, (uint64_t)E * O,
+                               64, F.bn[l])) ||
+            (rc = make_tmap_2d(&F.tm_w64[l], F.w_lp[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (uint64_t)Kp,
+                               (uint64_t)E * O, 64, kChainBNSmall)))
+            return rc;
+        maxw = std::max(maxw, (size_t)E * O);
+    }
+    const int C = a.dims[L], KL = a.dims[L - 1], cpad = a.head_cpad;
+    if ((rc = stack(&F.w_split, (size_t)3 * cpad * KL * 2, [&](const NetGPU &n) { return (const void *)n.w_split; })) ||
+        (rc = stack((void **)&F.b32[L - 1], (size_t)C * 4, [&](const NetGPU &n) { return (const void *)n.b32[L - 1]; })))
+        return rc;
+    if ((rc = make_tmap_2d(&F.tm_wsplit, F.w_split, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (uint64_t)KL,
+                           (uint64_t)E * 3 * cpad, 64, cpad)))
+        return rc;
+    if ((rc = ensure_act(c, maxw)) || (rc = ensure_chain(c, 0))) return rc;
+    *out = std::move(f);
+    return CBDFS_OK;
+}
+
 int cbdfs_combo_load(cbdfs_ctx *ctx, const cbdfs_combo_desc *d, int *heur_id) {
     if (!ctx || !d || !heur_id || !d->group_size || !d->members) return fail(CBDFS_EINVAL, "null argument");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
@@ -872,6 +959,10 @@ int cbdfs_combo_load(cbdfs_ctx *ctx, const cbdfs_combo_desc *d, int *heur_id) {
         if (total > kComboMaxTotal) return fail(CBDFS_EINVAL, "more than %d members", kComboMaxTotal);
     }
     CUDA_TRY(cudaSetDevice(c->device));
+    for (int grp = 0, m = 0; grp < cb->P.n_groups; m += cb->P.group_size[grp++]) {
+        int rc = fuse_group(c, cb->members.data() + m, cb->P.group_size[grp], &cb->fused[grp]);
+        if (rc) return rc;
+    }
     for (auto &s : c->slots)
         if (!s.combo) {
             int rc = dev_alloc(c, (void **)&s.combo, combo_bytes(c));

@@ -20,7 +20,10 @@ struct ChainMaps {
 struct ChainParams {
     int nh;                        // hidden layers (tensor-core layers) = L-1
     int dims[kMaxLayers + 1];
-    int kdim[kMaxLayers];          // K of hidden layer l (layer 0: padded one-hot width)
+    int kdim[kMaxLayers];          // K of hidden layer l (layer 0: padded one-hot width; a
+                                   // grouped layer: one member's K)
+    int group_nt[kMaxLayers];      // grouped layer (an ensemble run as one network): n-tiles per
+                                   // member, whose A is its own K-column block; 0: dense
     int nt[kMaxLayers];            // n-tiles of hidden layer l
     int tile_start[kMaxLayers + 1];
     int mblocks;
@@ -72,6 +75,10 @@ struct HeadTcParams {
     uint32_t *mask, *minf;
     float *y;          // optional [n][C] logits
     int *err;
+    // an ensemble run as one network: member e (blockIdx.y) reads A columns [e K, e K + K) and
+    // weight rows from e 3 cpad, writes h to h + e h_stride; no mask or minf then (0: one network)
+    int groups;
+    size_t h_stride;
 };
 
 int head_tc(int domain, const CUtensorMap &tmA, const CUtensorMap &tmW, const HeadTcParams &P, uint32_t rows_pad,

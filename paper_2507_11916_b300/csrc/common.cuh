@@ -73,6 +73,10 @@ struct NetGPU {
     void *w_split = nullptr;
     CUtensorMap tm_wsplit;
     int head_cpad = 0;
+    // an ensemble run as one network (composite heuristics): `groups` members stacked along
+    // every hidden width, each hidden layer after the first grouped (a member reads only its
+    // own columns); dims[1..L-1] are the stacked widths, dims[L] one member's outputs
+    int groups = 1;
     // FP32 weights for every layer (the FP32 path; the last layer for every path)
     float *w32[kMaxLayers] = {};
     float *b32[kMaxLayers] = {};
@@ -113,6 +117,8 @@ struct ComboGPU {
     int domain = 0;
     ComboParams P{};
     std::vector<int> members;          // heuristic ids, group by group
+    // per group: its networks run as one grouped network (null: the members one by one)
+    std::unique_ptr<NetGPU> fused[kComboMaxGroups];
 };
 
 // one evaluation slot: a stream plus the scratch a batch needs

@@ -41,6 +41,10 @@ k_head_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t m0 = blockIdx.x * kBM;
     const int KB = P.K / 64;
+    const int e = blockIdx.y;                 // ensemble member (0 for one network)
+    const int ax0 = e * P.K, wy0 = e * 3 * P.cpad;
+    const float *b_last = P.b_last + e * P.C;
+    uint8_t *h_out = P.h + e * P.h_stride;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kHtStages; ++s) {
             mbar_init(smem_u32(&full[s]), 1);
@@ -53,7 +57,7 @@ k_head_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         tmem_alloc(smem_u32(tmem_slot), tmem_cols);
         tmem_relinquish();
     }
-    for (int c = threadIdx.x; c < 128; c += kHtThreads) bsm[c] = c < P.C ? __ldg(P.b_last + c) : 0.f;
+    for (int c = threadIdx.x; c < 128; c += kHtThreads) bsm[c] = c < P.C ? __ldg(b_last + c) : 0.f;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -67,10 +71,10 @@ k_head_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 if (kb >= kHtStages && !mbar_wait(smem_u32(&empty[s]), (u - 1) & 1, P.err, DEVERR_STAGE_EMPTY)) break;
                 uint8_t *A = smem + s * stage;
                 mbar_arrive_expect_tx(smem_u32(&full[s]), stage);
-                tma_load_2d(smem_u32(A), &tmA, smem_u32(&full[s]), kb * 64, m0);
+                tma_load_2d(smem_u32(A), &tmA, smem_u32(&full[s]), ax0 + kb * 64, m0);
                 for (int sp = 0; sp < 3; ++sp)
                     tma_load_2d(smem_u32(A + kHtStageA + sp * P.cpad * 128), &tmW, smem_u32(&full[s]), kb * 64,
-                                sp * P.cpad);
+                                wy0 + sp * P.cpad);
                 ++issued;
             }
             // every load issued has landed before the CTA can exit (bounded)
@@ -117,7 +121,7 @@ k_head_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 const int c = ch * 32 + j;
                 if (c < P.C) {
                     const float v = head_logit(r, j, bsm, c);
-                    if (P.y && valid) P.y[(size_t)m * P.C + c] = v;
+                    if (P.y && valid && P.groups <= 1) P.y[(size_t)m * P.C + c] = v;
                     if (v > best) { best = v; bi = c; }
                     mx = fmaxf(mx, v);
                 }
@@ -170,14 +174,14 @@ k_head_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 goal = stp_is_goal<SIDE>(s);
             }
             hv = goal ? 0 : min(max(hv, md), 255);
-            P.h[m] = (uint8_t)hv;
+            h_out[m] = (uint8_t)hv;
             f = (uint32_t)P.g[m] + (uint32_t)hv;
             pass = f <= P.bound;
         }
         const uint32_t bits = __ballot_sync(0xFFFFFFFFu, pass);
         const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, pass ? 0xFFFFFFFFu : f);
         const uint32_t word = (m0 >> 5) + q;
-        if (lane == 0 && word < (P.n + 31) / 32) {
+        if (lane == 0 && P.groups <= 1 && word < (P.n + 31) / 32) {
             P.mask[word] = bits;
             if (mn != 0xFFFFFFFFu) atomicMin(P.minf, mn);
         }
@@ -197,7 +201,7 @@ int launch(const CUtensorMap &tmA, const CUtensorMap &tmW, const HeadTcParams &P
     CUDA_TRY(cudaFuncSetAttribute(k_head_tc<DOMAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     uint32_t cols = 32;
     while ((int)cols < P.cpad) cols <<= 1;
-    k_head_tc<DOMAIN><<<rows_pad / kBM, kHtThreads, smem, st>>>(tmA, tmW, P, cols);
+    k_head_tc<DOMAIN><<<dim3(rows_pad / kBM, P.groups > 1 ? P.groups : 1), kHtThreads, smem, st>>>(tmA, tmW, P, cols);
     CUDA_TRY(cudaGetLastError());
     return CBDFS_OK;
 }

@@ -314,6 +314,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
         for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++pi) {
             const Tile T = tile_of(P, t);
             const int KB = P.kdim[T.l] / KBLK;
+            const int kb0 = P.group_nt[T.l] ? (T.n / P.group_nt[T.l]) * KB : 0;  // member's K block
             if (lane == 0) stamp(P, pi, 0);
             // layer 0 reads the one-hot rows (16 units of 8 rows), layer l the stored tiles of
             // layer l-1 (4 warps per tile)
@@ -335,7 +336,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                 }
                 if (lane == 0) {
                     mbar_arrive_expect_tx(smem_u32(&full[s]), kStageA + kStageB);
-                    tma_load_2d(smem_u32(A + s * kStageA), &maps.a[T.l], smem_u32(&full[s]), kb * KBLK,
+                    tma_load_2d(smem_u32(A + s * kStageA), &maps.a[T.l], smem_u32(&full[s]), (kb + kb0) * KBLK,
                                 T.m * kBM);
                     tma_load_2d(smem_u32(B + s * kStageB), &maps.w[T.l], smem_u32(&full[s]), kb * KBLK,
                                 T.n * BN);

@@ -199,3 +199,23 @@ def test_tensor_core_head_is_fp32_accurate(P, ctx, orc, C):
     assert err.max() < 2e-6, err.max()
     want = orc.h_classifier(y.astype(np.float64), None, orc.is_goal_states(orc.DOM_STP4, s))
     assert np.array_equal(h, np.minimum(want, 255))
+
+
+def test_grouped_ensemble_equals_its_members(P, ctx, orc):
+    # four 81-class quantile networks of one shape in one group: run as one grouped network
+    # (stacked first layer, grouped hidden layers, grouped tensor-core heads), the minimum must
+    # be exactly the minimum of the members evaluated one by one
+    ids = []
+    for seed in (51, 52, 53, 54):
+        Wq, bq = W.net_weights(dims=[256, 1024, 1024, 512, 81], init="kaiming", seed=seed)
+        ids.append(P.cbdfs_net_load(ctx, P.DOM_STP4, Wq, bq, PREC["bf16"], P.HEAD_QUANTILE, 0, quantile=0.1))
+    cid = P.cbdfs_combo_load(ctx, P.DOM_STP4, [ids], add_md=False)
+    for n in (1, 129, 3001, 8192):
+        s = W.random_stp_states(4, n, 1900 + n)
+        g = _g(n, 1950 + n)
+        members = [P.heur_submit_batch(ctx, i, P.DOM_STP4, s, g, 255)[0] for i in ids]
+        h, mask, minf = P.heur_submit_batch(ctx, cid, P.DOM_STP4, s, g, 40)
+        want = orc.h_combo(members, [4], None, orc.is_goal_states(orc.DOM_STP4, s))
+        assert np.array_equal(h, want)
+        wm, wf = orc.bound_test(g, want, 40)
+        assert np.array_equal(mask, wm) and minf == wf
