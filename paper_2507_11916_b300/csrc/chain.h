@@ -71,7 +71,7 @@ struct HeadTcParams {
     const uint8_t *g;
     uint32_t bound;
     const float *b_last;
-    uint8_t *h;
+    uint8_t *h;        // null: only the logits (y), no rule and no bound test
     uint32_t *mask, *minf;
     float *y;          // optional [n][C] logits
     int *err;

@@ -44,7 +44,7 @@ k_head_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const int e = blockIdx.y;                 // ensemble member (0 for one network)
     const int ax0 = e * P.K, wy0 = e * 3 * P.cpad;
     const float *b_last = P.b_last + e * P.C;
-    uint8_t *h_out = P.h + e * P.h_stride;
+    uint8_t *h_out = P.h ? P.h + e * P.h_stride : nullptr;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kHtStages; ++s) {
             mbar_init(smem_u32(&full[s]), 1);
@@ -128,6 +128,7 @@ k_head_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             }
         }
         int hv = bi;
+        if (P.h) {  // (no h: the logits alone, for the training forward)
         if (P.head_kind == CBDFS_HEAD_QUANTILE && good) {
             // the smallest class whose softmax cumulative sum reaches q (quantile_class's order)
             float S = 0.f;
@@ -184,6 +185,7 @@ k_head_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         if (lane == 0 && P.groups <= 1 && word < (P.n + 31) / 32) {
             P.mask[word] = bits;
             if (mn != 0xFFFFFFFFu) atomicMin(P.minf, mn);
+        }
         }
     }
     tc_fence_before();

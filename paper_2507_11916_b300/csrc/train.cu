@@ -23,7 +23,7 @@
 #include <random>
 #include <type_traits>
 
-#include "common.cuh"
+#include "chain.h"
 
 namespace cbdfs {
 
@@ -651,8 +651,26 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
     const int KL = net.dims[L - 1];
     const dim3 blk(256);
     // logits[m][c] = sum_k A[m][k] W[c][k] + b[c]
-    k_fgemm<__nv_bfloat16, float, true, false, 1><<<dim3((C + FG_T - 1) / FG_T, (n + FG_T - 1) / FG_T, 1), blk, 0, st>>>(
-        T.act[L - 2], KL, 1, T.w[L - 1], 1, KL, n, C, KL, KL, T.logits, T.b[L - 1], nullptr, 0, nullptr);
+    if (net.w_split) {
+        // the logits on the tensor cores: the masters' three BF16 parts (re-split after every
+        // update) and biases, as the inference head computes them
+        const CUtensorMap *ma = bmap(T, T.act[L - 2], KL, Bp, kBM);
+        if (!ma) return CBDFS_EDEVICE;
+        HeadTcParams H{};
+        H.K = KL;
+        H.C = C;
+        H.cpad = net.head_cpad;
+        H.head_kind = net.head;
+        H.n = n;
+        H.b_last = net.b32[L - 1];
+        H.y = T.logits;
+        H.err = c->d_err;
+        H.groups = 1;
+        if (int r = head_tc(net.domain, *ma, net.tm_wsplit, H, Bp, st)) return r;
+    } else {
+        k_fgemm<__nv_bfloat16, float, true, false, 1><<<dim3((C + FG_T - 1) / FG_T, (n + FG_T - 1) / FG_T, 1), blk, 0, st>>>(
+            T.act[L - 2], KL, 1, T.w[L - 1], 1, KL, n, C, KL, KL, T.logits, T.b[L - 1], nullptr, 0, nullptr);
+    }
     k_loss<<<(n + 255) / 256, 256, 0, st>>>(T.logits, T.labels, n, C, loss_kind, T.dzl, T.row_loss);
     k_mean<<<1, 256, 0, st>>>(T.row_loss, n, T.loss);
     // last layer backward (FP32): dW[c][k] = sum_m dZ[m][c] A[m][k] in row splits, then the
