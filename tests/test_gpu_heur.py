@@ -387,3 +387,32 @@ def test_async_batches_and_wait(P, orc):
             jobs[0][0].wait()
     finally:
         P.cbdfs_destroy(ctx)
+
+
+@pytest.mark.parametrize("n", [65536, 262144])
+def test_chain_at_the_kernel_micro_sizes_sampled(P, orc, n):
+    # many tiles per CTA (the persistent schedule's later rounds, counters reused across row
+    # blocks): a seeded sample of rows against the oracle, the bound test over every row, in BF16
+    # and E4M3
+    ctx = P.cbdfs_create(0, max_batch=n, n_slots=2)
+    try:
+        Ws, bs = W.net_weights(**W.NET_C1)
+        sc = fp8_act_scales(orc, 1, Ws, bs, W.random_stp_states(4, 4096, 11))
+        s = W.random_stp_states(4, n, 9000 + n)
+        g = _g(n, 9100 + n, 60)
+        idx = np.random.default_rng(n).choice(n, 400, replace=False)
+        for prec in ("bf16", "fp8"):
+            hid = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, PREC[prec], P.HEAD_REGRESSION, 1,
+                                   act_scales=sc if prec == "fp8" else None)
+            h, mask, minf, y = P.heur_submit_batch(ctx, hid, P.DOM_STP4, s, g, 55, want_y=True)
+            y64, h64, margin = oracle_net(orc, 1, Ws, bs, prec, s[idx], "regression", True,
+                                          sc if prec == "fp8" else None)
+            check_logits(y[idx], y64, prec)
+            check_h(h[idx], h64, margin)
+            # every row: h follows the rule on the kernel's own y, and the bound test is exact
+            own = orc.h_regression(y[:, 0], orc.md_states(orc.DOM_STP4, s), orc.is_goal_states(orc.DOM_STP4, s))
+            assert np.array_equal(h, own)
+            _check_bound(orc, h, g, 55, mask, minf)
+        assert P.cbdfs_device_status(ctx) == 0
+    finally:
+        P.cbdfs_destroy(ctx)
