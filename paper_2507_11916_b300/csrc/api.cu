@@ -725,7 +725,7 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
                 return rc;
         }
     }
-    // the tensor-core head: a classifier of 33..128 outputs behind BF16 / E4M3 hidden layers
+    // the tensor-core head: a classifier of 17..128 outputs behind BF16 / E4M3 hidden layers
     // (the fused chain stores the last hidden layer in BF16 for it); W = W1 + W2 + W3 in BF16,
     // each part the rounding of what the previous ones leave (24 bits of mantissa in all)
     const int C = d->dims[L], KL = d->dims[L - 1];

@@ -1,4 +1,4 @@
-// head_tc.cu -- the last layer of a classifier network on the tensor cores (33..128 outputs),
+// head_tc.cu -- the last layer of a classifier network on the tensor cores (17..128 outputs),
 // after the fused chain has stored the last hidden layer in BF16.
 //
 // Y[128 rows][C] = A[128][K] W^T + b.  W (FP32, the last layer) is split on the host into three
