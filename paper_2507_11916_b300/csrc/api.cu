@@ -44,8 +44,9 @@ uint64_t npk(int n, int k);
 
 // the fused chain runs low-precision networks whose hidden widths are multiples of 256; a last
 // layer of at most 32 outputs runs in its epilogue, a wider one in a separate kernel after it
-// ints of a slot's chain counters: (layers + 2) per row block, and the finished-CTA count
-static int chain_counter_ints(const Ctx *c) { return (kMaxLayers + 2) * (c->max_batch_pad / kBM) + 1; }
+// ints of a slot's chain counters: (layers + 2) per row block.  A launch leaves them zero (after a
+// device error, cbdfs_device_status does)
+static int chain_counter_ints(const Ctx *c) { return (kMaxLayers + 2) * (c->max_batch_pad / kBM); }
 
 // a network's device buffers (at context teardown)
 static void free_net_buffers(NetGPU &n) {
@@ -357,6 +358,7 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     P.act[0] = s.act[0];
     P.act[1] = s.act[1];
     P.counters = s.counters;
+    P.unit_rows = net.k1pad * eb <= 512 ? 16 : 8;
     P.partial = s.partial;
     P.C = net.dims[L];
     P.head_kind = net.head;
@@ -378,7 +380,6 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
         *s.trace_grid = grid;
         CUDA_TRY(cudaMemsetAsync(s.trace, 0, sizeof(unsigned long long) * grid * s.trace_tiles * 8, st));
     }
-    P.done_index = chain_counter_ints(c) - 1;
     int rc = chain_launch(domain, fp8, bn, maps, P, grid, st);
     if (rc || (rc = mark(s, st)) || P.fused_head) return rc;
     // the last layer over the stored BF16 activations of the last hidden layer: on the tensor
@@ -1316,6 +1317,11 @@ int cbdfs_device_status(cbdfs_ctx *ctx) {
     CUDA_TRY(cudaDeviceSynchronize());
     int flag = 0;
     CUDA_TRY(cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        // a wait that ran out may have left chain counts behind: zero every slot's counters
+        for (Slot &s : c->slots)
+            if (s.counters) CUDA_TRY(cudaMemset(s.counters, 0, sizeof(int) * chain_counter_ints(c)));
+    }
     CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int)));
     return flag;
 }

@@ -33,10 +33,10 @@ struct ChainParams {
     void *act[2];
     const float *bias[kMaxLayers];
     float acc_scale[kMaxLayers], out_qscale[kMaxLayers];
-    int *counters;                 // [mblocks] one-hot units (16 = all rows), then [nh][mblocks]
+    int *counters;                 // [mblocks] one-hot units (kBM / unit_rows = all rows), then [nh][mblocks]
                                    // stored warp-tiles (4 per tile), then [mblocks] head counts;
-                                   // zero at launch, left zero by the last CTA to finish
-    int done_index;                // counters[done_index]: CTAs finished
+                                   // zero at launch; zeroed again once nothing reads them
+    int unit_rows;                 // rows of a one-hot pre-pass unit: 8 or 16
     float *partial;                // [nt_last][rows_pad][C]
     int rows_pad;
     int fused_head;                // 1: the last layer runs in the last hidden layer's epilogue;

@@ -68,7 +68,7 @@ struct NetGPU {
     CUtensorMap tm_w[kMaxLayers];      // TMA maps of w_lp (k-block x bn rows)
     CUtensorMap tm_w64[kMaxLayers];    // the same with 64-row boxes (small-batch chain tiles)
     int bn[kMaxLayers] = {};           // N tile per layer
-    // classifier heads of 33..128 outputs on a BF16/E4M3 network: the last layer split into three
+    // classifier heads of 17..128 outputs on a BF16/E4M3 network: the last layer split into three
     // BF16 parts [3][head_cpad][K] for the tensor-core head (head_cpad = 0: none)
     void *w_split = nullptr;
     CUtensorMap tm_wsplit;

@@ -51,6 +51,10 @@ __device__ __forceinline__ uint32_t ld_acquire(const int *p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+// count += v with release semantics at GPU scope (this thread's prior writes become visible first)
+__device__ __forceinline__ void red_release_add(int *p, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
@@ -270,40 +274,52 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
     constexpr int KBLK = FP8 ? 128 : 64;
 
     {
-        // one-hot pre-pass by every warp of the grid: unit v = rows [8v, 8v+8) goes to warp
-        // v mod (warps in the grid); a row block counts its 16 units
+        // one-hot pre-pass by every warp of the grid: unit v = rows [R v, R v + R) goes to warp
+        // v mod (warps in the grid), R = P.unit_rows (16 for one-hot rows of up to 512 bytes,
+        // else 8: about 8 KB per unit); a row block counts its kBM / R units.  The next unit's
+        // states are loaded while this one is written and published.
         constexpr int EB = FP8 ? 1 : 2;
         constexpr int nwarps = kChainThreads / 32;
-        const int units = P.mblocks * (kBM / 8);
+        const int R = P.unit_rows;
+        const int units = P.mblocks * (kBM / R);
         const int nchunk = P.kdim[0] * EB / 16;
-        for (int v = blockIdx.x * nwarps + warp; v < units; v += gridDim.x * nwarps) {
-            const uint32_t my = v * 8 + (lane & 7);
-            uint64_t s0 = 0, s1 = 0;
-            const bool lv = lane < 8 && my < P.n;
-            if (lv) {
+        const int vstride = gridDim.x * nwarps;
+        uint64_t n0 = 0, n1 = 0;
+        bool nlv = false;
+        auto load_unit = [&](int v) {
+            const uint32_t my = v * R + (lane & (R - 1));
+            n0 = n1 = 0;
+            nlv = lane < R && my < P.n;
+            if (nlv) {
                 if (DOMAIN == CBDFS_DOM_RC3) {
                     const ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2 *>(P.states) + my);
-                    s0 = w.x;
-                    s1 = w.y;
+                    n0 = w.x;
+                    n1 = w.y;
                 } else {
-                    s0 = __ldg(P.states + my);
+                    n0 = __ldg(P.states + my);
                 }
             }
+        };
+        if (blockIdx.x * nwarps + warp < units) load_unit(blockIdx.x * nwarps + warp);
+        for (int v = blockIdx.x * nwarps + warp; v < units; v += vstride) {
+            const uint64_t s0 = n0, s1 = n1;
+            const bool lv = nlv;
+            if (v + vstride < units) load_unit(v + vstride);
             uint64_t wa, wb;
             OneHot<DOMAIN>::prepare(s0, s1, wa, wb);
 #pragma unroll 1
-            for (int r = 0; r < 8; ++r) {
+            for (int r = 0; r < R; ++r) {
                 const uint64_t ar = __shfl_sync(0xFFFFFFFFu, wa, r);
                 const uint64_t br = DOMAIN == CBDFS_DOM_RC3 ? __shfl_sync(0xFFFFFFFFu, wb, r) : 0ull;
                 const bool lr = __shfl_sync(0xFFFFFFFFu, lv, r);
                 uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(P.onehot) +
-                                                       (size_t)(v * 8 + r) * P.kdim[0] * EB);
+                                                       (size_t)(v * R + r) * P.kdim[0] * EB);
                 for (int k = lane; k < nchunk; k += 32) dst[k] = onehot_chunk<DOMAIN, FP8>(ar, br, lr, k);
             }
             fence_proxy_async_global();  // the rows are read by TMA (the async proxy)
             __threadfence();
             __syncwarp();
-            if (lane == 0) atomicAdd(P.counters + v / (kBM / 8), 1);
+            if (lane == 0) atomicAdd(P.counters + v / (kBM / R), 1);
         }
     }
 
@@ -316,14 +332,17 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
             const int KB = P.kdim[T.l] / KBLK;
             const int kb0 = P.group_nt[T.l] ? (T.n / P.group_nt[T.l]) * KB : 0;  // member's K block
             if (lane == 0) stamp(P, pi, 0);
-            // layer 0 reads the one-hot rows (16 units of 8 rows), layer l the stored tiles of
+            // layer 0 reads the one-hot rows (kBM / R units), layer l the stored tiles of
             // layer l-1 (4 warps per tile)
-            const int *cnt = T.l == 0 ? P.counters + T.m : P.counters + T.l * P.mblocks + T.m;
-            const int want = T.l == 0 ? kBM / 8 : 4 * P.nt[T.l - 1];
+            const int *cnt = P.counters + T.l * P.mblocks + T.m;
+            const int want = T.l == 0 ? kBM / P.unit_rows : 4 * P.nt[T.l - 1];
             if (lane == 0) ok = wait_count(cnt, want, P.err);
             ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
             if (!ok) break;
             fence_proxy_async_global();
+            // this layer's inputs are complete, so every tile of the previous layer in this row
+            // block has read its own input count: that count is left zero for the next launch
+            if (lane == 0 && T.l > 0) P.counters[(T.l - 1) * P.mblocks + T.m] = 0;
             if (lane == 0) stamp(P, pi, 1);
             for (int kb = 0; kb < KB; ++kb, ++it) {
                 const int s = it % STAGES;
@@ -487,8 +506,15 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                     // publish this warp's 32 rows: stores complete, then the count (4 per tile)
                     bulk_wait_all();
                     fence_proxy_async_global();
-                    __threadfence();
-                    if (good) atomicAdd(P.counters + (1 + T.l) * P.mblocks + T.m, 1);
+                    int *oc = P.counters + (1 + T.l) * P.mblocks + T.m;
+                    if (good && T.l + 1 < P.nh) {
+                        red_release_add(oc, 1);
+                    } else if (good && atomicAdd(oc, 1) == 4 * P.nt[T.l] - 1) {
+                        // the last hidden layer, stored for a separate head kernel: the row block's
+                        // last warp leaves its own count and the layer's input count zero
+                        atomicExch(oc, 0);
+                        atomicExch(P.counters + T.l * P.mblocks + T.m, 0);
+                    }
                 }
                 __syncwarp();
             } else {
@@ -537,8 +563,13 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                 __threadfence();
                 epi_bar();
                 if (ep_tid == 0) {
-                    const int old = good ? atomicAdd(P.counters + (1 + P.nh) * P.mblocks + T.m, 1) : -1;
+                    int *hc = P.counters + (1 + P.nh) * P.mblocks + T.m;
+                    const int old = good ? atomicAdd(hc, 1) : -1;
                     *flag = old == P.nt[T.l] - 1;
+                    if (*flag) {  // the row block's last partial: its counts are left zero for the next launch
+                        atomicExch(hc, 0);
+                        atomicExch(P.counters + T.l * P.mblocks + T.m, 0);
+                    }
                 }
                 epi_bar();
                 if (*flag) {
@@ -566,21 +597,6 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, 2 * BN);
-    }
-    // the last CTA to finish (none polls a counter any more) leaves the counters zeroed for
-    // the next launch on this slot
-    if (threadIdx.x == 0) {
-        __threadfence();
-        *flag = atomicAdd(P.counters + P.done_index, 1) == (int)gridDim.x - 1;
-    }
-    __syncthreads();
-    if (*flag) {
-        __threadfence();
-        const int nints = (P.nh + 2) * P.mblocks;
-        for (int i = threadIdx.x; i < nints; i += blockDim.x) P.counters[i] = 0;
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) atomicExch(P.counters + P.done_index, 0);
     }
 }
 
