@@ -307,14 +307,24 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
             if (v + vstride < units) load_unit(v + vstride);
             uint64_t wa, wb;
             OneHot<DOMAIN>::prepare(s0, s1, wa, wb);
+            // eight rows at a time, unrolled, so that their shuffles and stores overlap; a lane
+            // writes chunks lane and lane + 32 of each row (rows of up to 1 KB; wider rows go on
+            // in the loop after)
 #pragma unroll 1
-            for (int r = 0; r < R; ++r) {
-                const uint64_t ar = __shfl_sync(0xFFFFFFFFu, wa, r);
-                const uint64_t br = DOMAIN == CBDFS_DOM_RC3 ? __shfl_sync(0xFFFFFFFFu, wb, r) : 0ull;
-                const bool lr = __shfl_sync(0xFFFFFFFFu, lv, r);
-                uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(P.onehot) +
-                                                       (size_t)(v * R + r) * P.kdim[0] * EB);
-                for (int k = lane; k < nchunk; k += 32) dst[k] = onehot_chunk<DOMAIN, FP8>(ar, br, lr, k);
+            for (int r0 = 0; r0 < R; r0 += 8) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int r = r0 + j;
+                    const uint64_t ar = __shfl_sync(0xFFFFFFFFu, wa, r);
+                    const uint64_t br = DOMAIN == CBDFS_DOM_RC3 ? __shfl_sync(0xFFFFFFFFu, wb, r) : 0ull;
+                    const bool lr = __shfl_sync(0xFFFFFFFFu, lv, r);
+                    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(P.onehot) +
+                                                           (size_t)(v * R + r) * P.kdim[0] * EB);
+#pragma unroll
+                    for (int q = 0; q < 2; ++q)
+                        if (lane + 32 * q < nchunk) dst[lane + 32 * q] = onehot_chunk<DOMAIN, FP8>(ar, br, lr, lane + 32 * q);
+                    for (int k = lane + 64; k < nchunk; k += 32) dst[k] = onehot_chunk<DOMAIN, FP8>(ar, br, lr, k);
+                }
             }
             fence_proxy_async_global();  // the rows are read by TMA (the async proxy)
             __threadfence();
