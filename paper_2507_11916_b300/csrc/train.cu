@@ -232,30 +232,36 @@ __global__ void k_onehot_t(const uint64_t *__restrict__ states, uint32_t n, int 
 // the class index; loss 1: 0.5 (y - label)^2 on one output.  Per-row losses to row_loss.
 __global__ void k_loss(const float *__restrict__ logits, const uint8_t *__restrict__ labels, int n, int C,
                        int loss, float *__restrict__ dz, float *__restrict__ row_loss) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= n) return;
+    // one warp per row: coalesced reads of the row's logits, butterfly reductions (every lane
+    // ends with the same maximum and sum, in a fixed order)
+    const int m = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (m >= n) return;  // warp-uniform
     const float *z = logits + (size_t)m * C;
+    float *d = dz + (size_t)m * C;
     const float inv_n = 1.f / (float)n;
     if (loss == 1) {
-        const float r = z[0] - (float)labels[m];
-        row_loss[m] = 0.5f * r * r;
-        dz[(size_t)m * C] = r * inv_n;
+        if (lane == 0) {
+            const float r = z[0] - (float)labels[m];
+            row_loss[m] = 0.5f * r * r;
+            d[0] = r * inv_n;
+        }
         return;
     }
-    float mx = z[0];
-    for (int c = 1; c < C; ++c) mx = fmaxf(mx, z[c]);
+    float mx = -INFINITY;
+    for (int c = lane; c < C; c += 32) mx = fmaxf(mx, z[c]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
     float sum = 0.f;
-    for (int c = 0; c < C; ++c) sum += expf(z[c] - mx);
+    for (int c = lane; c < C; c += 32) sum += expf(z[c] - mx);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
     const int y = labels[m];
-    row_loss[m] = logf(sum) + mx - z[y];
-    for (int c = 0; c < C; ++c) {
+    if (lane == 0) row_loss[m] = logf(sum) + mx - z[y];
+    for (int c = lane; c < C; c += 32) {
         const float p = expf(z[c] - mx) / sum;
-        dz[(size_t)m * C + c] = (p - (c == y ? 1.f : 0.f)) * inv_n;
+        d[c] = (p - (c == y ? 1.f : 0.f)) * inv_n;
     }
 }
-
-
-
 
 // ---- FP32 GEMM on the CUDA cores (the last layer's products) ----------------------------
 // out[z][m][n] = sum over k in split z of A(m,k) B(k,n), FP32: A(m,k) = A[m*sam + k*sak],
@@ -671,7 +677,7 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
         k_fgemm<__nv_bfloat16, float, true, false, 1><<<dim3((C + FG_T - 1) / FG_T, (n + FG_T - 1) / FG_T, 1), blk, 0, st>>>(
             T.act[L - 2], KL, 1, T.w[L - 1], 1, KL, n, C, KL, KL, T.logits, T.b[L - 1], nullptr, 0, nullptr);
     }
-    k_loss<<<(n + 255) / 256, 256, 0, st>>>(T.logits, T.labels, n, C, loss_kind, T.dzl, T.row_loss);
+    k_loss<<<(n + 7) / 8, 256, 0, st>>>(T.logits, T.labels, n, C, loss_kind, T.dzl, T.row_loss);
     k_mean<<<1, 256, 0, st>>>(T.row_loss, n, T.loss);
     // last layer backward (FP32): dW[c][k] = sum_m dZ[m][c] A[m][k] in row splits, then the
     // splits in order; db = column sums of dZ; dZ_prev = (dZ W) * [A > 0] in BF16
