@@ -162,11 +162,12 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 
 __global__ void k_sum_splits(const float *__restrict__ part, int S, int len, float *__restrict__ out);
 
-// splits > 1 (EPI 1 only): the partials go to `part` (splits x M x N floats), then their sum
-// in split order to `out`
+// splits > 1 (EPI 1 only): the partials go to `part` (splits x M x N floats), then (sum) their
+// sum in split order to `out`
 template <int BN, int EPI>
 int gemm_tn(const CUtensorMap &tmA, const CUtensorMap &tmB, int M, int N, int K, void *out,
-            const __nv_bfloat16 *mask, int *err, cudaStream_t st, int splits = 1, float *part = nullptr) {
+            const __nv_bfloat16 *mask, int *err, cudaStream_t st, int splits = 1, float *part = nullptr,
+            bool sum = true) {
     constexpr int kStageB = BN * 128;
     const int stages = 4;
     const size_t smem = 1024 + 256 + (size_t)stages * (kStageA + kStageB);
@@ -176,7 +177,7 @@ int gemm_tn(const CUtensorMap &tmA, const CUtensorMap &tmB, int M, int N, int K,
     kern<<<dim3(N / BN, M / kBM, split ? splits : 1), kThreads, smem, st>>>(tmA, tmB, K, N, split ? part : out,
                                                                            mask, stages, err);
     CUDA_TRY(cudaGetLastError());
-    if (split) {
+    if (split && sum) {
         const int len = M * N;
         k_sum_splits<<<(len + 255) / 256, 256, 0, st>>>(part, splits, len, static_cast<float *>(out));
         CUDA_TRY(cudaGetLastError());
@@ -329,11 +330,7 @@ k_fgemm(const TA *__restrict__ A, long sam, long sak, const TB *__restrict__ B, 
 // the last layer's FP32 weights w[C][K] as three BF16 parts out[part][cpad][K] (W = W1 + W2 + W3,
 // each part the round-to-nearest-even BF16 of what the previous parts leave), for the
 // tensor-core head
-__global__ void k_split3(const float *__restrict__ w, int C, int K, int cpad, __nv_bfloat16 *__restrict__ out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= C * K) return;
-    const int c = i / K, k = i % K;
-    float r = w[i];
+__device__ __forceinline__ void split3_store(float r, int c, int k, int K, int cpad, __nv_bfloat16 *__restrict__ out) {
 #pragma unroll
     for (int part = 0; part < 3; ++part) {
         const __nv_bfloat16 b = __float2bfloat16_rn(r);
@@ -393,25 +390,46 @@ __global__ void k_mean(const float *__restrict__ v, int n, float *__restrict__ o
     }
 }
 
-// Adam on FP32 masters; optional BF16 copies: w_lp[o][Kp] (padded inference layout) and
-// wt[i][O] (transposed, for the backward GEMM)
-__global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ mo,
-                       float *__restrict__ ve, int O, int I, float lr, float b1, float b2, float eps,
-                       float c1, float c2, __nv_bfloat16 *__restrict__ w_lp, int Kp,
-                       __nv_bfloat16 *__restrict__ wt) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= O * I) return;
-    const float gg = g[idx];
-    const float m = b1 * mo[idx] + (1.f - b1) * gg;
-    const float v = b2 * ve[idx] + (1.f - b2) * gg * gg;
-    mo[idx] = m;
-    ve[idx] = v;
-    const float mh = m / c1, vh = v / c2;
-    const float nw = w[idx] - lr * mh / (sqrtf(vh) + eps);
-    w[idx] = nw;
-    const int o = idx / I, i = idx % I;
-    if (w_lp) w_lp[(size_t)o * Kp + i] = __float2bfloat16(nw);
-    if (wt) wt[(size_t)i * O + o] = __float2bfloat16(nw);
+// Adam on the FP32 masters of every tensor in one launch: segment s (a layer's weights [O][I]
+// or biases [O]) owns blocks [block0, next block0).  Besides the master it writes the copies
+// the other kernels read: the BF16 inference weights w_lp[o][Kp], their transpose wt[i][O] for
+// the backward GEMM, an FP32 inference copy (the last layer, the biases) and the last layer's
+// three BF16 parts for the tensor-core head.
+struct AdamSeg {
+    float *w;
+    const float *g;  // parts x [O][I]: the gradient is the sum of the parts in order
+    float *m, *v;
+    int O, I, block0, Kp, cpad, parts;
+    __nv_bfloat16 *w_lp, *wt, *split;
+    float *w_out;
+};
+struct AdamParams {
+    AdamSeg seg[2 * kMaxLayers];
+    int nseg;
+    float lr, b1, b2, eps, c1, c2;
+};
+
+__global__ void __launch_bounds__(256) k_adam_all(const __grid_constant__ AdamParams P) {
+    int s = 0;
+    while (s + 1 < P.nseg && (int)blockIdx.x >= P.seg[s + 1].block0) ++s;
+    const AdamSeg &S = P.seg[s];
+    const int idx = ((int)blockIdx.x - S.block0) * blockDim.x + threadIdx.x;
+    if (idx >= S.O * S.I) return;
+    const size_t len = (size_t)S.O * S.I;
+    float gg = 0.f;
+    for (int z = 0; z < S.parts; ++z) gg += S.g[z * len + idx];
+    const float m = P.b1 * S.m[idx] + (1.f - P.b1) * gg;
+    const float v = P.b2 * S.v[idx] + (1.f - P.b2) * gg * gg;
+    S.m[idx] = m;
+    S.v[idx] = v;
+    const float mh = m / P.c1, vh = v / P.c2;
+    const float nw = S.w[idx] - P.lr * mh / (sqrtf(vh) + P.eps);
+    S.w[idx] = nw;
+    const int o = idx / S.I, i = idx % S.I;
+    if (S.w_lp) S.w_lp[(size_t)o * S.Kp + i] = __float2bfloat16(nw);
+    if (S.wt) S.wt[(size_t)i * S.O + o] = __float2bfloat16(nw);
+    if (S.w_out) S.w_out[idx] = nw;
+    if (S.split) split3_store(nw, o, i, S.I, S.cpad, S.split);
 }
 
 // wt[i][O] = BF16(w[o][i])
@@ -489,9 +507,13 @@ struct TrainState {
     __nv_bfloat16 *dz[kMaxLayers] = {};                    // dZ_l BF16 [Bp][dims[l+1]]
     __nv_bfloat16 *t_dz = nullptr, *t_a = nullptr;         // transposes (largest)
     float *logits = nullptr, *dzl = nullptr, *row_loss = nullptr, *loss = nullptr;
-    float *red = nullptr;                                  // split / row-chunk partial sums
-    size_t red_floats = 0;
-    float *dw_part = nullptr;                              // split-K partials of the hidden dW
+    // partial sums of every gradient tensor: the weights' row (split-K) partials and the
+    // biases' row-chunk partials, [parts][len] each; the gradient is their sum in part order
+    float *gw_buf[kMaxLayers] = {}, *gb_buf[kMaxLayers] = {};
+    size_t gw_buf_floats[kMaxLayers] = {}, gb_buf_floats[kMaxLayers] = {};
+    // where the last backward left each gradient: `parts` partials at gw_src (1: the sum itself)
+    const float *gw_src[kMaxLayers] = {}, *gb_src[kMaxLayers] = {};
+    int gw_parts[kMaxLayers] = {}, gb_parts[kMaxLayers] = {};
     uint64_t *states = nullptr;
     uint8_t *labels = nullptr;
     int64_t step = 0;
@@ -569,19 +591,15 @@ static int train_setup(Ctx *c, NetGPU &net, int B, const float *const *host_w, c
         if (!rc) rc = talloc(c, *T, (void **)&T->logits, (size_t)Bp * C * 4);
         if (!rc) rc = talloc(c, *T, (void **)&T->dzl, (size_t)Bp * C * 4);
         if (!rc) rc = talloc(c, *T, (void **)&T->row_loss, (size_t)Bp * 4);
-        {
-            // partials: the last layer's dW in row splits, and column sums in row chunks
-            const size_t KL = net.dims[L - 1];
-            T->red_floats = std::max((size_t)((Bp + kDwRows - 1) / kDwRows) * C * KL,
-                                     (size_t)((Bp + kSumRows - 1) / kSumRows) * std::max(maxw, (size_t)C));
-            if (!rc) rc = talloc(c, *T, (void **)&T->red, T->red_floats * 4);
-            size_t part = 0;  // the hidden layers' dW in row splits (dw_splits)
-            for (int l = 0; l < L - 1; ++l) {
-                const int O = net.dims[l + 1], I = l == 0 ? (int)k1 : net.dims[l];
-                const int S = dw_splits(c, O, I, Bp);
-                if (S > 1) part = std::max(part, (size_t)S * O * I);
-            }
-            if (!rc && part) rc = talloc(c, *T, (void **)&T->dw_part, part * 4);
+        // partials of every gradient tensor: the hidden dW in row splits (dw_splits), the last
+        // layer's dW in row splits of kDwRows, the biases' column sums in row chunks of kSumRows
+        for (int l = 0; l < L && !rc; ++l) {
+            const size_t O = net.dims[l + 1], I = l == 0 ? k1 : (size_t)net.dims[l];
+            const size_t parts = l < L - 1 ? (size_t)dw_splits(c, (int)O, (int)I, Bp) : (size_t)(Bp + kDwRows - 1) / kDwRows;
+            T->gw_buf_floats[l] = parts * O * I;
+            T->gb_buf_floats[l] = (size_t)((Bp + kSumRows - 1) / kSumRows) * O;
+            rc = talloc(c, *T, (void **)&T->gw_buf[l], T->gw_buf_floats[l] * 4);
+            if (!rc) rc = talloc(c, *T, (void **)&T->gb_buf[l], T->gb_buf_floats[l] * 4);
         }
         if (!rc) rc = talloc(c, *T, (void **)&T->loss, 4);
         if (!rc) rc = talloc(c, *T, (void **)&T->states, (size_t)Bp * 16);
@@ -623,23 +641,29 @@ static int train_setup(Ctx *c, NetGPU &net, int B, const float *const *host_w, c
 }
 
 // forward + loss + backward on the batch already in T.states / T.labels (n rows)
-// out[j] = sum of X[m][j] over m < n, by row chunks then chunks in order (deterministic)
+// column sums of X[m][j] over m < n by row chunks (fixed order) into part[R][J]; with sum,
+// the chunks then added in order into out (deterministic).  Returns R through *parts.
 template <typename T>
-static int colsum(TrainState &S, const T *X, int n, int J, float *out, cudaStream_t st) {
+static int colsum(const T *X, int n, int J, float *part, size_t part_floats, float *out, bool sum, int *parts,
+                  cudaStream_t st) {
     const int R = (n + kSumRows - 1) / kSumRows;
-    if ((size_t)R * J > S.red_floats) return fail(CBDFS_EINVAL, "column-sum scratch");
+    if ((size_t)R * J > part_floats) return fail(CBDFS_EINVAL, "column-sum scratch");
     if constexpr (std::is_same<T, __nv_bfloat16>::value) {
-        if (J % 2 == 0) k_colsum_part2<<<dim3((J / 2 + 255) / 256, R), 256, 0, st>>>(X, n, J, kSumRows, S.red);
-        else k_colsum_part<T><<<dim3((J + 255) / 256, R), 256, 0, st>>>(X, n, J, kSumRows, S.red);
+        if (J % 2 == 0) k_colsum_part2<<<dim3((J / 2 + 255) / 256, R), 256, 0, st>>>(X, n, J, kSumRows, part);
+        else k_colsum_part<T><<<dim3((J + 255) / 256, R), 256, 0, st>>>(X, n, J, kSumRows, part);
     } else {
-        k_colsum_part<T><<<dim3((J + 255) / 256, R), 256, 0, st>>>(X, n, J, kSumRows, S.red);
+        k_colsum_part<T><<<dim3((J + 255) / 256, R), 256, 0, st>>>(X, n, J, kSumRows, part);
     }
-    k_sum_splits<<<(J + 255) / 256, 256, 0, st>>>(S.red, R, J, out);
+    if (sum) k_sum_splits<<<(J + 255) / 256, 256, 0, st>>>(part, R, J, out);
+    *parts = R;
     CUDA_TRY(cudaGetLastError());
     return CBDFS_OK;
 }
 
-static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t st) {
+// forward + loss + backward on the batch already in T.states / T.labels (n rows).  sum: every
+// gradient summed into gw / gb; otherwise the partials stay where gw_src / gb_src say (the
+// training step's Adam adds them)
+static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t st, bool sum) {
     TrainState &T = *net.train;
     const int L = net.L, C = net.dims[L];
     const int Bp = (n + kBM - 1) / kBM * kBM;
@@ -683,9 +707,16 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
     // splits in order; db = column sums of dZ; dZ_prev = (dZ W) * [A > 0] in BF16
     const int sdw = (n + kDwRows - 1) / kDwRows;
     k_fgemm<float, __nv_bfloat16, false, true, 0><<<dim3((KL + FG_T - 1) / FG_T, (C + FG_T - 1) / FG_T, sdw), blk, 0, st>>>(
-        T.dzl, 1, C, T.act[L - 2], KL, 1, C, KL, n, kDwRows, T.red, nullptr, nullptr, 0, nullptr);
-    k_sum_splits<<<(C * KL + 255) / 256, 256, 0, st>>>(T.red, sdw, C * KL, T.gw[L - 1]);
-    if (int r = colsum(T, T.dzl, n, C, T.gb[L - 1], st)) return r;
+        T.dzl, 1, C, T.act[L - 2], KL, 1, C, KL, n, kDwRows, T.gw_buf[L - 1], nullptr, nullptr, 0, nullptr);
+    if (sum) k_sum_splits<<<(C * KL + 255) / 256, 256, 0, st>>>(T.gw_buf[L - 1], sdw, C * KL, T.gw[L - 1]);
+    T.gw_src[L - 1] = sum ? T.gw[L - 1] : T.gw_buf[L - 1];
+    T.gw_parts[L - 1] = sum ? 1 : sdw;
+    {
+        int parts = 0;
+        if (int r = colsum(T.dzl, n, C, T.gb_buf[L - 1], T.gb_buf_floats[L - 1], T.gb[L - 1], sum, &parts, st)) return r;
+        T.gb_src[L - 1] = sum ? T.gb[L - 1] : T.gb_buf[L - 1];
+        T.gb_parts[L - 1] = sum ? 1 : parts;
+    }
     k_fgemm<float, float, true, true, 2><<<dim3((KL + FG_T - 1) / FG_T, Bp / FG_T, 1), blk, 0, st>>>(
         T.dzl, C, 1, T.w[L - 1], KL, 1, Bp, KL, C, C, nullptr, nullptr, T.act[L - 2], n, T.dz[L - 2]);
     // hidden layers, last to first
@@ -706,11 +737,19 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
         const CUtensorMap *ma = bmap(T, T.t_dz, Bp, O, kBM);
         const CUtensorMap *mb = bmap(T, T.t_a, Bp, I, I % 256 == 0 ? 256 : 128);
         if (!ma || !mb) return CBDFS_EDEVICE;
-        const int S = T.dw_part ? dw_splits(c, O, I, Bp) : 1;
-        rc = (I % 256 == 0) ? gemm_tn<256, 1>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st, S, T.dw_part)
-                            : gemm_tn<128, 1>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st, S, T.dw_part);
+        const int S = dw_splits(c, O, I, Bp);
+        if ((size_t)S * O * I > T.gw_buf_floats[l]) return fail(CBDFS_EINVAL, "dW scratch");
+        rc = (I % 256 == 0) ? gemm_tn<256, 1>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st, S, T.gw_buf[l], sum)
+                            : gemm_tn<128, 1>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st, S, T.gw_buf[l], sum);
         if (rc) return rc;
-        if (int r = colsum(T, T.dz[l], n, O, T.gb[l], st)) return r;
+        T.gw_src[l] = S > 1 && !sum ? T.gw_buf[l] : T.gw[l];
+        T.gw_parts[l] = S > 1 && !sum ? S : 1;
+        {
+            int parts = 0;
+            if (int r = colsum(T.dz[l], n, O, T.gb_buf[l], T.gb_buf_floats[l], T.gb[l], sum, &parts, st)) return r;
+            T.gb_src[l] = sum ? T.gb[l] : T.gb_buf[l];
+            T.gb_parts[l] = sum ? 1 : parts;
+        }
         if (l > 0) {
             // dZ_{l-1} = (dZ_l W_l) * [A_{l-1} > 0]
             const CUtensorMap *mz = bmap(T, T.dz[l], O, T.Bp, kBM);
@@ -728,26 +767,50 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
 static int train_update(Ctx *c, NetGPU &net, const cbdfs_train_cfg &tc, cudaStream_t st) {
     TrainState &T = *net.train;
     T.step++;
-    const float c1 = 1.f - powf(tc.beta1, (float)T.step), c2 = 1.f - powf(tc.beta2, (float)T.step);
+    AdamParams A{};
+    A.lr = tc.lr;
+    A.b1 = tc.beta1;
+    A.b2 = tc.beta2;
+    A.eps = tc.eps;
+    A.c1 = 1.f - powf(tc.beta1, (float)T.step);
+    A.c2 = 1.f - powf(tc.beta2, (float)T.step);
+    int blocks = 0;
+    auto add = [&](const AdamSeg &g) {
+        A.seg[A.nseg] = g;
+        A.seg[A.nseg].block0 = blocks;
+        blocks += (g.O * g.I + 255) / 256;
+        ++A.nseg;
+    };
     for (int l = 0; l < net.L; ++l) {
         const int O = net.dims[l + 1], I = l == 0 ? net.k1pad : net.dims[l];
-        __nv_bfloat16 *wlp = l < net.L - 1 ? static_cast<__nv_bfloat16 *>(net.w_lp[l]) : nullptr;
-        const int Kp = I;
-        k_adam<<<(O * I + 255) / 256, 256, 0, st>>>(T.w[l], T.gw[l], T.mw[l], T.vw[l], O, I, tc.lr, tc.beta1,
-                                                    tc.beta2, tc.eps, c1, c2, wlp, Kp,
-                                                    (l >= 1 && l < net.L - 1) ? T.wt[l] : nullptr);
-        k_adam<<<(O + 255) / 256, 256, 0, st>>>(T.b[l], T.gb[l], T.mb[l], T.vb[l], O, 1, tc.lr, tc.beta1, tc.beta2,
-                                                tc.eps, c1, c2, nullptr, 0, nullptr);
-        if (l == net.L - 1) {  // the inference head reads the FP32 last layer
-            CUDA_TRY(cudaMemcpyAsync(net.w32[l], T.w[l], (size_t)O * I * 4, cudaMemcpyDeviceToDevice, st));
-            if (net.w_split) {  // and the tensor-core head its three BF16 parts
-                k_split3<<<(O * I + 255) / 256, 256, 0, st>>>(T.w[l], O, I, net.head_cpad,
-                                                               static_cast<__nv_bfloat16 *>(net.w_split));
-                CUDA_TRY(cudaGetLastError());
-            }
-        }
-        CUDA_TRY(cudaMemcpyAsync(net.b32[l], T.b[l], (size_t)O * 4, cudaMemcpyDeviceToDevice, st));
+        const bool last = l == net.L - 1;
+        AdamSeg w{};
+        w.w = T.w[l];
+        w.g = T.gw_src[l];
+        w.parts = T.gw_parts[l];
+        w.m = T.mw[l];
+        w.v = T.vw[l];
+        w.O = O;
+        w.I = I;
+        w.w_lp = last ? nullptr : static_cast<__nv_bfloat16 *>(net.w_lp[l]);
+        w.Kp = I;
+        w.wt = (l >= 1 && !last) ? T.wt[l] : nullptr;
+        w.w_out = last ? net.w32[l] : nullptr;  // the inference head reads the FP32 last layer
+        w.split = last ? static_cast<__nv_bfloat16 *>(net.w_split) : nullptr;  // and the tensor-core head its parts
+        w.cpad = net.head_cpad;
+        add(w);
+        AdamSeg b{};
+        b.w = T.b[l];
+        b.g = T.gb_src[l];
+        b.parts = T.gb_parts[l];
+        b.m = T.mb[l];
+        b.v = T.vb[l];
+        b.O = O;
+        b.I = 1;
+        b.w_out = net.b32[l];
+        add(b);
     }
+    k_adam_all<<<blocks, 256, 0, st>>>(A);
     CUDA_TRY(cudaGetLastError());
     return CBDFS_OK;
 }
@@ -806,7 +869,7 @@ int cbdfs_train_grad(cbdfs_ctx *ctx, int net_id, const uint64_t *states, const u
     if ((rc = train_setup(c, *net, (int)n, hw, hbv.data()))) return rc;
     cudaStream_t st = c->slots[0].stream;
     if ((rc = upload_batch(c, *net, states, labels, n, st))) return rc;
-    if ((rc = train_fwd_bwd(c, *net, (int)n, loss, st))) return rc;
+    if ((rc = train_fwd_bwd(c, *net, (int)n, loss, st, true))) return rc;
     TrainState &T = *net->train;
     CUDA_TRY(cudaMemcpyAsync(loss_out, T.loss, 4, cudaMemcpyDeviceToHost, st));
     for (int l = 0; l < net->L; ++l) {
@@ -896,7 +959,7 @@ int net_train(cbdfs_ctx *ctx, int net_id, const uint64_t *states, const uint8_t 
             const uint32_t off = (uint32_t)(k * tc.batch);
             const uint32_t bn = (uint32_t)std::min<uint64_t>(tc.batch, n - off);
             k_gather<<<(bn + 255) / 256, 256, 0, st>>>(d_states, d_labels, d_idx + off, w, bn, T.states, T.labels);
-            rc = train_fwd_bwd(c, *net, (int)bn, tc.loss, st);
+            rc = train_fwd_bwd(c, *net, (int)bn, tc.loss, st, false);
             if (!rc) rc = train_update(c, *net, tc, st);
             if (!rc && (steps == 0 || (steps & 255) == 255)) {
                 if (cudaMemcpyAsync(&loss, T.loss, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
