@@ -7,14 +7,17 @@
 //             activations A_l kept in BF16; last layer FP32: logits = A_{L-2} W_L^T + b_L
 //   loss      cross-entropy over the classes (labels = class index) or MSE (one output);
 //             dZ_L = dLoss/dlogits (mean over the batch)
-//   backward  last layer FP32: dW_L = dZ_L^T A_{L-2}, db_L = colsum(dZ_L),
+//   backward  last layer, FP32-accurate on the tensor cores: dZ_L (FP32) as two BF16 parts and
+//             W_L as three, every product exact and accumulated in FP32:
+//             dW_L = dZ_L^T A_{L-2} (split-K over the batch), db_L = colsum(dZ_L),
 //             dZ_{L-2} = (dZ_L W_L) * [A_{L-2} > 0] (BF16)
 //             hidden l: dW_l = dZ_l^T A_{l-1} as a tcgen05 GEMM over the batch (both operands
 //             transposed to K-major by a tiled transpose; A_{-1} is the transposed one-hot),
 //             db_l = colsum(dZ_l), dZ_{l-1} = (dZ_l W_l) * [A_{l-1} > 0] as a tcgen05 GEMM
 //             with the mask fused in the epilogue (W_l^T kept in BF16 beside W_l)
-//   update    Adam (bias-corrected) on the FP32 masters; BF16 copies W_l (K-padded, the
-//             inference layout) and W_l^T rewritten by the same kernel
+//   update    Adam (bias-corrected) on the FP32 masters of every tensor in one launch, adding
+//             the gradient's split partials in order; BF16 copies W_l (K-padded, the
+//             inference layout), W_l^T and the last layer's parts rewritten by the same kernel
 // Every reduction has a fixed order, so a step is deterministic.
 #include <algorithm>
 #include <chrono>
@@ -38,7 +41,6 @@ namespace {
 using namespace dev;
 
 constexpr int kThreads = 192;
-constexpr int kDwRows = 512;   // rows of one split of the last layer's dW
 constexpr int kSumRows = 64;   // rows of one chunk of a column sum
 constexpr int kStageA = kBM * 128;
 
@@ -193,11 +195,12 @@ int gemm_tn(const CUtensorMap &tmA, const CUtensorMap &tmB, int M, int N, int K,
 // memory, moved as element pairs: a warp reads and writes 128 contiguous bytes, and the padded
 // rows (65 elements) keep the column reads on distinct banks.  Block (32, 8).
 __global__ void __launch_bounds__(256) k_transpose(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ out,
-                                                   int R, int C) {
+                                                   int R, int C, int ldi, int ldo,
+                                                   __nv_bfloat16 *__restrict__ out2) {
     __shared__ __nv_bfloat16 t[64][65];
     const int c0 = blockIdx.x * 64, r0 = blockIdx.y * 64, tx = threadIdx.x;
     for (int i = threadIdx.y; i < 64; i += 8) {
-        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(in + (size_t)(r0 + i) * C + c0 + 2 * tx);
+        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(in + (size_t)(r0 + i) * ldi + c0 + 2 * tx);
         t[i][2 * tx] = v.x;
         t[i][2 * tx + 1] = v.y;
     }
@@ -206,7 +209,8 @@ __global__ void __launch_bounds__(256) k_transpose(const __nv_bfloat16 *__restri
         __nv_bfloat162 v;
         v.x = t[2 * tx][j];
         v.y = t[2 * tx + 1][j];
-        *reinterpret_cast<__nv_bfloat162 *>(out + (size_t)(c0 + j) * R + r0 + 2 * tx) = v;
+        *reinterpret_cast<__nv_bfloat162 *>(out + (size_t)(c0 + j) * ldo + r0 + 2 * tx) = v;
+        if (out2) *reinterpret_cast<__nv_bfloat162 *>(out2 + (size_t)(c0 + j) * ldo + r0 + 2 * tx) = v;
     }
 }
 
@@ -231,12 +235,53 @@ __global__ void k_onehot_t(const uint64_t *__restrict__ states, uint32_t n, int 
 
 // loss and dZ = dLoss/dlogits (mean over n rows).  loss 0: softmax cross-entropy against
 // the class index; loss 1: 0.5 (y - label)^2 on one output.  Per-row losses to row_loss.
-__global__ void k_loss(const float *__restrict__ logits, const uint8_t *__restrict__ labels, int n, int C,
-                       int loss, float *__restrict__ dz, float *__restrict__ row_loss) {
+constexpr int kExtParts = 5;
+// BF16 parts of x: x ~ p[0] + p[1] + p[2], each the round-to-nearest-even of what is left
+__device__ __forceinline__ void bf16_parts3(float r, __nv_bfloat16 (&p)[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        p[i] = __float2bfloat16_rn(r);
+        r -= __bfloat162float(p[i]);
+    }
+}
+// w_ext[k][s cs + c] for the last layer's weight w = W[c][k] (sections W1 W2 W3 W1 W2)
+__device__ __forceinline__ void ext_store_w(float w, int c, int k, int cs, __nv_bfloat16 *__restrict__ w_ext) {
+    __nv_bfloat16 p[3];
+    bf16_parts3(w, p);
+    __nv_bfloat16 *row = w_ext + (size_t)k * kExtParts * cs + c;
+    row[0] = p[0];
+    row[cs] = p[1];
+    row[2 * cs] = p[2];
+    row[3 * cs] = p[0];
+    row[4 * cs] = p[1];
+}
+// dz_ext[m][s cs + c] for the loss gradient d = dZ[m][c] (sections D1 D1 D1 D2 D2)
+__device__ __forceinline__ void ext_store_dz(float d, int c, __nv_bfloat16 *__restrict__ row, int cs) {
+    const __nv_bfloat16 d1 = __float2bfloat16_rn(d);
+    const __nv_bfloat16 d2 = __float2bfloat16_rn(d - __bfloat162float(d1));
+    row[c] = d1;
+    row[cs + c] = d1;
+    row[2 * cs + c] = d1;
+    row[3 * cs + c] = d2;
+    row[4 * cs + c] = d2;
+}
+__global__ void k_write_ext(const float *__restrict__ w, int C, int K, int cs, __nv_bfloat16 *__restrict__ w_ext) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < C * K) ext_store_w(w[i], i / K, i % K, cs, w_ext);
+}
+
+__global__ void k_loss(const float *__restrict__ logits, const uint8_t *__restrict__ labels, int n, int Bp,
+                       int C, int loss, float *__restrict__ dz, float *__restrict__ row_loss,
+                       __nv_bfloat16 *__restrict__ dz_ext, int cs) {
     // one warp per row: coalesced reads of the row's logits, butterfly reductions (every lane
-    // ends with the same maximum and sum, in a fixed order)
+    // ends with the same maximum and sum, in a fixed order).  Rows n..Bp-1 of dz_ext are zeroed.
     const int m = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (m >= n) return;  // warp-uniform
+    if (m >= Bp) return;  // warp-uniform
+    __nv_bfloat16 *e = dz_ext + (size_t)m * kExtParts * cs;
+    if (m >= n) {
+        for (int c = lane; c < C; c += 32) ext_store_dz(0.f, c, e, cs);
+        return;
+    }
     const float *z = logits + (size_t)m * C;
     float *d = dz + (size_t)m * C;
     const float inv_n = 1.f / (float)n;
@@ -245,6 +290,7 @@ __global__ void k_loss(const float *__restrict__ logits, const uint8_t *__restri
             const float r = z[0] - (float)labels[m];
             row_loss[m] = 0.5f * r * r;
             d[0] = r * inv_n;
+            ext_store_dz(r * inv_n, 0, e, cs);
         }
         return;
     }
@@ -260,7 +306,9 @@ __global__ void k_loss(const float *__restrict__ logits, const uint8_t *__restri
     if (lane == 0) row_loss[m] = logf(sum) + mx - z[y];
     for (int c = lane; c < C; c += 32) {
         const float p = expf(z[c] - mx) / sum;
-        d[c] = (p - (c == y ? 1.f : 0.f)) * inv_n;
+        const float g = (p - (c == y ? 1.f : 0.f)) * inv_n;
+        d[c] = g;
+        ext_store_dz(g, c, e, cs);
     }
 }
 
@@ -399,8 +447,9 @@ struct AdamSeg {
     float *w;
     const float *g;  // parts x [O][I]: the gradient is the sum of the parts in order
     float *m, *v;
-    int O, I, block0, Kp, cpad, parts;
-    __nv_bfloat16 *w_lp, *wt, *split;
+    int O, I, block0, Kp, cpad, parts, cs;
+    size_t pstride;  // floats from one gradient part to the next
+    __nv_bfloat16 *w_lp, *wt, *split, *w_ext;
     float *w_out;
 };
 struct AdamParams {
@@ -415,9 +464,8 @@ __global__ void __launch_bounds__(256) k_adam_all(const __grid_constant__ AdamPa
     const AdamSeg &S = P.seg[s];
     const int idx = ((int)blockIdx.x - S.block0) * blockDim.x + threadIdx.x;
     if (idx >= S.O * S.I) return;
-    const size_t len = (size_t)S.O * S.I;
     float gg = 0.f;
-    for (int z = 0; z < S.parts; ++z) gg += S.g[z * len + idx];
+    for (int z = 0; z < S.parts; ++z) gg += S.g[z * S.pstride + idx];
     const float m = P.b1 * S.m[idx] + (1.f - P.b1) * gg;
     const float v = P.b2 * S.v[idx] + (1.f - P.b2) * gg * gg;
     S.m[idx] = m;
@@ -430,6 +478,7 @@ __global__ void __launch_bounds__(256) k_adam_all(const __grid_constant__ AdamPa
     if (S.wt) S.wt[(size_t)i * S.O + o] = __float2bfloat16(nw);
     if (S.w_out) S.w_out[idx] = nw;
     if (S.split) split3_store(nw, o, i, S.I, S.cpad, S.split);
+    if (S.w_ext) ext_store_w(nw, o, i, S.cs, S.w_ext);
 }
 
 // wt[i][O] = BF16(w[o][i])
@@ -514,6 +563,18 @@ struct TrainState {
     // where the last backward left each gradient: `parts` partials at gw_src (1: the sum itself)
     const float *gw_src[kMaxLayers] = {}, *gb_src[kMaxLayers] = {};
     int gw_parts[kMaxLayers] = {}, gb_parts[kMaxLayers] = {};
+    size_t gw_pstride[kMaxLayers] = {};  // floats from one weight-gradient part to the next
+    // the last layer's dX on the tensor cores: dZ_L (FP32) as BF16 parts D1 + D2 and W_L as
+    // W1 + W2 + W3, stacked along K in kExtParts sections of `cs` columns (C padded to 64):
+    // dz_ext[m] = [D1 D1 D1 D2 D2], w_ext[k] = [W1 W2 W3 W1 W2] (columns c of each section), so
+    // one K = 5 cs GEMM adds D1 W1 + D1 W2 + D1 W3 + D2 W1 + D2 W2
+    __nv_bfloat16 *dz_ext = nullptr, *w_ext = nullptr;
+    int cs = 0;
+    // the last layer's dW = dZ^T A on the tensor cores: K-major operands over 2 Bp batch
+    // columns, t_dz_ext = [D1^T | D2^T] ([Mp][2 Bp], rows >= C zero) and t_a_ext = [A^T | A^T]
+    // ([KL][2 Bp]); the product rows are Mp = C rounded up to the 128-row tile
+    __nv_bfloat16 *t_dz_ext = nullptr, *t_a_ext = nullptr;
+    int Mp = 0;
     uint64_t *states = nullptr;
     uint8_t *labels = nullptr;
     int64_t step = 0;
@@ -579,7 +640,8 @@ static int train_setup(Ctx *c, NetGPU &net, int B, const float *const *host_w, c
             if (!rc) rc = talloc(c, *T, (void **)&T->vw[l], O * I * 4);
             if (!rc) rc = talloc(c, *T, (void **)&T->mb[l], O * 4);
             if (!rc) rc = talloc(c, *T, (void **)&T->vb[l], O * 4);
-            if (!rc) rc = talloc(c, *T, (void **)&T->gw[l], O * I * 4);
+            // the last layer's gradient has C rounded up to 128 rows (its GEMM's row tile)
+            if (!rc) rc = talloc(c, *T, (void **)&T->gw[l], (l == L - 1 ? (O + 127) / 128 * 128 : O) * I * 4);
             if (!rc) rc = talloc(c, *T, (void **)&T->gb[l], O * 4);
             if (!rc && l >= 1 && l < L - 1) rc = talloc(c, *T, (void **)&T->wt[l], O * I * 2);
             if (!rc && l < L - 1) rc = talloc(c, *T, (void **)&T->act[l], (size_t)Bp * O * 2);
@@ -591,12 +653,20 @@ static int train_setup(Ctx *c, NetGPU &net, int B, const float *const *host_w, c
         if (!rc) rc = talloc(c, *T, (void **)&T->logits, (size_t)Bp * C * 4);
         if (!rc) rc = talloc(c, *T, (void **)&T->dzl, (size_t)Bp * C * 4);
         if (!rc) rc = talloc(c, *T, (void **)&T->row_loss, (size_t)Bp * 4);
-        // partials of every gradient tensor: the hidden dW in row splits (dw_splits), the last
-        // layer's dW in row splits of kDwRows, the biases' column sums in row chunks of kSumRows
+        T->cs = (C + 63) / 64 * 64;
+        if (!rc) rc = talloc(c, *T, (void **)&T->dz_ext, (size_t)Bp * kExtParts * T->cs * 2);
+        if (!rc) rc = talloc(c, *T, (void **)&T->w_ext, (size_t)net.dims[L - 1] * kExtParts * T->cs * 2);
+        T->Mp = (C + 127) / 128 * 128;
+        if (!rc) rc = talloc(c, *T, (void **)&T->t_dz_ext, (size_t)T->Mp * 2 * Bp * 2);
+        if (!rc) rc = talloc(c, *T, (void **)&T->t_a_ext, (size_t)net.dims[L - 1] * 2 * Bp * 2);
+        // partials of every gradient tensor: each layer's dW in row splits (dw_splits; the last
+        // layer's over its 2 Bp stacked columns, Mp rows), the biases' column sums in row chunks
+        // of kSumRows
         for (int l = 0; l < L && !rc; ++l) {
             const size_t O = net.dims[l + 1], I = l == 0 ? k1 : (size_t)net.dims[l];
-            const size_t parts = l < L - 1 ? (size_t)dw_splits(c, (int)O, (int)I, Bp) : (size_t)(Bp + kDwRows - 1) / kDwRows;
-            T->gw_buf_floats[l] = parts * O * I;
+            const size_t Op = l < L - 1 ? O : (O + 127) / 128 * 128;
+            const size_t parts = (size_t)dw_splits(c, (int)Op, (int)I, l < L - 1 ? Bp : 2 * Bp);
+            T->gw_buf_floats[l] = parts * Op * I;
             T->gb_buf_floats[l] = (size_t)((Bp + kSumRows - 1) / kSumRows) * O;
             rc = talloc(c, *T, (void **)&T->gw_buf[l], T->gw_buf_floats[l] * 4);
             if (!rc) rc = talloc(c, *T, (void **)&T->gb_buf[l], T->gb_buf_floats[l] * 4);
@@ -630,11 +700,12 @@ static int train_setup(Ctx *c, NetGPU &net, int B, const float *const *host_w, c
             train_free(c, old);
         }
         net.train = T;
-        // W^T copies of the hidden layers >= 1
+        // W^T copies of the hidden layers >= 1, the last layer's stacked parts
         for (int l = 1; l < L - 1; ++l) {
             const int O = net.dims[l + 1], I = net.dims[l];
             k_write_t<<<(O * I + 255) / 256, 256>>>(T->w[l], O, I, T->wt[l]);
         }
+        k_write_ext<<<(C * net.dims[L - 1] + 255) / 256, 256>>>(T->w[L - 1], C, net.dims[L - 1], T->cs, T->w_ext);
         CUDA_TRY(cudaDeviceSynchronize());
     }
     return CBDFS_OK;
@@ -701,36 +772,60 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
         k_fgemm<__nv_bfloat16, float, true, false, 1><<<dim3((C + FG_T - 1) / FG_T, (n + FG_T - 1) / FG_T, 1), blk, 0, st>>>(
             T.act[L - 2], KL, 1, T.w[L - 1], 1, KL, n, C, KL, KL, T.logits, T.b[L - 1], nullptr, 0, nullptr);
     }
-    k_loss<<<(n + 7) / 8, 256, 0, st>>>(T.logits, T.labels, n, C, loss_kind, T.dzl, T.row_loss);
+    k_loss<<<(Bp + 7) / 8, 256, 0, st>>>(T.logits, T.labels, n, Bp, C, loss_kind, T.dzl, T.row_loss, T.dz_ext, T.cs);
     k_mean<<<1, 256, 0, st>>>(T.row_loss, n, T.loss);
-    // last layer backward (FP32): dW[c][k] = sum_m dZ[m][c] A[m][k] in row splits, then the
-    // splits in order; db = column sums of dZ; dZ_prev = (dZ W) * [A > 0] in BF16
-    const int sdw = (n + kDwRows - 1) / kDwRows;
-    k_fgemm<float, __nv_bfloat16, false, true, 0><<<dim3((KL + FG_T - 1) / FG_T, (C + FG_T - 1) / FG_T, sdw), blk, 0, st>>>(
-        T.dzl, 1, C, T.act[L - 2], KL, 1, C, KL, n, kDwRows, T.gw_buf[L - 1], nullptr, nullptr, 0, nullptr);
-    if (sum) k_sum_splits<<<(C * KL + 255) / 256, 256, 0, st>>>(T.gw_buf[L - 1], sdw, C * KL, T.gw[L - 1]);
-    T.gw_src[L - 1] = sum ? T.gw[L - 1] : T.gw_buf[L - 1];
-    T.gw_parts[L - 1] = sum ? 1 : sdw;
+    // last layer backward: dW[c][k] = sum_m dZ[m][c] A[m][k] with dZ = D1 + D2 (BF16 parts, the
+    // products exact, FP32 accumulation) as one split-K tensor-core GEMM over 2 Bp columns;
+    // db = column sums of dZ; dZ_prev = (dZ W) * [A > 0] in BF16
+    {
+        const int Kd = 2 * Bp;
+        k_transpose<<<dim3(T.cs / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.dz_ext, T.t_dz_ext, Bp, T.cs,
+                                                                      kExtParts * T.cs, Kd, nullptr);
+        k_transpose<<<dim3(T.cs / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.dz_ext + 3 * T.cs, T.t_dz_ext + Bp, Bp, T.cs,
+                                                                      kExtParts * T.cs, Kd, nullptr);
+        k_transpose<<<dim3(KL / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.act[L - 2], T.t_a_ext, Bp, KL, KL, Kd,
+                                                                    T.t_a_ext + Bp);
+        const CUtensorMap *ma = bmap(T, T.t_dz_ext, Kd, T.Mp, kBM);
+        const CUtensorMap *mb = bmap(T, T.t_a_ext, Kd, KL, KL % 256 == 0 ? 256 : 128);
+        if (!ma || !mb) return CBDFS_EDEVICE;
+        const int S = dw_splits(c, T.Mp, KL, Kd);
+        if ((size_t)S * T.Mp * KL > T.gw_buf_floats[L - 1]) return fail(CBDFS_EINVAL, "dW scratch");
+        rc = KL % 256 == 0 ? gemm_tn<256, 1>(*ma, *mb, T.Mp, KL, Kd, T.gw[L - 1], nullptr, c->d_err, st, S, T.gw_buf[L - 1], sum)
+                           : gemm_tn<128, 1>(*ma, *mb, T.Mp, KL, Kd, T.gw[L - 1], nullptr, c->d_err, st, S, T.gw_buf[L - 1], sum);
+        if (rc) return rc;
+        T.gw_src[L - 1] = S > 1 && !sum ? T.gw_buf[L - 1] : T.gw[L - 1];
+        T.gw_parts[L - 1] = S > 1 && !sum ? S : 1;
+        T.gw_pstride[L - 1] = (size_t)T.Mp * KL;
+    }
     {
         int parts = 0;
         if (int r = colsum(T.dzl, n, C, T.gb_buf[L - 1], T.gb_buf_floats[L - 1], T.gb[L - 1], sum, &parts, st)) return r;
         T.gb_src[L - 1] = sum ? T.gb[L - 1] : T.gb_buf[L - 1];
         T.gb_parts[L - 1] = sum ? 1 : parts;
     }
-    k_fgemm<float, float, true, true, 2><<<dim3((KL + FG_T - 1) / FG_T, Bp / FG_T, 1), blk, 0, st>>>(
-        T.dzl, C, 1, T.w[L - 1], KL, 1, Bp, KL, C, C, nullptr, nullptr, T.act[L - 2], n, T.dz[L - 2]);
+    {
+        // dZ_{L-2} = (dZ_L W_L) * [A_{L-2} > 0]: the split parts on the tensor cores (rows n..Bp-1
+        // of dz_ext are zero, so those rows of the product are zero)
+        const int Ke = kExtParts * T.cs;
+        const CUtensorMap *mz = bmap(T, T.dz_ext, Ke, T.Bp, kBM);
+        const CUtensorMap *mw = bmap(T, T.w_ext, Ke, KL, KL % 256 == 0 ? 256 : 128);
+        if (!mz || !mw) return CBDFS_EDEVICE;
+        rc = KL % 256 == 0 ? gemm_tn<256, 2>(*mz, *mw, Bp, KL, Ke, T.dz[L - 2], T.act[L - 2], c->d_err, st)
+                           : gemm_tn<128, 2>(*mz, *mw, Bp, KL, Ke, T.dz[L - 2], T.act[L - 2], c->d_err, st);
+        if (rc) return rc;
+    }
     // hidden layers, last to first
     for (int l = L - 2; l >= 0; --l) {
         const int O = net.dims[l + 1], I = l == 0 ? net.k1pad : net.dims[l];
         // dW_l = dZ_l^T A_{l-1}: transpose both to K-major over the batch
-        k_transpose<<<dim3(O / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.dz[l], T.t_dz, Bp, O);
+        k_transpose<<<dim3(O / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.dz[l], T.t_dz, Bp, O, O, Bp, nullptr);
         if (l == 0) {
             CUDA_TRY(cudaMemsetAsync(T.t_a, 0, (size_t)I * Bp * 2, st));
             if (net.domain == CBDFS_DOM_STP3) k_onehot_t<CBDFS_DOM_STP3><<<(Bp + 255) / 256, 256, 0, st>>>(T.states, n, Bp, T.t_a);
             else if (net.domain == CBDFS_DOM_STP4) k_onehot_t<CBDFS_DOM_STP4><<<(Bp + 255) / 256, 256, 0, st>>>(T.states, n, Bp, T.t_a);
             else k_onehot_t<CBDFS_DOM_RC3><<<(Bp + 255) / 256, 256, 0, st>>>(T.states, n, Bp, T.t_a);
         } else {
-            k_transpose<<<dim3(I / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.act[l - 1], T.t_a, Bp, I);
+            k_transpose<<<dim3(I / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.act[l - 1], T.t_a, Bp, I, I, Bp, nullptr);
         }
         // the output width is the (padded) input width; padding columns of the one-hot are
         // zero, so their gradient is exactly zero
@@ -744,6 +839,7 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
         if (rc) return rc;
         T.gw_src[l] = S > 1 && !sum ? T.gw_buf[l] : T.gw[l];
         T.gw_parts[l] = S > 1 && !sum ? S : 1;
+        T.gw_pstride[l] = (size_t)O * I;
         {
             int parts = 0;
             if (int r = colsum(T.dz[l], n, O, T.gb_buf[l], T.gb_buf_floats[l], T.gb[l], sum, &parts, st)) return r;
@@ -788,6 +884,7 @@ static int train_update(Ctx *c, NetGPU &net, const cbdfs_train_cfg &tc, cudaStre
         w.w = T.w[l];
         w.g = T.gw_src[l];
         w.parts = T.gw_parts[l];
+        w.pstride = T.gw_pstride[l];
         w.m = T.mw[l];
         w.v = T.vw[l];
         w.O = O;
@@ -798,11 +895,14 @@ static int train_update(Ctx *c, NetGPU &net, const cbdfs_train_cfg &tc, cudaStre
         w.w_out = last ? net.w32[l] : nullptr;  // the inference head reads the FP32 last layer
         w.split = last ? static_cast<__nv_bfloat16 *>(net.w_split) : nullptr;  // and the tensor-core head its parts
         w.cpad = net.head_cpad;
+        w.w_ext = last ? T.w_ext : nullptr;  // and the backward its stacked parts
+        w.cs = T.cs;
         add(w);
         AdamSeg b{};
         b.w = T.b[l];
         b.g = T.gb_src[l];
         b.parts = T.gb_parts[l];
+        b.pstride = O;
         b.m = T.mb[l];
         b.v = T.vb[l];
         b.O = O;
