@@ -196,7 +196,7 @@ int gemm_tn(const CUtensorMap &tmA, const CUtensorMap &tmB, int M, int N, int K,
 // rows (65 elements) keep the column reads on distinct banks.  Block (32, 8).
 __global__ void __launch_bounds__(256) k_transpose(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ out,
                                                    int R, int C, int ldi, int ldo,
-                                                   __nv_bfloat16 *__restrict__ out2) {
+                                                   __nv_bfloat16 *__restrict__ out2, float *__restrict__ colsum) {
     __shared__ __nv_bfloat16 t[64][65];
     const int c0 = blockIdx.x * 64, r0 = blockIdx.y * 64, tx = threadIdx.x;
     for (int i = threadIdx.y; i < 64; i += 8) {
@@ -211,6 +211,15 @@ __global__ void __launch_bounds__(256) k_transpose(const __nv_bfloat16 *__restri
         v.y = t[2 * tx + 1][j];
         *reinterpret_cast<__nv_bfloat162 *>(out + (size_t)(c0 + j) * ldo + r0 + 2 * tx) = v;
         if (out2) *reinterpret_cast<__nv_bfloat162 *>(out2 + (size_t)(c0 + j) * ldo + r0 + 2 * tx) = v;
+    }
+    // the tile's column sums over its 64 rows, in row order: the row-chunk partials of the
+    // bias gradient (chunk r0 / 64)
+    static_assert(kSumRows == 64, "a bias-gradient chunk is one transpose tile");
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    if (colsum && tid < 64) {
+        float sum = 0.f;
+        for (int i = 0; i < 64; ++i) sum += __bfloat162float(t[i][tid]);
+        colsum[(size_t)blockIdx.y * C + c0 + tid] = sum;
     }
 }
 
@@ -780,11 +789,11 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
     {
         const int Kd = 2 * Bp;
         k_transpose<<<dim3(T.cs / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.dz_ext, T.t_dz_ext, Bp, T.cs,
-                                                                      kExtParts * T.cs, Kd, nullptr);
+                                                                      kExtParts * T.cs, Kd, nullptr, nullptr);
         k_transpose<<<dim3(T.cs / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.dz_ext + 3 * T.cs, T.t_dz_ext + Bp, Bp, T.cs,
-                                                                      kExtParts * T.cs, Kd, nullptr);
+                                                                      kExtParts * T.cs, Kd, nullptr, nullptr);
         k_transpose<<<dim3(KL / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.act[L - 2], T.t_a_ext, Bp, KL, KL, Kd,
-                                                                    T.t_a_ext + Bp);
+                                                                    T.t_a_ext + Bp, nullptr);
         const CUtensorMap *ma = bmap(T, T.t_dz_ext, Kd, T.Mp, kBM);
         const CUtensorMap *mb = bmap(T, T.t_a_ext, Kd, KL, KL % 256 == 0 ? 256 : 128);
         if (!ma || !mb) return CBDFS_EDEVICE;
@@ -818,14 +827,15 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
     for (int l = L - 2; l >= 0; --l) {
         const int O = net.dims[l + 1], I = l == 0 ? net.k1pad : net.dims[l];
         // dW_l = dZ_l^T A_{l-1}: transpose both to K-major over the batch
-        k_transpose<<<dim3(O / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.dz[l], T.t_dz, Bp, O, O, Bp, nullptr);
+        // (and db_l's row-chunk partials: the column sums of each 64-row tile)
+        k_transpose<<<dim3(O / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.dz[l], T.t_dz, Bp, O, O, Bp, nullptr, T.gb_buf[l]);
         if (l == 0) {
             CUDA_TRY(cudaMemsetAsync(T.t_a, 0, (size_t)I * Bp * 2, st));
             if (net.domain == CBDFS_DOM_STP3) k_onehot_t<CBDFS_DOM_STP3><<<(Bp + 255) / 256, 256, 0, st>>>(T.states, n, Bp, T.t_a);
             else if (net.domain == CBDFS_DOM_STP4) k_onehot_t<CBDFS_DOM_STP4><<<(Bp + 255) / 256, 256, 0, st>>>(T.states, n, Bp, T.t_a);
             else k_onehot_t<CBDFS_DOM_RC3><<<(Bp + 255) / 256, 256, 0, st>>>(T.states, n, Bp, T.t_a);
         } else {
-            k_transpose<<<dim3(I / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.act[l - 1], T.t_a, Bp, I, I, Bp, nullptr);
+            k_transpose<<<dim3(I / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.act[l - 1], T.t_a, Bp, I, I, Bp, nullptr, nullptr);
         }
         // the output width is the (padded) input width; padding columns of the one-hot are
         // zero, so their gradient is exactly zero
@@ -841,10 +851,11 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
         T.gw_parts[l] = S > 1 && !sum ? S : 1;
         T.gw_pstride[l] = (size_t)O * I;
         {
-            int parts = 0;
-            if (int r = colsum(T.dz[l], n, O, T.gb_buf[l], T.gb_buf_floats[l], T.gb[l], sum, &parts, st)) return r;
+            // db_l: the transpose's row-chunk partials (rows n..Bp-1 of dZ_l are zero)
+            const int R = Bp / kSumRows;
+            if (sum) k_sum_splits<<<(O + 255) / 256, 256, 0, st>>>(T.gb_buf[l], R, O, T.gb[l]);
             T.gb_src[l] = sum ? T.gb[l] : T.gb_buf[l];
-            T.gb_parts[l] = sum ? 1 : parts;
+            T.gb_parts[l] = sum ? 1 : R;
         }
         if (l > 0) {
             // dZ_{l-1} = (dZ_l W_l) * [A_{l-1} > 0]
