@@ -321,26 +321,23 @@ __global__ void k_loss(const float *__restrict__ logits, const uint8_t *__restri
     }
 }
 
-// ---- FP32 GEMM on the CUDA cores (the last layer's products) ----------------------------
-// out[z][m][n] = sum over k in split z of A(m,k) B(k,n), FP32: A(m,k) = A[m*sam + k*sak],
+// ---- FP32 GEMM on the CUDA cores (the logits of a network without split last-layer weights) --
+// out[m][n] = sum over k of A(m,k) B(k,n) + bias[n], FP32: A(m,k) = A[m*sam + k*sak],
 // B(k,n) = B[k*sbk + n*sbn].  64x64 tiles, k-steps of 16, 256 threads each owning a 4x4 block.
 // AK: A is contiguous along k (else along m); BNC: B is contiguous along n (else along k).
-// EPI 0: write split z's partial sums; 1: write + bias[n] (one split); 2: write BF16
-// acc * [mask[m][n] > 0], zero for rows m >= nvalid (one split).
 constexpr int FG_T = 64, FG_BK = 16;
 __device__ __forceinline__ float tof(float x) { return x; }
 __device__ __forceinline__ float tof(__nv_bfloat16 x) { return __bfloat162float(x); }
 
-template <typename TA, typename TB, bool AK, bool BNC, int EPI>
+template <typename TA, typename TB, bool AK, bool BNC>
 __global__ void __launch_bounds__(256)
 k_fgemm(const TA *__restrict__ A, long sam, long sak, const TB *__restrict__ B, long sbk, long sbn, int M,
-        int N, int K, int kchunk, float *__restrict__ out, const float *__restrict__ bias,
-        const __nv_bfloat16 *__restrict__ mask, int nvalid, __nv_bfloat16 *__restrict__ out16) {
+        int N, int K, float *__restrict__ out, const float *__restrict__ bias) {
     __shared__ __align__(16) float As[FG_BK][FG_T];
     __shared__ __align__(16) float Bs[FG_BK][FG_T];
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     const int m0 = blockIdx.y * FG_T, n0 = blockIdx.x * FG_T;
-    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    const int kb = 0, ke = K;
     float acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -377,10 +374,7 @@ k_fgemm(const TA *__restrict__ A, long sam, long sak, const TB *__restrict__ B, 
         for (int j = 0; j < 4; ++j) {
             const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
             if (m >= M || n >= N) continue;
-            const size_t o = (size_t)m * N + n;
-            if (EPI == 0) out[(size_t)blockIdx.z * M * N + o] = acc[i][j];
-            else if (EPI == 1) out[o] = acc[i][j] + bias[n];
-            else out16[o] = __float2bfloat16(m < nvalid && __bfloat162float(mask[o]) > 0.f ? acc[i][j] : 0.f);
+            out[(size_t)m * N + n] = acc[i][j] + bias[n];
         }
 }
 
@@ -778,8 +772,8 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
         H.groups = 1;
         if (int r = head_tc(net.domain, *ma, net.tm_wsplit, H, Bp, st)) return r;
     } else {
-        k_fgemm<__nv_bfloat16, float, true, false, 1><<<dim3((C + FG_T - 1) / FG_T, (n + FG_T - 1) / FG_T, 1), blk, 0, st>>>(
-            T.act[L - 2], KL, 1, T.w[L - 1], 1, KL, n, C, KL, KL, T.logits, T.b[L - 1], nullptr, 0, nullptr);
+        k_fgemm<__nv_bfloat16, float, true, false><<<dim3((C + FG_T - 1) / FG_T, (n + FG_T - 1) / FG_T, 1), blk, 0, st>>>(
+            T.act[L - 2], KL, 1, T.w[L - 1], 1, KL, n, C, KL, T.logits, T.b[L - 1]);
     }
     k_loss<<<(Bp + 7) / 8, 256, 0, st>>>(T.logits, T.labels, n, Bp, C, loss_kind, T.dzl, T.row_loss, T.dz_ext, T.cs);
     k_mean<<<1, 256, 0, st>>>(T.row_loss, n, T.loss);
