@@ -124,6 +124,27 @@ def test_c0_fp32_regression(P, ctx, orc, n):
     _check_bound(orc, h, g, 30, mask, minf)
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+@pytest.mark.parametrize("n", [1, 31, 129, 2000])
+def test_c0_chain_8puzzle(P, ctx, orc, prec, n):
+    # the 8-puzzle network 81-256-256-1 in the fused chain (the one-hot rows 81 wide, padded to
+    # 128; 16-row pre-pass units), against the oracle on the same rounded weights
+    Ws, bs = W.net_weights(**W.NET_C0)
+    kw = {}
+    if prec == "fp8":
+        kw["act_scales"] = fp8_act_scales(orc, 0, Ws, bs, W.random_stp_states(3, 4096, 12))
+    hid = P.cbdfs_net_load(ctx, P.DOM_STP3, Ws, bs, PREC[prec], P.HEAD_REGRESSION, 1, **kw)
+    s = W.random_stp_states(3, n, 45 + n)
+    s[0] = W.stp_goal(3)
+    g = _g(n, n + 7)
+    h, mask, minf, y = P.heur_submit_batch(ctx, hid, P.DOM_STP3, s, g, 30, want_y=True)
+    y64, h64, margin = oracle_net(orc, 0, Ws, bs, prec, s, "regression", True, **kw)
+    check_logits(y, y64, prec)
+    check_h(h, h64, margin)
+    assert h[0] == 0
+    _check_bound(orc, h, g, 30, mask, minf)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("n", [1, 127, 129, 1000])
 def test_c1_regression(P, ctx, orc, prec, n):
