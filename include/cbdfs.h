@@ -43,7 +43,7 @@ typedef enum {
     CBDFS_ETIMEDOUT = -3,   /* a bounded wait (host or device) ran out */
     CBDFS_EDEVICE = -4,     /* a CUDA call failed; the message names it */
     CBDFS_ECANCELED = -5,   /* cbdfs_cancel() stopped the call */
-    CBDFS_ENOTFOUND = -6    /* the search space holds no solution within the limits */
+    CBDFS_ENOTFOUND = -6    /* no solution within the limits; a file that does not exist */
 } cbdfs_status;
 
 typedef enum { CBDFS_DOM_STP3 = 0, CBDFS_DOM_STP4 = 1, CBDFS_DOM_RC3 = 2 } cbdfs_domain;
@@ -166,6 +166,21 @@ int cbdfs_pdb_load(cbdfs_ctx *ctx, const cbdfs_pdb_desc *d, int *heur_id);
  * Errors: EINVAL (cap too small, bad tiles), ENOMEM, EDEVICE. */
 int pdb_build(cbdfs_ctx *ctx, int domain, const int *pattern_tiles, int k, uint8_t *table_out,
               size_t cap, size_t *entries);
+
+/* PDB table files (the tables are built offline and reused): a 128-byte header, then the
+ * table bytes.  Header, little-endian: "CBDFSPDB" (8 bytes), format version 1 (uint32),
+ * domain (int32), k (int32), the pattern's tiles (16 x int32, unused ones 0), the DIV factor
+ * (uint32; 1 = a full table), the entry count (uint64), the FNV-1a 64-bit hash of the table
+ * bytes (uint64), zero padding.  Host-only calls: no context, no GPU.
+ * cbdfs_pdb_file_write writes `entries` bytes of `table`.  Errors: EINVAL (arguments),
+ * EDEVICE (the file could not be written).
+ * cbdfs_pdb_file_read fills the header fields (tiles: 16 ints) and *entries; with table
+ * non-NULL it also reads the bytes (cap >= entries) and checks the hash.  Errors: EINVAL (not
+ * such a file, version, cap too small, hash mismatch, short file), ENOTFOUND (no file). */
+int cbdfs_pdb_file_write(const char *path, int domain, const int *tiles, int k, uint32_t div,
+                         const uint8_t *table, uint64_t entries);
+int cbdfs_pdb_file_read(const char *path, int *domain, int *tiles, int *k, uint32_t *div,
+                        uint8_t *table, uint64_t cap, uint64_t *entries);
 
 /* ---------------------------------------------------------------------------------------
  * Composite heuristic (Related Work: the minimum over an ensemble of networks keeps a
@@ -397,6 +412,20 @@ int cbdfs_train_grad(cbdfs_ctx *ctx, int heur_id, const uint64_t *states, const 
 /* The network's FP32 weights (the training masters once trained), host buffers as in
  * cbdfs_net_desc. */
 int cbdfs_net_read(cbdfs_ctx *ctx, int heur_id, float *const *w_out, float *const *b_out);
+
+/* Training checkpoints: the network's training state (FP32 master weights and biases, Adam's
+ * first and second moments, the step count that drives Adam's bias correction) to a file,
+ * and back.  After cbdfs_train_load the heuristic evaluates the loaded masters (its BF16
+ * weights and FP32 last layer are rewritten) and net_train continues from the loaded state,
+ * exactly as if it had not stopped (same data and seed: the same weights).  File: "CBDFSTRN"
+ * (8 bytes), version 1 (uint32), L (uint32), dims[0..8] (uint32, unused 0), the padded
+ * one-hot width (uint32), the step (int64), the payload bytes (uint64), the FNV-1a 64-bit
+ * hash of the payload (uint64); then per layer l: W_l [dims[l+1]][K_l], b_l, m(W_l), v(W_l),
+ * m(b_l), v(b_l), FP32, K_0 the padded one-hot width, K_l = dims[l] otherwise.
+ * Errors: EINVAL (not a BF16 network, another shape, not such a file, hash mismatch, a
+ * server is running), ENOTFOUND (no file), EDEVICE (I/O or device), ENOMEM. */
+int cbdfs_train_save(cbdfs_ctx *ctx, int heur_id, const char *path);
+int cbdfs_train_load(cbdfs_ctx *ctx, int heur_id, const char *path);
 
 /* n sliding-tile states from random walks of the blank from the goal, walk i = first..:
  * its splitmix64 stream starts at mix((tag << 32) | (i mod 2^32)); the walk's length is

@@ -167,6 +167,13 @@ _lib.net_train.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_uint64, ctypes.
 _lib.cbdfs_train_grad.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_uint32, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_float), _FPP, _FPP]
 _lib.cbdfs_net_read.argtypes = [_vp, ctypes.c_int, _FPP, _FPP]
+_lib.cbdfs_train_save.argtypes = [_vp, ctypes.c_int, ctypes.c_char_p]
+_lib.cbdfs_train_load.argtypes = [_vp, ctypes.c_int, ctypes.c_char_p]
+_IP = ctypes.POINTER(ctypes.c_int)
+_lib.cbdfs_pdb_file_write.argtypes = [ctypes.c_char_p, ctypes.c_int, _IP, ctypes.c_int, ctypes.c_uint32, _vp,
+                                      ctypes.c_uint64]
+_lib.cbdfs_pdb_file_read.argtypes = [ctypes.c_char_p, _IP, _IP, _IP, ctypes.POINTER(ctypes.c_uint32), _vp,
+                                     ctypes.c_uint64, _u64p]
 _lib.cbdfs_gen_walk_states.argtypes = [_vp, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64,
                                        ctypes.c_uint64, ctypes.c_int, _vp]
 _lib.cbdfs_server_start.argtypes = [_vp, ctypes.POINTER(ServerCfg)]
@@ -191,7 +198,8 @@ EXPORTED = ["cbdfs_create", "cbdfs_destroy", "cbdfs_last_error", "cbdfs_mem_used
             "heur_submit_batch_real", "heur_eval_device_real", "heur_eval_device_static",
             "heur_submit_batch_async", "heur_wait",
             "cbdfs_device_status", "cbdfs_eval_profile", "cbdfs_eval_trace", "net_train",
-            "cbdfs_train_grad", "cbdfs_net_read", "cbdfs_gen_walk_states", "cbdfs_server_start",
+            "cbdfs_train_grad", "cbdfs_net_read", "cbdfs_train_save", "cbdfs_train_load",
+            "cbdfs_pdb_file_write", "cbdfs_pdb_file_read", "cbdfs_gen_walk_states", "cbdfs_server_start",
             "cbdfs_server_stop", "heur_request_submit", "heur_request_wait", "cbdfs_server_get_stats", "cbdfs_apply_moves", "cbdfs_manhattan", "cbdfs_solve",
             "cbdfs_search_defaults", "cbdfs_cancel"]
 
@@ -441,6 +449,38 @@ def cbdfs_train_grad(ctx, heur_id, states, labels, dims, loss=LOSS_CE):
     _check(_lib.cbdfs_train_grad(ctx, heur_id, _ptr(states), _ptr(labels), len(labels), loss,
                                  ctypes.byref(out), _float_ptrs(gw), _float_ptrs(gb)))
     return out.value, gw, gb
+
+
+def cbdfs_train_save(ctx, heur_id, path):
+    """The network's training state (masters, Adam moments, step) to a checkpoint file."""
+    _check(_lib.cbdfs_train_save(ctx, heur_id, os.fsencode(path)))
+
+
+def cbdfs_train_load(ctx, heur_id, path):
+    """A checkpoint back into the network: net_train continues from it."""
+    _check(_lib.cbdfs_train_load(ctx, heur_id, os.fsencode(path)))
+
+
+def cbdfs_pdb_file_write(path, domain, tiles, table, div=1):
+    """One pattern's table (uint8) to a PDB file with its pattern and hash."""
+    tiles = [int(t) for t in tiles]
+    table = np.ascontiguousarray(table, dtype=np.uint8)
+    _check(_lib.cbdfs_pdb_file_write(os.fsencode(path), domain, (ctypes.c_int * len(tiles))(*tiles), len(tiles),
+                                     div, _ptr(table), len(table)))
+
+
+def cbdfs_pdb_file_read(path):
+    """(domain, tiles, div, table) of a PDB file; the table's hash is checked."""
+    dom, k, div = ctypes.c_int(), ctypes.c_int(), ctypes.c_uint32()
+    tiles = (ctypes.c_int * 16)()
+    entries = ctypes.c_uint64()
+    p = os.fsencode(path)
+    _check(_lib.cbdfs_pdb_file_read(p, ctypes.byref(dom), tiles, ctypes.byref(k), ctypes.byref(div), None, 0,
+                                    ctypes.byref(entries)))
+    table = np.empty(entries.value, dtype=np.uint8)
+    _check(_lib.cbdfs_pdb_file_read(p, ctypes.byref(dom), tiles, ctypes.byref(k), ctypes.byref(div), _ptr(table),
+                                    len(table), ctypes.byref(entries)))
+    return dom.value, list(tiles[:k.value]), div.value, table
 
 
 def cbdfs_net_read(ctx, heur_id, dims):

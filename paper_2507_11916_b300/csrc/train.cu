@@ -20,8 +20,10 @@
 //             inference layout), W_l^T and the last layer's parts rewritten by the same kernel
 // Every reduction has a fixed order, so a step is deterministic.
 #include <algorithm>
+#include <cerrno>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <random>
 #include <type_traits>
@@ -30,6 +32,7 @@
 
 namespace cbdfs {
 
+uint64_t fnv1a64(const void *data, size_t n, uint64_t h);  // files.cpp
 int tc_layer(bool first, int domain, bool fp8, bool out_fp8, int bn, const CUtensorMap &tmA,
              const CUtensorMap &tmB, const uint64_t *states, uint32_t n, uint32_t rows_pad, int K,
              int N, const float *bias, void *out, float acc_scale, float out_qscale, int *err,
@@ -458,6 +461,7 @@ struct AdamSeg {
 struct AdamParams {
     AdamSeg seg[2 * kMaxLayers];
     int nseg;
+    int copies_only;  // no update: only the copies of the masters as they are (a loaded checkpoint)
     float lr, b1, b2, eps, c1, c2;
 };
 
@@ -467,15 +471,18 @@ __global__ void __launch_bounds__(256) k_adam_all(const __grid_constant__ AdamPa
     const AdamSeg &S = P.seg[s];
     const int idx = ((int)blockIdx.x - S.block0) * blockDim.x + threadIdx.x;
     if (idx >= S.O * S.I) return;
-    float gg = 0.f;
-    for (int z = 0; z < S.parts; ++z) gg += S.g[z * S.pstride + idx];
-    const float m = P.b1 * S.m[idx] + (1.f - P.b1) * gg;
-    const float v = P.b2 * S.v[idx] + (1.f - P.b2) * gg * gg;
-    S.m[idx] = m;
-    S.v[idx] = v;
-    const float mh = m / P.c1, vh = v / P.c2;
-    const float nw = S.w[idx] - P.lr * mh / (sqrtf(vh) + P.eps);
-    S.w[idx] = nw;
+    float nw = S.w[idx];
+    if (!P.copies_only) {
+        float gg = 0.f;
+        for (int z = 0; z < S.parts; ++z) gg += S.g[z * S.pstride + idx];
+        const float m = P.b1 * S.m[idx] + (1.f - P.b1) * gg;
+        const float v = P.b2 * S.v[idx] + (1.f - P.b2) * gg * gg;
+        S.m[idx] = m;
+        S.v[idx] = v;
+        const float mh = m / P.c1, vh = v / P.c2;
+        nw = S.w[idx] - P.lr * mh / (sqrtf(vh) + P.eps);
+        S.w[idx] = nw;
+    }
     const int o = idx / S.I, i = idx % S.I;
     if (S.w_lp) S.w_lp[(size_t)o * S.Kp + i] = __float2bfloat16(nw);
     if (S.wt) S.wt[(size_t)i * S.O + o] = __float2bfloat16(nw);
@@ -865,16 +872,19 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
     return CBDFS_OK;
 }
 
-static int train_update(Ctx *c, NetGPU &net, const cbdfs_train_cfg &tc, cudaStream_t st) {
+// one Adam launch over every tensor (copies_only: no update, the copies of the masters)
+static int launch_adam(NetGPU &net, const cbdfs_train_cfg *tc, bool copies_only, cudaStream_t st) {
     TrainState &T = *net.train;
-    T.step++;
     AdamParams A{};
-    A.lr = tc.lr;
-    A.b1 = tc.beta1;
-    A.b2 = tc.beta2;
-    A.eps = tc.eps;
-    A.c1 = 1.f - powf(tc.beta1, (float)T.step);
-    A.c2 = 1.f - powf(tc.beta2, (float)T.step);
+    A.copies_only = copies_only ? 1 : 0;
+    if (tc) {
+        A.lr = tc->lr;
+        A.b1 = tc->beta1;
+        A.b2 = tc->beta2;
+        A.eps = tc->eps;
+        A.c1 = 1.f - powf(tc->beta1, (float)T.step);
+        A.c2 = 1.f - powf(tc->beta2, (float)T.step);
+    }
     int blocks = 0;
     auto add = [&](const AdamSeg &g) {
         A.seg[A.nseg] = g;
@@ -919,6 +929,57 @@ static int train_update(Ctx *c, NetGPU &net, const cbdfs_train_cfg &tc, cudaStre
     CUDA_TRY(cudaGetLastError());
     return CBDFS_OK;
 }
+
+static int train_update(Ctx *, NetGPU &net, const cbdfs_train_cfg &tc, cudaStream_t st) {
+    net.train->step++;
+    return launch_adam(net, &tc, false, st);
+}
+
+
+// ---- training checkpoints ---------------------------------------------------------------
+namespace {
+
+struct TrainFileHeader {
+    char magic[8];
+    uint32_t version, L;
+    uint32_t dims[kMaxLayers + 1];
+    uint32_t k1pad;
+    int64_t step;
+    uint64_t payload, hash;
+};
+constexpr char kTrainMagic[8] = {'C', 'B', 'D', 'F', 'S', 'T', 'R', 'N'};
+constexpr uint64_t kFnvBasis = 14695981039346656037ull;
+
+// layer l's six FP32 tensors in file order: W, b, m(W), v(W), m(b), v(b)
+void layer_tensors(TrainState &T, const NetGPU &net, int l, float *(&p)[6], size_t (&cnt)[6]) {
+    const size_t O = net.dims[l + 1], I = l == 0 ? (size_t)net.k1pad : (size_t)net.dims[l];
+    float *pp[6] = {T.w[l], T.b[l], T.mw[l], T.vw[l], T.mb[l], T.vb[l]};
+    const size_t cc[6] = {O * I, O, O * I, O * I, O, O};
+    for (int i = 0; i < 6; ++i) {
+        p[i] = pp[i];
+        cnt[i] = cc[i];
+    }
+}
+
+// the training state, created from the loaded weights if the network has not been trained
+int ensure_train_state(Ctx *c, NetGPU &net) {
+    if (net.train) return CBDFS_OK;
+    std::vector<const float *> hw, hb;
+    for (int l = 0; l < net.L; ++l) {
+        hw.push_back(net.host_w[l].data());
+        hb.push_back(net.host_b[l].data());
+    }
+    return train_setup(c, net, (int)std::min<uint32_t>(c->max_batch, 8192), hw.data(), hb.data());
+}
+
+struct FileCloser {
+    FILE *f = nullptr;
+    ~FileCloser() {
+        if (f) fclose(f);
+    }
+};
+
+}  // namespace
 
 }  // namespace cbdfs
 
@@ -1140,6 +1201,101 @@ int cbdfs_gen_walk_states(cbdfs_ctx *ctx, int domain, uint32_t tag, uint64_t fir
     }
     dev_free(c, d, std::min(n, chunk) * 8);
     return rc;
+}
+
+
+int cbdfs_train_save(cbdfs_ctx *ctx, int net_id, const char *path) {
+    NetGPU *net;
+    int rc = get_train_net(ctx, net_id, &net);
+    if (rc) return rc;
+    if (!path) return fail(CBDFS_EINVAL, "null argument");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    CUDA_TRY(cudaSetDevice(c->device));
+    std::lock_guard<std::mutex> lk(c->device_call_mu);
+    if ((rc = ensure_train_state(c, *net))) return rc;
+    CUDA_TRY(cudaDeviceSynchronize());
+    TrainState &T = *net->train;
+    std::vector<unsigned char> payload;
+    for (int l = 0; l < net->L; ++l) {
+        float *p[6];
+        size_t cnt[6];
+        layer_tensors(T, *net, l, p, cnt);
+        for (int i = 0; i < 6; ++i) {
+            const size_t off = payload.size();
+            payload.resize(off + cnt[i] * 4);
+            CUDA_TRY(cudaMemcpy(payload.data() + off, p[i], cnt[i] * 4, cudaMemcpyDeviceToHost));
+        }
+    }
+    TrainFileHeader hd;
+    std::memset(&hd, 0, sizeof hd);
+    std::memcpy(hd.magic, kTrainMagic, 8);
+    hd.version = 1;
+    hd.L = (uint32_t)net->L;
+    for (int l = 0; l <= net->L; ++l) hd.dims[l] = (uint32_t)net->dims[l];
+    hd.k1pad = (uint32_t)net->k1pad;
+    hd.step = T.step;
+    hd.payload = payload.size();
+    hd.hash = fnv1a64(payload.data(), payload.size(), kFnvBasis);
+    FileCloser out;
+    out.f = fopen(path, "wb");
+    if (!out.f) return fail(CBDFS_EDEVICE, "%s: %s", path, strerror(errno));
+    if (fwrite(&hd, sizeof hd, 1, out.f) != 1 || fwrite(payload.data(), 1, payload.size(), out.f) != payload.size())
+        return fail(CBDFS_EDEVICE, "%s: short write", path);
+    const int closed = fclose(out.f);
+    out.f = nullptr;
+    return closed == 0 ? CBDFS_OK : fail(CBDFS_EDEVICE, "%s: close", path);
+}
+
+int cbdfs_train_load(cbdfs_ctx *ctx, int net_id, const char *path) {
+    NetGPU *net;
+    int rc = get_train_net(ctx, net_id, &net);
+    if (rc) return rc;
+    if (!path) return fail(CBDFS_EINVAL, "null argument");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    // the server's launches read the weights this rewrites
+    if (c->server) return fail(CBDFS_EINVAL, "stop the server before loading a checkpoint");
+    if (net->prec != CBDFS_PREC_BF16) return fail(CBDFS_EINVAL, "training needs a BF16 network");
+    FileCloser in;
+    in.f = fopen(path, "rb");
+    if (!in.f) return fail(CBDFS_ENOTFOUND, "%s: %s", path, strerror(errno));
+    TrainFileHeader hd;
+    if (fread(&hd, sizeof hd, 1, in.f) != 1 || std::memcmp(hd.magic, kTrainMagic, 8) != 0)
+        return fail(CBDFS_EINVAL, "%s is not a training checkpoint", path);
+    if (hd.version != 1) return fail(CBDFS_EINVAL, "%s: format version %u", path, hd.version);
+    bool same = hd.L == (uint32_t)net->L && hd.k1pad == (uint32_t)net->k1pad;
+    for (int l = 0; l <= net->L && same; ++l) same = hd.dims[l] == (uint32_t)net->dims[l];
+    if (!same) return fail(CBDFS_EINVAL, "%s holds another network shape", path);
+    size_t want = 0;
+    for (int l = 0; l < net->L; ++l) {
+        const size_t O = net->dims[l + 1], I = l == 0 ? (size_t)net->k1pad : (size_t)net->dims[l];
+        want += (3 * O * I + 3 * O) * 4;
+    }
+    if (hd.payload != want) return fail(CBDFS_EINVAL, "%s: payload of %llu bytes, %zu expected", path,
+                                        (unsigned long long)hd.payload, want);
+    std::vector<unsigned char> payload(want);
+    if (fread(payload.data(), 1, want, in.f) != want) return fail(CBDFS_EINVAL, "%s: short file", path);
+    if (fnv1a64(payload.data(), want, kFnvBasis) != hd.hash) return fail(CBDFS_EINVAL, "%s: hash mismatch", path);
+    CUDA_TRY(cudaSetDevice(c->device));
+    std::lock_guard<std::mutex> lk(c->device_call_mu);
+    if ((rc = ensure_train_state(c, *net))) return rc;
+    CUDA_TRY(cudaDeviceSynchronize());
+    TrainState &T = *net->train;
+    size_t off = 0;
+    for (int l = 0; l < net->L; ++l) {
+        float *p[6];
+        size_t cnt[6];
+        layer_tensors(T, *net, l, p, cnt);
+        for (int i = 0; i < 6; ++i) {
+            CUDA_TRY(cudaMemcpy(p[i], payload.data() + off, cnt[i] * 4, cudaMemcpyHostToDevice));
+            off += cnt[i] * 4;
+        }
+    }
+    T.step = hd.step;
+    // the copies the heuristic and the backward read: BF16 weights, transposes, FP32 head, parts
+    cudaStream_t st = c->slots[0].stream;
+    if ((rc = launch_adam(*net, nullptr, true, st))) return rc;
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return CBDFS_OK;
 }
 
 }  // extern "C"

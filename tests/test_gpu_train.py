@@ -149,3 +149,44 @@ def test_training_on_pdb_labels_gains_over_manhattan(P, ctx, orc):
         print(f"instance {i}: MD cost {a['cost']} expanded {a['expanded']}; "
               f"network cost {b['cost']} expanded {b['expanded']}")
     assert tot_nn < tot_md
+
+
+def test_checkpoint_resume_continues_exactly(P, ctx, orc, tmp_path):
+    # train, save, train on: a second network loaded from the checkpoint and trained on the same
+    # way ends with the same weights bit for bit, and right after the load it evaluates exactly
+    # as the first network did when it was saved (its BF16 weights and FP32 head rewritten)
+    dims = W.NET_C3["dims"]
+    Ws, bs = W.net_weights(**W.NET_C3)
+    s = W.random_stp_states(4, 3072, 321)
+    labels = (W.splitmix64_array(322, 3072) % np.uint64(81)).astype(np.uint8)
+    probe = W.random_stp_states(4, 1000, 323)
+    g0 = np.zeros(1000, np.uint8)
+    a = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, PREC["bf16"], P.HEAD_CLASSIFIER, 0)
+    P.net_train(ctx, a, s, labels, batch=1024, epochs=1, lr=1e-3, seed=5)
+    path = tmp_path / "c3.ckpt"
+    P.cbdfs_train_save(ctx, a, path)
+    h_saved, _, _, y_saved = P.heur_submit_batch(ctx, a, P.DOM_STP4, probe, g0, 255, want_y=True, n_out=81)
+    W_saved, b_saved = P.cbdfs_net_read(ctx, a, dims)
+    P.net_train(ctx, a, s, labels, batch=1024, epochs=1, lr=1e-3, seed=6)
+    Wa, ba = P.cbdfs_net_read(ctx, a, dims)
+
+    b = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, PREC["bf16"], P.HEAD_CLASSIFIER, 0)
+    P.cbdfs_train_load(ctx, b, path)
+    Wl, bl = P.cbdfs_net_read(ctx, b, dims)
+    assert all(np.array_equal(x, y) for x, y in zip(Wl + bl, W_saved + b_saved))
+    h_loaded, _, _, y_loaded = P.heur_submit_batch(ctx, b, P.DOM_STP4, probe, g0, 255, want_y=True, n_out=81)
+    assert np.array_equal(h_loaded, h_saved) and np.array_equal(y_loaded, y_saved)
+    P.net_train(ctx, b, s, labels, batch=1024, epochs=1, lr=1e-3, seed=6)
+    Wb, bb = P.cbdfs_net_read(ctx, b, dims)
+    assert all(np.array_equal(x, y) for x, y in zip(Wb + bb, Wa + ba))
+
+    # another shape, or a damaged file, is refused and leaves the network as it was
+    c1 = P.cbdfs_net_load(ctx, P.DOM_STP4, *W.net_weights(**W.NET_C1), PREC["bf16"], P.HEAD_REGRESSION, 1)
+    with pytest.raises(P.CbdfsError):
+        P.cbdfs_train_load(ctx, c1, path)
+    raw = bytearray(path.read_bytes())
+    raw[-5] ^= 0x40
+    (tmp_path / "bad.ckpt").write_bytes(bytes(raw))
+    with pytest.raises(P.CbdfsError):
+        P.cbdfs_train_load(ctx, b, tmp_path / "bad.ckpt")
+    assert all(np.array_equal(x, y) for x, y in zip(P.cbdfs_net_read(ctx, b, dims)[0], Wb))
