@@ -990,9 +990,25 @@ def profile_case(P, args):
                 the Manhattan max, on --profile-states random states (k_chain);
       pdb78  -- the 7-8 partition with tables of the real sizes (57,657,600 + 518,918,400 bytes;
                 content does not change the access pattern) on --profile-states states
-                (k_pdb_gather)."""
+                (k_pdb_gather);
+      train  -- twelve training steps of the 81-class network (batch 8192, seeded states and
+                labels): the kernels of the training step, for a launch list."""
     import torch
     n = args.profile_states
+    if args.profile_case == "train":
+        ctx = P.cbdfs_create(0, max_batch=8192, n_slots=2)
+        try:
+            Ws, bs = W.net_weights(**W.NET_C3)
+            hid = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, P.PREC_BF16, P.HEAD_CLASSIFIER, 0)
+            states = W.random_stp_states(4, 12 * 8192, 3)
+            labels = (W.splitmix64_array(4, 12 * 8192) % np.uint64(81)).astype(np.uint8)
+            rep = P.net_train(ctx, hid, states, labels, batch=8192, epochs=1, lr=1e-3, seed=3)
+            print(f"train: {rep['steps']} steps, {rep['seconds'] * 1e3 / rep['steps']:.3f} ms per step")
+            if P.cbdfs_device_status(ctx) != 0:
+                raise SystemExit("device error flag set")
+        finally:
+            P.cbdfs_destroy(ctx)
+        return
     ctx = P.cbdfs_create(0, max_batch=n, n_slots=1)
     try:
         if args.profile_case == "chain":
@@ -1043,7 +1059,7 @@ def main():
     ap.add_argument("--train-epochs", type=int, default=5)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-threads", type=int, default=64)
-    ap.add_argument("--profile-case", choices=["chain", "pdb78"],
+    ap.add_argument("--profile-case", choices=["chain", "pdb78", "train"],
                     help="run four launches of one kernel for an ncu capture and exit")
     ap.add_argument("--profile-states", type=int, default=BATCH)
     ap.add_argument("--sweep", action="store_true",
