@@ -322,7 +322,9 @@ int cbdfs_eval_trace(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_
                      int tiles_per_cta, int *ctas);
 
 /* Reads and clears the device-side error flag (0 = none; otherwise a code naming the
- * wait that ran out).  Synchronises the context's device. */
+ * wait that ran out).  Synchronises the context's device.  A set flag also resets every slot's
+ * dependency counters of the fused network kernel (a launch whose wait ran out may leave them
+ * counted); until this call, every evaluation on the context reports ETIMEDOUT. */
 int cbdfs_device_status(cbdfs_ctx *ctx);
 
 /* ---------------------------------------------------------------------------------------
