@@ -194,34 +194,49 @@ int gemm_tn(const CUtensorMap &tmA, const CUtensorMap &tmB, int M, int N, int K,
 // small kernels
 // ---------------------------------------------------------------------------------------
 
-// BF16 transpose: in [R][C] -> out [C][R] (R, C multiples of 64), 64 x 64 tiles through shared
-// memory, moved as element pairs: a warp reads and writes 128 contiguous bytes, and the padded
-// rows (65 elements) keep the column reads on distinct banks.  Block (32, 8).
+// BF16 transpose: in [R][C] (row stride ldi) -> out [C][R] (row stride ldo; and out2 when
+// given), R and C multiples of 64, 64 x 64 tiles through shared memory moved as 16-byte
+// vectors: eight threads read one 128-byte tile row and eight write one 128-byte output row.
+// The tile rows are 66 elements (33 words) apart, so the eight rows a column read gathers fall
+// on distinct banks.  colsum (optional): the column sums of the tile's 64 rows, in row order,
+// at colsum[tile row][C].  Block (32, 8).
+constexpr int kTrPitch = 66;
 __global__ void __launch_bounds__(256) k_transpose(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ out,
                                                    int R, int C, int ldi, int ldo,
                                                    __nv_bfloat16 *__restrict__ out2, float *__restrict__ colsum) {
-    __shared__ __nv_bfloat16 t[64][65];
-    const int c0 = blockIdx.x * 64, r0 = blockIdx.y * 64, tx = threadIdx.x;
-    for (int i = threadIdx.y; i < 64; i += 8) {
-        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(in + (size_t)(r0 + i) * ldi + c0 + 2 * tx);
-        t[i][2 * tx] = v.x;
-        t[i][2 * tx + 1] = v.y;
+    __shared__ __align__(16) __nv_bfloat16 t[64 * kTrPitch];
+    const int c0 = blockIdx.x * 64, r0 = blockIdx.y * 64;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int v = tid & 7;  // the 16-byte vector of a 64-element row
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int r = (tid >> 3) + 32 * p;
+        const uint4 x = *reinterpret_cast<const uint4 *>(in + (size_t)(r0 + r) * ldi + c0 + 8 * v);
+        uint32_t *row = reinterpret_cast<uint32_t *>(t + r * kTrPitch + 8 * v);  // 4-byte aligned
+        row[0] = x.x;
+        row[1] = x.y;
+        row[2] = x.z;
+        row[3] = x.w;
     }
     __syncthreads();
-    for (int j = threadIdx.y; j < 64; j += 8) {
-        __nv_bfloat162 v;
-        v.x = t[2 * tx][j];
-        v.y = t[2 * tx + 1][j];
-        *reinterpret_cast<__nv_bfloat162 *>(out + (size_t)(c0 + j) * ldo + r0 + 2 * tx) = v;
-        if (out2) *reinterpret_cast<__nv_bfloat162 *>(out2 + (size_t)(c0 + j) * ldo + r0 + 2 * tx) = v;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int c = (tid >> 3) + 32 * p;  // input column = output row
+        const unsigned short *ts = reinterpret_cast<const unsigned short *>(t);
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            w[i] = (uint32_t)ts[(8 * v + 2 * i) * kTrPitch + c] | ((uint32_t)ts[(8 * v + 2 * i + 1) * kTrPitch + c] << 16);
+        const uint4 y = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(out + (size_t)(c0 + c) * ldo + r0 + 8 * v) = y;
+        if (out2) *reinterpret_cast<uint4 *>(out2 + (size_t)(c0 + c) * ldo + r0 + 8 * v) = y;
     }
     // the tile's column sums over its 64 rows, in row order: the row-chunk partials of the
     // bias gradient (chunk r0 / 64)
     static_assert(kSumRows == 64, "a bias-gradient chunk is one transpose tile");
-    const int tid = threadIdx.y * 32 + threadIdx.x;
     if (colsum && tid < 64) {
         float sum = 0.f;
-        for (int i = 0; i < 64; ++i) sum += __bfloat162float(t[i][tid]);
+        for (int i = 0; i < 64; ++i) sum += __bfloat162float(t[i * kTrPitch + tid]);
         colsum[(size_t)blockIdx.y * C + c0 + tid] = sum;
     }
 }
