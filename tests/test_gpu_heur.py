@@ -437,3 +437,44 @@ def test_chain_at_the_kernel_micro_sizes_sampled(P, orc, n):
         assert P.cbdfs_device_status(ctx) == 0
     finally:
         P.cbdfs_destroy(ctx)
+
+
+@pytest.mark.parametrize("net", ["c1_bf16", "c1_fp8", "c2_bf16", "c3_bf16"])
+def test_chain_counts_left_zero_between_launches(P, orc, net):
+    # the fused kernel's dependency counts are zeroed by the launch itself (each count once
+    # nothing reads it any more): a batch evaluated after launches of other sizes on the same
+    # slot gives what the first launch of a fresh context gives, bit for bit (a count left
+    # behind would let a layer start early or make a wait run out)
+    cfg, dom, head, md = {"c1": (W.NET_C1, P.DOM_STP4, P.HEAD_REGRESSION, 1),
+                          "c2": (W.NET_C2, P.DOM_RC3, P.HEAD_CLASSIFIER, 0),
+                          "c3": (W.NET_C3, P.DOM_STP4, P.HEAD_CLASSIFIER, 1)}[net[:2]]
+    prec = net[3:]
+    Ws, bs = W.net_weights(**cfg)
+    kw = {}
+    if prec == "fp8":
+        kw["act_scales"] = fp8_act_scales(orc, 1, Ws, bs, W.random_stp_states(4, 4096, 11))
+
+    def batch(n, seed):
+        s = W.random_rc_states(n, seed).reshape(-1) if dom == P.DOM_RC3 else W.random_stp_states(4, n, seed)
+        return s, _g(n, seed + 1, 40)
+
+    def fresh(s, g):
+        c = P.cbdfs_create(0, max_batch=8192, n_slots=2)
+        try:
+            hid = P.cbdfs_net_load(c, dom, Ws, bs, PREC[prec], head, md, **kw)
+            return P.heur_submit_batch(c, hid, dom, s, g, 30)
+        finally:
+            P.cbdfs_destroy(c)
+
+    ctx = P.cbdfs_create(0, max_batch=8192, n_slots=2)
+    try:
+        hid = P.cbdfs_net_load(ctx, dom, Ws, bs, PREC[prec], head, md, **kw)
+        for k, n in enumerate((8192, 129, 1, 4096, 8192, 300, 2000)):
+            s, g = batch(n, 8800 + k)
+            got = P.heur_submit_batch(ctx, hid, dom, s, g, 30)
+            if k in (0, 2, 4, 6):
+                want = fresh(s, g)
+                assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1]) and got[2] == want[2]
+        assert P.cbdfs_device_status(ctx) == 0
+    finally:
+        P.cbdfs_destroy(ctx)
