@@ -911,6 +911,7 @@ def run_ours(args):
         "e2e": {"value": e2e, "unit": "states/s", "h2d_bytes_per_step": B * 8 + B,
                 "d2h_bytes_per_step": B + (B + 31) // 32 * 4 + 4,
                 "mode": f"heur_submit_batch_async, {E2E_DEPTH} batches in flight, page-locked host buffers",
+                "l2": "not flushed between batches (the weights stay in L2, as in a running search)",
                 "sync_call_value": e2e_sync},
         "roofline": roof, "clocks": clk,
         "fp32_states_per_s": fp32_rate, "bf16_over_fp32": value / world / fp32_rate,
