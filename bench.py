@@ -209,6 +209,7 @@ def search_rates(P, ctx, hids, seconds, work_num=256):
 
     def run(hid, fixed):
         costs, iters, exp, gen, secs, nb, ev = [], [], 0, 0, 0.0, 0, 0
+        hist, flight_us = [0] * 16, 0.0
         for s in starts:
             r = P.cbdfs_solve(ctx, P.DOM_STP4, s, P.ALGO_IDA, hid, partial_ok=True, threads=threads,
                               work_num=work_num, batch=8192, timeout_us=500, time_limit_s=seconds,
@@ -221,8 +222,14 @@ def search_rates(P, ctx, hids, seconds, work_num=256):
             secs += r["seconds"]
             nb += r["batches"]
             ev += r["evaluated"]
+            hist = [x + y for x, y in zip(hist, r["batch_hist"])]
+            flight_us += r["batch_flight_us"] * r["batches"]
+        # batches by size class (2^i .. 2^(i+1)-1 states) and the mean number of batches in
+        # flight (submission to results readable, summed over batches, over the wall time)
         return {"costs": costs, "expanded_per_s": exp / secs, "generated_per_s": gen / secs,
-                "avg_batch": ev / max(nb, 1), "seconds": secs}, iters
+                "avg_batch": ev / max(nb, 1), "seconds": secs,
+                "batch_hist": {f"{1 << i}-{(1 << (i + 1)) - 1}": c for i, c in enumerate(hist) if c},
+                "batches_in_flight": flight_us / 1e6 / secs}, iters
 
     for mode in ("fixed_tree", "network_pruned"):
         res, its = {}, {}

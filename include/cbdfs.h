@@ -470,6 +470,7 @@ typedef struct {
 } cbdfs_search_cfg;
 
 #define CBDFS_MAX_ITERS 256
+#define CBDFS_BATCH_HIST 16
 
 typedef struct {
     int cost;                       /* solution cost (-1 if none) */
@@ -493,6 +494,10 @@ typedef struct {
     int real_valued;                /* 1: the pruning heuristic is real-valued (CBDFS_HEAD_REAL);
                                        its bounds are in iter_bound_real, iter_bound holds 0 */
     double iter_bound_real[CBDFS_MAX_ITERS];  /* every search's bound as a real number */
+    int64_t batch_hist[CBDFS_BATCH_HIST];     /* GPU batches by size (those of the initial
+                                                 partition too): entry i counts the batches of
+                                                 2^i .. 2^(i+1)-1 states (the last: 2^15 and
+                                                 more); the entries add up to `batches` */
 } cbdfs_result;
 
 /* Solve from `start` (packed words).  heur_id: a network, a PDB or a built-in id.

@@ -125,7 +125,8 @@ class Result(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("d_init", ctypes.c_int),
                 ("work_items", ctypes.c_int64), ("batch_fill_us", ctypes.c_double),
                 ("batch_flight_us", ctypes.c_double), ("submit_us", ctypes.c_double),
-                ("real_valued", ctypes.c_int), ("iter_bound_real", ctypes.c_double * MAX_ITERS)]
+                ("real_valued", ctypes.c_int), ("iter_bound_real", ctypes.c_double * MAX_ITERS),
+                ("batch_hist", ctypes.c_int64 * 16)]
 
 
 _vp, _u64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)
@@ -585,7 +586,7 @@ def cbdfs_solve(ctx, domain, start, algo=ALGO_IDA, heur_id=HEUR_MD, partial_ok=F
                 n_iters=r.n_iters, expanded=r.expanded, generated=r.generated,
                 batches=r.batches, evaluated=r.evaluated, seconds=r.seconds, d_init=r.d_init,
                 work_items=r.work_items, batch_fill_us=r.batch_fill_us,
-                batch_flight_us=r.batch_flight_us, submit_us=r.submit_us)
+                batch_flight_us=r.batch_flight_us, submit_us=r.submit_us, batch_hist=list(r.batch_hist))
 
 
 def cbdfs_cancel(ctx):

@@ -117,6 +117,7 @@ struct Shared {
     std::vector<int> slot_free;
     // results
     std::atomic<int64_t> expanded{0}, generated{0}, evaluated{0}, nbatches{0};
+    int64_t hist[CBDFS_BATCH_HIST] = {};  // batches by size class (processor thread only)
     int64_t fill_ns = 0, flight_ns = 0, submit_ns = 0;  // batch timing sums (processor thread)
     std::atomic<uint32_t> minf{kNone};
     std::atomic<int> found{0}, stop{0}, cut{0};
@@ -160,6 +161,13 @@ bool open_batch(Shared &S) {
 // timeout_us, or when every live worker is idle; evaluates sealed batches on the GPU
 // slots asynchronously; publishes results.
 // ---------------------------------------------------------------------------------------
+// the histogram class of a batch of n states: 2^i <= n < 2^(i+1), the last class open-ended
+int batch_class(uint32_t n) {
+    int cls = 0;
+    while (cls + 1 < CBDFS_BATCH_HIST && (n >> (cls + 1)) != 0) ++cls;
+    return cls;
+}
+
 int submit(Shared &S, Batch &b) {
     const auto t_in = Clock::now();
     S.fill_ns += std::chrono::duration_cast<std::chrono::nanoseconds>(t_in - b.first_add).count();
@@ -186,6 +194,7 @@ int submit(Shared &S, Batch &b) {
         return fail(CBDFS_EDEVICE, "result download");
     b.state = 2;
     S.nbatches++;
+    S.hist[batch_class(n)]++;
     S.evaluated += n;
     b.submitted = Clock::now();
     S.submit_ns += std::chrono::duration_cast<std::chrono::nanoseconds>(b.submitted - t_in).count();
@@ -501,6 +510,7 @@ struct Solver {
     std::vector<int> slots;
     std::vector<std::unique_ptr<Batch>> batches;
     int64_t evaluated = 0, nbatches = 0, search_batches = 0;
+    int64_t hist[CBDFS_BATCH_HIST] = {};
     int64_t fill_ns = 0, flight_ns = 0, submit_ns = 0;
     double seconds = 0;
     int64_t expanded_total = 0;
@@ -546,6 +556,7 @@ struct Solver {
             CUDA_TRY(cudaStreamSynchronize(s));
             evaluated += n;
             nbatches++;
+            hist[batch_class(n)]++;
         }
         if (!real)
             for (size_t i = 0; i < st.size(); ++i) h[i] = (float)h8[i];
@@ -705,6 +716,7 @@ struct Solver {
         evaluated += S.evaluated.load();
         nbatches += S.nbatches.load();
         search_batches += S.nbatches.load();
+        for (int i = 0; i < CBDFS_BATCH_HIST; ++i) hist[i] += S.hist[i];
         fill_ns += S.fill_ns;
         flight_ns += S.flight_ns;
         submit_ns += S.submit_ns;
@@ -1012,6 +1024,7 @@ int cbdfs_solve(cbdfs_ctx *ctx, int domain, const uint64_t *start, int algo, int
     c->slot_cv.notify_all();
     out->real_valued = sv.real;
     out->batches = sv.nbatches;
+    for (int i = 0; i < CBDFS_BATCH_HIST; ++i) out->batch_hist[i] = sv.hist[i];
     out->evaluated = sv.evaluated;
     const double nb = (double)std::max<int64_t>(1, sv.search_batches);
     out->batch_fill_us = sv.fill_ns / nb / 1e3;

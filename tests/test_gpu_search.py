@@ -117,6 +117,8 @@ def test_rc_classifier_fixed_tree(P, ctx, orc):
                       timeout_us=300, fixed_tree_heur=P.HEUR_ZERO)
     assert r["cost"] == want["cost"] and _iters(r) == [list(t) for t in want["iters"]]
     assert r["batches"] > 0 and r["evaluated"] >= r["expanded"]
+    # every search batch is in exactly one size class of the histogram
+    assert sum(r["batch_hist"]) == r["batches"] and len(r["batch_hist"]) == 16
 
 
 @pytest.mark.parametrize("n0", [1, 10, 10000])
