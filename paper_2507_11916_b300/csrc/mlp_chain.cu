@@ -10,9 +10,11 @@
 // can always proceed.  Activations of a row block stay in L2 between layers.
 //
 // Before the tiles, every warp of the grid decodes packed states into the one-hot input rows
-// (units of 8 rows, one coalesced state load per unit, 16-byte coalesced stores, every chunk
-// computed branch-free) and counts finished units per row block, so that layer 0 waits only
-// for its own 128 rows.
+// (units of 16 or 8 rows, about 8 KB each, one coalesced state load per unit, 16-byte
+// coalesced stores, every chunk computed branch-free) and counts finished units per row
+// block, so that layer 0 waits only for its own 128 rows.  The launch leaves every count zero
+// for the next one: a count is zeroed once nothing reads it any more (by the next layer's
+// producer, the row block's head finisher, or a stored last layer's final warp).
 //
 // Per CTA (192 threads):
 //   warp 0      producer: TMA loads the A k-block (the one-hot rows for layer 0, the stored
