@@ -146,9 +146,24 @@ def cpu_oracle_rate(seconds=10.0, chunk=1024):
         n += chunk
     dt = time.perf_counter() - t0
     threads = blas_threads()
-    return {"value": n / dt, "unit": "states/s", "cores": threads, "kind": "oracle",
-            "sample": f"{n} states of the workload in chunks of {chunk} (float64 numpy forward, "
-                      f"integer-h rule and bound test), {dt:.1f} s"}
+    out = {"value": n / dt, "unit": "states/s", "cores": threads, "kind": "oracle",
+           "sample": f"{n} states of the workload in chunks of {chunk} (float64 numpy forward, "
+                     f"integer-h rule and bound test), {dt:.1f} s"}
+    # the same evaluation on one core (BLAS limited to one thread), a shorter sample
+    try:
+        from threadpoolctl import threadpool_limits
+        with threadpool_limits(limits=1):
+            n1, t1 = 0, time.perf_counter()
+            while time.perf_counter() - t1 < seconds / 4:
+                y = oracle.mlp_forward(Wq, bs, oracle.one_hot(oracle.DOM_STP4, states))
+                h = oracle.h_regression(y[:, 0], oracle.md_states(oracle.DOM_STP4, states),
+                                        oracle.is_goal_states(oracle.DOM_STP4, states))
+                oracle.bound_test(g, h, BOUND)
+                n1 += chunk
+            out["single_core_value"] = n1 / (time.perf_counter() - t1)
+    except ImportError:
+        pass
+    return out
 
 
 def run_reference(args):
