@@ -70,3 +70,22 @@ def test_bad_arguments(P, tmp_path):
         P.cbdfs_pdb_file_write(tmp_path / "x.bin", 7, [1, 2], np.zeros(4, np.uint8))  # no such domain
     with pytest.raises(P.CbdfsError):
         P.cbdfs_pdb_file_write(tmp_path / "x.bin", P.DOM_STP3, [], np.zeros(4, np.uint8))  # no tiles
+
+
+def test_header_layout_is_the_documented_one(P, tmp_path):
+    # "CBDFSPDB", version, domain, k, 16 tiles, DIV factor, entry count, FNV-1a 64 of the table
+    import struct
+    table = np.arange(1000, dtype=np.uint64).astype(np.uint8)
+    path = tmp_path / "layout.bin"
+    P.cbdfs_pdb_file_write(path, P.DOM_STP4, [10, 11, 15], table, div=3)
+    raw = path.read_bytes()
+    magic, version, dom, k = struct.unpack_from("<8sIii", raw, 0)
+    tiles = struct.unpack_from("<16i", raw, 20)
+    div, entries, h = struct.unpack_from("<IQQ", raw, 84)
+    assert (magic, version, dom, k) == (b"CBDFSPDB", 1, P.DOM_STP4, 3)
+    assert tiles == (10, 11, 15) + (0,) * 13 and div == 3 and entries == 1000
+    fnv = 14695981039346656037
+    for b in table.tobytes():
+        fnv = ((fnv ^ b) * 1099511628211) % (1 << 64)
+    assert h == fnv
+    assert raw[128:] == table.tobytes() and len(raw) == 128 + 1000
