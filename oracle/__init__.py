@@ -696,13 +696,22 @@ def quantise_weights(Ws, prec: str):
     raise ValueError(prec)
 
 
-def mlp_forward(Ws, bs, X, return_hidden=False, act_scales=None):
+def mlp_forward(Ws, bs, X, return_hidden=False, act_scales=None, bf16_acts=False,
+                store_last=False):
     """z_l = a_{l-1} W_l^T + b_l with ReLU on every layer but the last, in float64.
 
-    act_scales (optional): emulate E4M3 storage of the activations that feed a following
-    hidden layer: hidden layer l's output (l < L-2) becomes s_l * E4M3(float32(a) *
-    float32(1/s_l)); the last hidden layer's output, which feeds the float32 last layer,
-    is not rounded."""
+    The arithmetic stays float64; the options below only round the values a low-precision
+    network stores between its layers (the storage formats of Experimental Setup's h_M run
+    in BF16 or FP8 here), each stored value rounded once from its float64 value:
+
+    act_scales: E4M3 storage of the activations that feed a following hidden layer: hidden
+        layer l's output (l < L-2) becomes s_l * E4M3(float32(a) * float32(1/s_l)).
+    bf16_acts: BF16 storage of those activations instead (when act_scales is None):
+        a -> bfloat16(float32(a)), round to nearest, ties to even.
+    store_last: the last hidden layer's output, which feeds the float32 last layer, is
+        stored in BF16 too (a network whose last layer runs as a separate step reads it
+        from memory); without it that output is not rounded (the last layer reads the
+        accumulator)."""
     a = np.asarray(X, dtype=np.float64)
     hidden = []
     L = len(Ws)
@@ -710,10 +719,12 @@ def mlp_forward(Ws, bs, X, return_hidden=False, act_scales=None):
         z = a @ np.asarray(W, np.float64).T + np.asarray(b, np.float64)
         if l < L - 1:
             a = np.maximum(z, 0.0)
-            if act_scales is not None and l < L - 2:
+            if l < L - 2 and act_scales is not None:
                 inv = np.float32(1.0) / np.float32(act_scales[l])
                 q = e4m3_round(a.astype(np.float32) * inv)
                 a = q.astype(np.float64) * float(np.float32(act_scales[l]))
+            elif (l < L - 2 and bf16_acts) or (l == L - 2 and store_last):
+                a = bf16_round(a.astype(np.float32)).astype(np.float64)
             hidden.append(a)
         else:
             a = z

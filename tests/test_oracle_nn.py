@@ -188,6 +188,40 @@ def test_e4m3_activation_emulation(orc):
     assert (np.abs(he[0] - hp[0])[big] <= 2 ** -4 * hp[0][big] + 1e-12).all()
 
 
+def test_bf16_activation_storage_emulation(orc):
+    # Stored activations that bfloat16 represents exactly are unchanged by the emulation.
+    W1 = np.zeros((3, 16))
+    W1[0, 0], W1[1, 1], W1[2, 2] = 2.0, 1.5, 0.375
+    Ws = [W1, np.eye(3), np.ones((1, 3))]
+    bs = [np.zeros(3), np.zeros(3), np.zeros(1)]
+    X = np.eye(16)[:3]
+    plain = orc.mlp_forward(Ws, bs, X)
+    assert np.array_equal(plain, orc.mlp_forward(Ws, bs, X, bf16_acts=True, store_last=True))
+    # Hand-worked: one input 1; first hidden layer a0 = (1 + 2^-8, 1 + 2^-7 + 2^-9);
+    # second hidden layer a1 = a0[0] + a0[1] + 2^-10; y = a1.
+    #  - plain float64: y = 2.013671875 + 2^-10 = 2.0146484375
+    #  - bf16_acts: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7 and goes to the even
+    #    mantissa, 1.0; 1.009765625 is nearer 1.0078125 than 1.015625; a1 = 2.0087890625
+    #  - store_last as well: at 2 the bfloat16 step is 2^-6, and 2.0087890625 is nearer
+    #    2.015625 than 2.0, so y = 2.015625
+    Ws = [np.array([[1 + 2 ** -8], [1 + 2 ** -7 + 2 ** -9]]), np.array([[1.0, 1.0]]), np.array([[1.0]])]
+    bs = [np.zeros(2), np.array([2 ** -10]), np.zeros(1)]
+    X = np.ones((1, 1))
+    assert orc.mlp_forward(Ws, bs, X)[0, 0] == 2.0146484375
+    assert orc.mlp_forward(Ws, bs, X, bf16_acts=True)[0, 0] == 2.0087890625
+    assert orc.mlp_forward(Ws, bs, X, bf16_acts=True, store_last=True)[0, 0] == 2.015625
+    # E4M3 activations (scale 1: step 1/8 at 1) with a BF16-stored last hidden layer:
+    # a0 -> (1, 1), a1 = 2 + 2^-10 -> 2.0
+    assert orc.mlp_forward(Ws, bs, X, act_scales=[1.0], store_last=True)[0, 0] == 2.0
+    # and a random network: every stored value within half a bfloat16 step of the float64 one
+    Ws2, bs2 = W.net_weights([16, 32, 32, 1], "kaiming", 5)
+    X2 = np.random.default_rng(2).random((50, 16))
+    _, hp = orc.mlp_forward(Ws2, bs2, X2, return_hidden=True)
+    _, he = orc.mlp_forward(Ws2, bs2, X2, return_hidden=True, bf16_acts=True)
+    assert (np.abs(he[0] - hp[0]) <= 2 ** -8 * hp[0] + 1e-30).all()
+    assert np.array_equal(he[0], orc.bf16_round(hp[0].astype(np.float32)))
+
+
 def test_bf16_storage_emulation(orc):
     # with every stored value exactly representable in bfloat16 the emulation changes nothing
     Ws = [np.array([[1.0, 0.5], [0.25, -1.0]]), np.array([[2.0, -0.5], [1.0, 1.0]]),
@@ -206,3 +240,18 @@ def test_bf16_storage_emulation(orc):
     g1 = orc.train_forward_backward(Ws2, bs2, X2, lab, "ce")
     g2 = orc.train_forward_backward(Ws2, bs2, X2, lab, "ce", bf16_storage=True)
     assert abs(g1[0] - g2[0]) < 1e-2 * abs(g1[0])
+
+
+def test_md_plus_network_construction(orc):
+    # The test network "Manhattan distance plus the seeded network's output" computes exactly
+    # MD when the seeded part is scaled to zero, in float64 and with BF16 storage emulated.
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from helpers import md_plus_net
+    Ws, bs = md_plus_net(*W.net_weights([256, 1024, 1024, 512, 1], "kaiming", 1), 4, scale=0.0, shift=0.0)
+    s = W.random_stp_states(4, 100, 5)
+    X = orc.one_hot(orc.DOM_STP4, s)
+    md = orc.md_states(orc.DOM_STP4, s)
+    assert np.array_equal(orc.mlp_forward(Ws, bs, X)[:, 0], md)
+    Wq = orc.quantise_weights(Ws[:-1], "bf16") + [Ws[-1]]
+    assert np.array_equal(orc.mlp_forward(Wq, bs, X, bf16_acts=True)[:, 0], md)
