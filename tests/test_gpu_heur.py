@@ -4,7 +4,8 @@ import numpy as np
 import pytest
 
 import workloads as W
-from helpers import PREC, check_h, check_logits, fp8_act_scales, normwise, oracle_net
+from helpers import (PREC, check_h, check_logits, fp8_act_scales, logit_ratio, md_plus_net, normwise,
+                     oracle_net, plain_mismatches, report)
 
 pytestmark = pytest.mark.gpu
 
@@ -141,6 +142,7 @@ def test_c0_chain_8puzzle(P, ctx, orc, prec, n):
     y64, h64, margin = oracle_net(orc, 0, Ws, bs, prec, s, "regression", True, **kw)
     check_logits(y, y64, prec)
     check_h(h, h64, margin)
+    report(f"c0 {prec} n={n}", h, h64, margin, plain_mismatches(orc, 0, Ws, bs, prec, s, h, "regression", True))
     assert h[0] == 0
     _check_bound(orc, h, g, 30, mask, minf)
 
@@ -171,6 +173,7 @@ def test_c1_regression_without_md_exposes_rounding(P, ctx, orc):
     check_logits(y, y64, "bf16")
     assert len(set(h64.tolist())) > 5
     check_h(h, h64, margin)
+    report("c1 x20 bf16 no MD", h, h64, margin, plain_mismatches(orc, 1, Ws, bs, "bf16", s, h))
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
@@ -184,10 +187,11 @@ def test_c2_classifier(P, ctx, orc, prec, n):
                                            n_out=21)
     y64, h64, margin = oracle_net(orc, 2, Ws, bs, prec, s, "classifier", False)
     check_logits(y, y64, prec)
-    nm = check_h(h, h64, margin)
+    check_h(h, h64, margin)
     assert h[0] == 0
     _check_bound(orc, h, g, 25, mask, minf)
-    print(f"margin mismatches: {nm} of {n}")
+    report(f"c2 {prec} n={n}", h, h64, margin,
+           plain_mismatches(orc, 2, Ws, bs, prec, s, h, "classifier") if prec != "fp32" else None)
 
 
 def test_c1_full_batch_sampled(P, ctx, orc):
@@ -203,6 +207,38 @@ def test_c1_full_batch_sampled(P, ctx, orc):
     check_logits(y[idx], y64, "bf16")
     check_h(h[idx], h64, margin)
     _check_bound(orc, h, g, 60, mask, minf)
+
+
+# A network of the 15-puzzle regression shape whose output decides h on most rows: Manhattan
+# distance plus four times the seeded network's output plus 1.5 (helpers.md_plus_net).  With
+# the seeded network alone, y stays within (-1, 1) and the max with MD decides every h.
+
+@pytest.fixture(scope="module")
+def c1_md_plus(orc):
+    Ws, bs = md_plus_net(*W.net_weights(**W.NET_C1), 4)
+    sc = fp8_act_scales(orc, 1, Ws, bs, W.random_stp_states(4, 4096, 11))
+    return Ws, bs, sc
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+@pytest.mark.parametrize("n", [1, 129, 1000, 8192])
+def test_c1_network_decides_h(P, ctx, orc, c1_md_plus, prec, n):
+    Ws, bs, sc = c1_md_plus
+    kw = {"act_scales": sc} if prec == "fp8" else {}
+    hid = P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, PREC[prec], P.HEAD_REGRESSION, 1, **kw)
+    s = W.random_stp_states(4, n, 3100 + n)
+    s[0] = W.stp_goal(4)
+    g = _g(n, 3200 + n, 20)
+    h, mask, minf, y = P.heur_submit_batch(ctx, hid, P.DOM_STP4, s, g, 60, want_y=True)
+    ye, he, margin = oracle_net(orc, 1, Ws, bs, prec, s, "regression", True, **kw)
+    check_logits(y, ye, prec)
+    check_h(h, he, margin)
+    assert h[0] == 0
+    if n >= 1000:  # the network, not the max with MD, decides most rows
+        assert (he > orc.md_states(orc.DOM_STP4, s)).mean() > 0.4
+    _check_bound(orc, h, g, 60, mask, minf)
+    report(f"c1 MD-plus {prec} n={n}", h, he, margin,
+           plain_mismatches(orc, 1, Ws, bs, prec, s, h, "regression", True))
 
 
 def test_device_entry_matches_host_entry(P, ctx):
@@ -244,10 +280,11 @@ def test_c1_fp8(P, ctx, orc, n):
     ye, he, margin = oracle_net(orc, 1, Ws, bs, "fp8", s, "regression", True, act_scales=sc)
     check_logits(y, ye, "fp8")
     check_h(h, he, margin)
-    y64, _, _ = oracle_net(orc, 1, Ws, bs, "fp8", s, "regression", True)
+    y64, _, _ = oracle_net(orc, 1, Ws, bs, "fp8", s, "regression", True, emulate=False)
     if n > 1:
         assert normwise(y, y64) <= 6e-2
     _check_bound(orc, h, g, 60, mask, minf)
+    print(f"c1 fp8 n={n}: per-logit error vs plain float64 {logit_ratio(y, y64, 'fp8'):.2f} x tolerance (reported)")
 
 
 @pytest.mark.parametrize("n", [129, 1000])
@@ -261,12 +298,13 @@ def test_c2_fp8(P, ctx, orc, n):
                                            n_out=21)
     ye, he, margin = oracle_net(orc, 2, Ws, bs, "fp8", s, "classifier", False, act_scales=sc)
     check_logits(y, ye, "fp8")
-    nm = check_h(h, he, margin)
-    y64, _, _ = oracle_net(orc, 2, Ws, bs, "fp8", s, "classifier", False)
+    check_h(h, he, margin)
+    y64, _, _ = oracle_net(orc, 2, Ws, bs, "fp8", s, "classifier", False, emulate=False)
     err = normwise(y, y64)
     assert err <= 6e-2
     _check_bound(orc, h, g, 25, mask, minf)
-    print(f"fp8 margin mismatches: {nm} of {n}; normwise error vs float64 {err:.4f}")
+    report(f"c2 fp8 n={n}", h, he, margin, plain_mismatches(orc, 2, Ws, bs, "fp8", s, h, "classifier"))
+    print(f"normwise error vs plain float64 {err:.4f}; per logit {logit_ratio(y, y64, 'fp8'):.2f} x tolerance")
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
@@ -311,10 +349,10 @@ def test_c3_classifier_81(P, ctx, orc, prec, n):
     h, mask, minf, y = P.heur_submit_batch(ctx, hid, P.DOM_STP4, s, g, 70, want_y=True, n_out=81)
     ye, he, margin = oracle_net(orc, 1, Ws, bs, prec, s, "classifier", True, act_scales=sc)
     check_logits(y, ye, prec)
-    nm = check_h(h, he, margin)
+    check_h(h, he, margin)
     assert h[0] == 0
     _check_bound(orc, h, g, 70, mask, minf)
-    print(f"{prec} 81-class margin mismatches: {nm} of {n}")
+    report(f"c3 {prec} n={n}", h, he, margin, plain_mismatches(orc, 1, Ws, bs, prec, s, h, "classifier", True))
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
@@ -410,14 +448,17 @@ def test_async_batches_and_wait(P, orc):
         P.cbdfs_destroy(ctx)
 
 
+@pytest.mark.parametrize("net", ["c1", "c1_md_plus"])
 @pytest.mark.parametrize("n", [65536, 262144])
-def test_chain_at_the_kernel_micro_sizes_sampled(P, orc, n):
+def test_chain_at_the_kernel_micro_sizes_sampled(P, orc, n, net):
     # many tiles per CTA (the persistent schedule's later rounds, counters reused across row
     # blocks): a seeded sample of rows against the oracle, the bound test over every row, in BF16
-    # and E4M3
+    # and E4M3; the seeded network (h = MD on every row) and the one whose output decides h
     ctx = P.cbdfs_create(0, max_batch=n, n_slots=2)
     try:
         Ws, bs = W.net_weights(**W.NET_C1)
+        if net == "c1_md_plus":
+            Ws, bs = md_plus_net(Ws, bs, 4)
         sc = fp8_act_scales(orc, 1, Ws, bs, W.random_stp_states(4, 4096, 11))
         s = W.random_stp_states(4, n, 9000 + n)
         g = _g(n, 9100 + n, 60)
@@ -430,6 +471,7 @@ def test_chain_at_the_kernel_micro_sizes_sampled(P, orc, n):
                                           sc if prec == "fp8" else None)
             check_logits(y[idx], y64, prec)
             check_h(h[idx], h64, margin)
+            report(f"{net} {prec} n={n} (sample of 400)", h[idx], h64, margin)
             # every row: h follows the rule on the kernel's own y, and the bound test is exact
             own = orc.h_regression(y[:, 0], orc.md_states(orc.DOM_STP4, s), orc.is_goal_states(orc.DOM_STP4, s))
             assert np.array_equal(h, own)

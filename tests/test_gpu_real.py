@@ -87,7 +87,7 @@ def test_real_h_and_bound_test(P, ctx, orc, nets, case, n):
     h, mask, minf = P.heur_submit_batch_real(ctx, hid, dom, s, g, bound)
     assert h.dtype == np.float32 and h[0] == 0.0
     # h is 1-Lipschitz in y (the clamp and the max with MD), so y's tolerance bounds it
-    scale = np.abs(y64[:, 0]) + np.sqrt(np.mean(y64[:, 0] ** 2))
+    scale = np.maximum(np.abs(y64[:, 0]), np.sqrt(np.mean(y64[:, 0] ** 2)))
     err = np.abs(h.astype(np.float64) - h64) / scale
     assert err.max() <= RTOL[prec], f"worst {err.max() / RTOL[prec]:.3f} x tolerance"
     _check_bound_fp32(orc, g, h, bound, mask, minf)
