@@ -70,6 +70,13 @@ typedef struct {
     size_t mem_budget;      /* bytes of device memory the context may allocate; 0 = no limit */
     uint32_t max_batch;     /* largest n one heuristic call accepts (sizes the scratch); 0 = 65536 */
     int n_slots;            /* concurrent evaluation slots (stream + scratch each); 0 = 4 */
+    uint64_t device_wait_ns; /* bound on a tile's wait for the previous layer's rows inside the
+                               fused network kernel, in ns of %globaltimer; 0 = 2 s.  Its stage
+                               and accumulator waits get twice this bound, so that a row count
+                               that never comes is the wait that runs out first.  A wait that
+                               runs out sets the device error flag (cbdfs_device_status; the
+                               first cause is kept) and the kernel winds down; too small a bound
+                               makes an ordinary launch report a timeout */
 } cbdfs_config;
 
 /* Create a context on cfg->device.  *out receives it.  Errors: EINVAL, EDEVICE, ENOMEM. */
@@ -172,11 +179,15 @@ int pdb_build(cbdfs_ctx *ctx, int domain, const int *pattern_tiles, int k, uint8
  * domain (int32), k (int32), the pattern's tiles (16 x int32, unused ones 0), the DIV factor
  * (uint32; 1 = a full table), the entry count (uint64), the FNV-1a 64-bit hash of the table
  * bytes (uint64), zero padding.  Host-only calls: no context, no GPU.
- * cbdfs_pdb_file_write writes `entries` bytes of `table`.  Errors: EINVAL (arguments),
- * EDEVICE (the file could not be written).
+ * `entries` must be the table size the pattern implies: N!/(N-k)! for k tiles of a sliding-tile
+ * puzzle of N = 9 or 16 cells (k <= N-1), 8! * 3^7 for the cube's 8-corner table (k = 8), in
+ * both cases divided by the DIV factor and rounded up.
+ * cbdfs_pdb_file_write writes `entries` bytes of `table`.  Errors: EINVAL (arguments, an entry
+ * count the pattern does not imply), EDEVICE (the file could not be written).
  * cbdfs_pdb_file_read fills the header fields (tiles: 16 ints) and *entries; with table
  * non-NULL it also reads the bytes (cap >= entries) and checks the hash.  Errors: EINVAL (not
- * such a file, version, cap too small, hash mismatch, short file), ENOTFOUND (no file). */
+ * such a file, version, a domain, DIV factor or entry count that is not a valid table's, cap
+ * too small, hash mismatch, short file), ENOTFOUND (no file). */
 int cbdfs_pdb_file_write(const char *path, int domain, const int *tiles, int k, uint32_t div,
                          const uint8_t *table, uint64_t entries);
 int cbdfs_pdb_file_read(const char *path, int *domain, int *tiles, int *k, uint32_t *div,
@@ -326,6 +337,16 @@ int cbdfs_eval_trace(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_
  * dependency counters of the fused network kernel (a launch whose wait ran out may leave them
  * counted); until this call, every evaluation on the context reports ETIMEDOUT. */
 int cbdfs_device_status(cbdfs_ctx *ctx);
+
+/* Failure-detection testing (no counterpart in the paper): the next launch of the fused network
+ * kernel on this context skips the first hidden layer's completion count of one 128-state row
+ * block (row_block < 0: nothing skipped), so that the second layer's tiles of that row block
+ * wait for rows that never come.  Their wait runs out after cbdfs_config.device_wait_ns, the
+ * evaluation returns CBDFS_ETIMEDOUT (or, for device-buffer calls, cbdfs_device_status returns
+ * the wait's code, 5), and the kernel ends normally; nothing faults and the context stays
+ * usable once cbdfs_device_status has cleared the flag.  One launch only; the setting is then
+ * cleared.  Errors: EINVAL (null context). */
+int cbdfs_debug_withhold_publish(cbdfs_ctx *ctx, int row_block);
 
 /* ---------------------------------------------------------------------------------------
  * Serving: continuous batching of requests from many threads (paper: the batch-processing

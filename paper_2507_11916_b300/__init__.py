@@ -52,7 +52,8 @@ class CbdfsError(RuntimeError):
 
 class Config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("mem_budget", ctypes.c_size_t),
-                ("max_batch", ctypes.c_uint32), ("n_slots", ctypes.c_int)]
+                ("max_batch", ctypes.c_uint32), ("n_slots", ctypes.c_int),
+                ("device_wait_ns", ctypes.c_uint64)]
 
 
 class NetDesc(ctypes.Structure):
@@ -132,6 +133,7 @@ class Result(ctypes.Structure):
 _vp, _u64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)
 _lib.cbdfs_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(_vp)]
 _lib.cbdfs_destroy.argtypes = [_vp]
+_lib.cbdfs_debug_withhold_publish.argtypes = [_vp, ctypes.c_int]
 _lib.cbdfs_destroy.restype = None
 _lib.cbdfs_last_error.restype = ctypes.c_char_p
 _lib.cbdfs_mem_used.argtypes = [_vp]
@@ -198,7 +200,7 @@ EXPORTED = ["cbdfs_create", "cbdfs_destroy", "cbdfs_last_error", "cbdfs_mem_used
             "cbdfs_pdb_load", "cbdfs_combo_load", "pdb_build", "heur_submit_batch", "heur_eval_device",
             "heur_submit_batch_real", "heur_eval_device_real", "heur_eval_device_static",
             "heur_submit_batch_async", "heur_wait",
-            "cbdfs_device_status", "cbdfs_eval_profile", "cbdfs_eval_trace", "net_train",
+            "cbdfs_device_status", "cbdfs_debug_withhold_publish", "cbdfs_eval_profile", "cbdfs_eval_trace", "net_train",
             "cbdfs_train_grad", "cbdfs_net_read", "cbdfs_train_save", "cbdfs_train_load",
             "cbdfs_pdb_file_write", "cbdfs_pdb_file_read", "cbdfs_gen_walk_states", "cbdfs_server_start",
             "cbdfs_server_stop", "heur_request_submit", "heur_request_wait", "cbdfs_server_get_stats", "cbdfs_apply_moves", "cbdfs_manhattan", "cbdfs_solve",
@@ -224,8 +226,8 @@ def cbdfs_last_error() -> str:
     return _lib.cbdfs_last_error().decode()
 
 
-def cbdfs_create(device=0, mem_budget=0, max_batch=0, n_slots=0):
-    cfg = Config(device, mem_budget, max_batch, n_slots)
+def cbdfs_create(device=0, mem_budget=0, max_batch=0, n_slots=0, device_wait_ns=0):
+    cfg = Config(device, mem_budget, max_batch, n_slots, device_wait_ns)
     h = _vp()
     _check(_lib.cbdfs_create(ctypes.byref(cfg), ctypes.byref(h)))
     return h
@@ -411,6 +413,10 @@ def cbdfs_eval_trace(ctx, heur_id, domain, d_states, d_g, bound, n, d_h, d_mask,
                                  _ptr(d_h), _ptr(d_mask), _ptr(d_minf), s, _ptr(d_trace),
                                  tiles_per_cta, ctypes.byref(k)))
     return k.value
+
+
+def cbdfs_debug_withhold_publish(ctx, row_block: int) -> None:
+    _check(_lib.cbdfs_debug_withhold_publish(ctx, row_block))
 
 
 def cbdfs_device_status(ctx) -> int:

@@ -373,6 +373,8 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     P.minf = d_minf;
     P.y = d_y;
     P.err = c->d_err;
+    P.wait_ns = c->wait_ns;
+    P.hold_mblock = c->hold_mblock.exchange(-1);
     const int grid = std::min(c->num_sms, max_tiles);
     if (s.trace) {
         P.trace = s.trace;
@@ -594,6 +596,7 @@ int cbdfs_create(const cbdfs_config *cfg, cbdfs_ctx **out) {
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, cfg->device);
     if (c->num_sms <= 0) c->num_sms = 1;
     c->mem_budget = cfg->mem_budget;
+    c->wait_ns = cfg->device_wait_ns ? cfg->device_wait_ns : dev::kWaitNs;
     c->max_batch = cfg->max_batch ? cfg->max_batch : 65536;
     c->max_batch_pad = (c->max_batch + kBM - 1) / kBM * kBM;
     const int nslots = 1 + (cfg->n_slots > 0 ? cfg->n_slots : 4);  // slot 0: device-buffer calls
@@ -1308,6 +1311,12 @@ int cbdfs_eval_trace(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t *d_
     if (!rc && cudaEventRecord(s.done, st) != cudaSuccess) rc = fail(CBDFS_EDEVICE, "event record");
     if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(CBDFS_EDEVICE, "trace sync");
     return rc;
+}
+
+int cbdfs_debug_withhold_publish(cbdfs_ctx *ctx, int row_block) {
+    if (!ctx) return fail(CBDFS_EINVAL, "null argument");
+    reinterpret_cast<Ctx *>(ctx)->hold_mblock.store(row_block < 0 ? -1 : row_block);
+    return CBDFS_OK;
 }
 
 int cbdfs_device_status(cbdfs_ctx *ctx) {

@@ -54,6 +54,9 @@ struct ChainParams {
     uint32_t *mask, *minf;
     float *y;                      // raw outputs; CBDFS_HEAD_REAL: the real h
     int *err;
+    unsigned long long wait_ns;    // bound on each wait (ns of %globaltimer)
+    int hold_mblock;               // failure-detection testing: the row block whose first-layer
+                                   // completion count this launch skips (-1: none)
     unsigned long long *trace;     // optional: [grid][trace_tiles][8] %globaltimer stamps
     int trace_tiles;
 };

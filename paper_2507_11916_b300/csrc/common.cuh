@@ -158,6 +158,8 @@ struct Ctx {
     uint32_t max_batch = 0, max_batch_pad = 0;
     size_t act_bytes = 0;              // bytes per activation buffer
     int *d_err = nullptr;              // device error flag
+    uint64_t wait_ns = 0;              // bound on each fused-kernel wait (cbdfs_config.device_wait_ns)
+    std::atomic<int> hold_mblock{-1};  // cbdfs_debug_withhold_publish: the next chain launch's held row block
     std::vector<std::unique_ptr<NetGPU>> nets;    // heur ids 0..: nets and PDBs interleaved
     std::vector<std::unique_ptr<PdbGPU>> pdbs;
     std::vector<std::unique_ptr<ComboGPU>> combos;
@@ -222,7 +224,7 @@ inline int dom_onehot(int d) { return d == CBDFS_DOM_STP3 ? 81 : d == CBDFS_DOM_
 namespace cbdfs {
 namespace dev {
 
-constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on every device wait
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s: the default bound on a device wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -261,9 +263,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: gives up after kWaitNs (or 2^30 polls), records `code` in *err and
-// returns false.  Never traps.
-// A wait also gives up at once when the error flag is already set (another wait failed).
+// Bounded wait: gives up after limit_ns (or 2^30 polls), records `code` in *err unless
+// another wait recorded its code first (the first cause is kept), and returns false.  Never
+// traps.  A wait also gives up at once when the error flag is already set (another wait
+// failed).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code,
                                           unsigned long long limit_ns = kWaitNs) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -275,7 +278,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *er
             if (globaltimer() - t0 > limit_ns) break;
         }
     }
-    atomicExch(err, code);
+    atomicCAS(err, 0, code);
     return false;
 }
 

@@ -29,7 +29,8 @@
 //               partials in tile order (deterministic), applies the integer-h rule (rint or
 //               argmax, max with Manhattan distance, goal = 0) and the bound test (mask bits
 //               by ballot, least f above the bound by warp minimum + atomicMin).
-// Every wait is bounded (2 s of %globaltimer) and reports through the error flag.
+// Every wait is bounded (ChainParams::wait_ns of %globaltimer, 2 s unless the context sets
+// another bound) and reports through the error flag.
 #include <cuda_fp8.h>
 
 #include <mutex>
@@ -65,7 +66,7 @@ __device__ __forceinline__ void epi_bar() {  // the 128 epilogue threads
 }
 
 // bounded wait until *p >= want (acquire)
-__device__ __forceinline__ bool wait_count(const int *p, int want, int *err) {
+__device__ __forceinline__ bool wait_count(const int *p, int want, int *err, unsigned long long limit_ns) {
     if ((int)ld_acquire(p) >= want) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t i = 1; i < (1u << 28); ++i) {
@@ -73,10 +74,10 @@ __device__ __forceinline__ bool wait_count(const int *p, int want, int *err) {
         __nanosleep(64);
         if ((i & 63) == 0) {
             if (*reinterpret_cast<volatile int *>(err) != 0) return false;
-            if (globaltimer() - t0 > kWaitNs) break;
+            if (globaltimer() - t0 > limit_ns) break;
         }
     }
-    atomicExch(err, DEVERR_DEPENDENCY);
+    atomicCAS(err, 0, DEVERR_DEPENDENCY);
     return false;
 }
 
@@ -245,6 +246,10 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int total = P.tile_start[P.nh];
+    // stage and accumulator waits wait on work that itself waits on row-block counts: their
+    // bound is twice the count wait's, so that a count that never comes is the wait that runs
+    // out first and names the cause
+    const unsigned long long stage_ns = 2 * P.wait_ns;
     const int last_l = P.fused_head ? P.nh - 1 : P.nh;  // the layer whose epilogue runs the head
 
     if (threadIdx.x == 0) {
@@ -348,7 +353,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
             // layer l-1 (4 warps per tile)
             const int *cnt = P.counters + T.l * P.mblocks + T.m;
             const int want = T.l == 0 ? kBM / P.unit_rows : 4 * P.nt[T.l - 1];
-            if (lane == 0) ok = wait_count(cnt, want, P.err);
+            if (lane == 0) ok = wait_count(cnt, want, P.err, P.wait_ns);
             ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
             if (!ok) break;
             fence_proxy_async_global();
@@ -361,7 +366,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                 const uint32_t u = it / STAGES;
                 if (it >= STAGES) {
                     bool w = true;
-                    if (lane == 0) w = mbar_wait(smem_u32(&empty[s]), (u - 1) & 1, P.err, DEVERR_STAGE_EMPTY);
+                    if (lane == 0) w = mbar_wait(smem_u32(&empty[s]), (u - 1) & 1, P.err, DEVERR_STAGE_EMPTY, stage_ns);
                     w = __shfl_sync(0xFFFFFFFFu, w, 0);
                     if (!w) { ok = false; break; }
                 }
@@ -393,13 +398,13 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                 const Tile T = tile_of(P, t);
                 const int KB = P.kdim[T.l] / KBLK;
                 const uint32_t b = i & 1, u = i >> 1;
-                if (i >= 2 && !mbar_wait(smem_u32(&acc_empty[b]), (u - 1) & 1, P.err, DEVERR_ACCUM)) break;
+                if (i >= 2 && !mbar_wait(smem_u32(&acc_empty[b]), (u - 1) & 1, P.err, DEVERR_ACCUM, stage_ns)) break;
                 tc_fence_after();
                 stamp(P, i, 3);
                 const uint32_t d = tmem + b * BN;
                 for (int kb = 0; kb < KB; ++kb, ++it) {
                     const int s = it % STAGES;
-                    if (!mbar_wait(smem_u32(&full[s]), (it / STAGES) & 1, P.err, DEVERR_TMA_FULL)) {
+                    if (!mbar_wait(smem_u32(&full[s]), (it / STAGES) & 1, P.err, DEVERR_TMA_FULL, stage_ns)) {
                         ok = false;
                         break;
                     }
@@ -436,7 +441,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
             epi_bar();
             // after a failed wait the warps skip the work but keep every barrier, so that
             // the four epilogue warps stay in step
-            const bool good = mbar_wait(smem_u32(&acc_full[b]), u & 1, P.err, DEVERR_ACCUM);
+            const bool good = mbar_wait(smem_u32(&acc_full[b]), u & 1, P.err, DEVERR_ACCUM, stage_ns);
             tc_fence_after();
             if (ep_tid == 0) stamp(P, i, 5);
             const uint32_t taddr = tmem + b * BN + ((uint32_t)(q * 32) << 16);
@@ -520,7 +525,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                     fence_proxy_async_global();
                     int *oc = P.counters + (1 + T.l) * P.mblocks + T.m;
                     if (good && T.l + 1 < P.nh) {
-                        red_release_add(oc, 1);
+                        if (!(T.l == 0 && T.m == P.hold_mblock)) red_release_add(oc, 1);
                     } else if (good && atomicAdd(oc, 1) == 4 * P.nt[T.l] - 1) {
                         // the last hidden layer, stored for a separate head kernel: the row block's
                         // last warp leaves its own count and the layer's input count zero

@@ -144,7 +144,7 @@ k_tc_layer(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 umma_commit(smem_u32(&empty[s]));
             }
             if (ok) umma_commit(smem_u32(accum));
-            else atomicExch(err, DEVERR_TMA_FULL);
+            else atomicCAS(err, 0, DEVERR_TMA_FULL);
         }
     } else {
         // epilogue: warps 2..5 cover TMEM lane quarters (warp % 4)

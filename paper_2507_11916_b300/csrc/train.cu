@@ -115,7 +115,7 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 umma_commit(smem_u32(&empty[s]));
             }
             umma_commit(smem_u32(accum));
-            if (!ok) atomicExch(err, DEVERR_TMA_FULL);
+            if (!ok) atomicCAS(err, 0, DEVERR_TMA_FULL);
         }
     } else {
         const int q = warp & 3;
