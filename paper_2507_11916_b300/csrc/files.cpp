@@ -38,6 +38,26 @@ struct PdbFileHeader {
 static_assert(sizeof(PdbFileHeader) == 128, "the PDB file header is 128 bytes");
 constexpr char kPdbMagic[8] = {'C', 'B', 'D', 'F', 'S', 'P', 'D', 'B'};
 
+// entries of a table for (domain, k, div): sliding-tile patterns of k tiles have
+// N!/(N-k)! ranks (N = 9 or 16 cells, k <= N-1); the cube's table is the 8-corner one, 8! 3^7
+// entries; DIV compression keeps ceil(ranks / div).  0 when the pattern is not one of these.
+uint64_t table_entries(int domain, int k, uint32_t div) {
+    if (div < 1) return 0;
+    uint64_t ranks = 0;
+    if (domain == CBDFS_DOM_STP3 || domain == CBDFS_DOM_STP4) {
+        const int N = domain == CBDFS_DOM_STP3 ? 9 : 16;
+        if (k < 1 || k > N - 1) return 0;
+        ranks = 1;
+        for (int i = 0; i < k; ++i) ranks *= (uint64_t)(N - i);
+    } else if (domain == CBDFS_DOM_RC3) {
+        if (k != 8) return 0;
+        ranks = 40320ull * 2187ull;
+    } else {
+        return 0;
+    }
+    return (ranks + div - 1) / div;
+}
+
 struct File {
     FILE *f = nullptr;
     ~File() {
@@ -57,6 +77,10 @@ int cbdfs_pdb_file_write(const char *path, int domain, const int *tiles, int k, 
                          const uint8_t *table, uint64_t entries) {
     if (!path || !tiles || (!table && entries)) return fail(CBDFS_EINVAL, "null argument");
     if (domain < 0 || domain > 2 || k < 1 || k > 16 || div < 1) return fail(CBDFS_EINVAL, "pattern");
+    if (entries != table_entries(domain, k, div))
+        return fail(CBDFS_EINVAL, "%llu entries; a table of %d tiles (domain %d, DIV %u) has %llu",
+                    (unsigned long long)entries, k, domain, div,
+                    (unsigned long long)table_entries(domain, k, div));
     PdbFileHeader hd;
     std::memset(&hd, 0, sizeof hd);
     std::memcpy(hd.magic, kPdbMagic, 8);
@@ -91,6 +115,12 @@ int cbdfs_pdb_file_read(const char *path, int *domain, int *tiles, int *k, uint3
         return fail(CBDFS_EINVAL, "%s is not a PDB file", path);
     if (hd.version != 1) return fail(CBDFS_EINVAL, "%s: format version %u", path, hd.version);
     if (hd.k < 1 || hd.k > 16) return fail(CBDFS_EINVAL, "%s: pattern size %d", path, hd.k);
+    if (hd.domain < 0 || hd.domain > 2) return fail(CBDFS_EINVAL, "%s: domain %d", path, hd.domain);
+    if (hd.div < 1) return fail(CBDFS_EINVAL, "%s: DIV factor %u", path, hd.div);
+    if (hd.entries != table_entries(hd.domain, hd.k, hd.div))
+        return fail(CBDFS_EINVAL, "%s: %llu entries, but a table of %d tiles (domain %d, DIV %u) has %llu", path,
+                    (unsigned long long)hd.entries, hd.k, hd.domain, hd.div,
+                    (unsigned long long)table_entries(hd.domain, hd.k, hd.div));
     *domain = hd.domain;
     *k = hd.k;
     for (int i = 0; i < 16; ++i) tiles[i] = hd.tiles[i];
