@@ -184,3 +184,47 @@ def fp8_act_scales(orc, dom, Ws, bs, states, margin=1.0):
 def normwise(y_gpu, y64):
     y64 = np.asarray(y64, np.float64)
     return float(np.linalg.norm(np.asarray(y_gpu, np.float64) - y64) / np.linalg.norm(y64))
+
+
+def cube_classifier_net(Ws, bs, noise=0.3):
+    """A cube classifier of the given shape (480 -> H1 -> H2 -> H3 -> C, C >= 21) whose class
+    logits are -|c - x(s)| plus `noise` times the seeded network's own logits, with x(s) =
+    (cubies not in their home slot with zero twist or flip) / 8.  A face turn moves 8 cubies,
+    so ceil(x) never exceeds the distance to the goal; the argmax lies near x, and the noise
+    moves it where two classes are close, so the network, not a fixed rule, decides h.
+    Hidden unit 0 of the first layer computes x (weight 1/8 on every one-hot entry other than
+    a cubie's home entry); units 1..2C of the second compute relu(x - c) and relu(c - x);
+    the third passes them on; the last layer adds each class's pair with weight -1.  Every
+    weight and stored value of that part is exact in BF16."""
+    Ws = [np.array(w, np.float32, copy=True) for w in Ws]
+    bs = [np.array(b, np.float32, copy=True) for b in bs]
+    C = Ws[-1].shape[0]
+    k = 1 + 2 * C  # units carrying the construction in the second and third hidden layers
+    w0 = np.full(Ws[0].shape[1], 0.125, np.float32)
+    for c in range(8):
+        w0[c * 24 + c * 3] = 0.0            # corner cubie c home: slot c, twist 0
+    for e in range(12):
+        w0[192 + e * 24 + e * 2] = 0.0      # edge cubie e home: slot e, flip 0
+    Ws[0][0, :] = w0
+    bs[0][0] = 0.0
+    W1, b1 = Ws[1], bs[1]
+    W1[:k, :] = 0.0
+    W1[k:, 0] = 0.0
+    b1[:k] = 0.0
+    for c in range(C):
+        W1[1 + 2 * c, 0], b1[1 + 2 * c] = 1.0, -float(c)
+        W1[2 + 2 * c, 0], b1[2 + 2 * c] = -1.0, float(c)
+    for l in range(2, len(Ws) - 1):
+        Ws[l][:k, :] = 0.0
+        Ws[l][k:, :k] = 0.0
+        for j in range(1, k):
+            Ws[l][j, j] = 1.0
+        bs[l][:k] = 0.0
+    WL = Ws[-1] * np.float32(noise)
+    WL[:, :k] = 0.0
+    for c in range(C):
+        WL[c, 1 + 2 * c] = -1.0
+        WL[c, 2 + 2 * c] = -1.0
+    Ws[-1] = WL
+    bs[-1] = bs[-1] * np.float32(noise)
+    return Ws, bs
