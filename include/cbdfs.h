@@ -519,6 +519,10 @@ typedef struct {
                                                  partition too): entry i counts the batches of
                                                  2^i .. 2^(i+1)-1 states (the last: 2^15 and
                                                  more); the entries add up to `batches` */
+    double gpu_busy_s;              /* wall time during which at least one GPU batch was in flight
+                                       (from its submission until the batch processor saw it
+                                       complete); gpu_busy_s / seconds bounds the GPU's busy
+                                       fraction from above */
 } cbdfs_result;
 
 /* Solve from `start` (packed words).  heur_id: a network, a PDB or a built-in id.

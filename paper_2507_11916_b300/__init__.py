@@ -127,7 +127,7 @@ class Result(ctypes.Structure):
                 ("work_items", ctypes.c_int64), ("batch_fill_us", ctypes.c_double),
                 ("batch_flight_us", ctypes.c_double), ("submit_us", ctypes.c_double),
                 ("real_valued", ctypes.c_int), ("iter_bound_real", ctypes.c_double * MAX_ITERS),
-                ("batch_hist", ctypes.c_int64 * 16)]
+                ("batch_hist", ctypes.c_int64 * 16), ("gpu_busy_s", ctypes.c_double)]
 
 
 _vp, _u64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)
@@ -592,7 +592,8 @@ def cbdfs_solve(ctx, domain, start, algo=ALGO_IDA, heur_id=HEUR_MD, partial_ok=F
                 n_iters=r.n_iters, expanded=r.expanded, generated=r.generated,
                 batches=r.batches, evaluated=r.evaluated, seconds=r.seconds, d_init=r.d_init,
                 work_items=r.work_items, batch_fill_us=r.batch_fill_us,
-                batch_flight_us=r.batch_flight_us, submit_us=r.submit_us, batch_hist=list(r.batch_hist))
+                batch_flight_us=r.batch_flight_us, submit_us=r.submit_us, batch_hist=list(r.batch_hist),
+                gpu_busy_s=r.gpu_busy_s)
 
 
 def cbdfs_cancel(ctx):

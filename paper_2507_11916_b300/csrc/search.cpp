@@ -119,6 +119,8 @@ struct Shared {
     std::atomic<int64_t> expanded{0}, generated{0}, evaluated{0}, nbatches{0};
     int64_t hist[CBDFS_BATCH_HIST] = {};  // batches by size class (processor thread only)
     int64_t fill_ns = 0, flight_ns = 0, submit_ns = 0;  // batch timing sums (processor thread)
+    int64_t busy_ns = 0;                  // time with at least one batch in flight (processor thread)
+    Clock::time_point busy_from;
     std::atomic<uint32_t> minf{kNone};
     std::atomic<int> found{0}, stop{0}, cut{0};
     std::mutex sol_mu;
@@ -220,6 +222,8 @@ void processor(Shared &S) {
                     b.done_gen.store(b.gen, std::memory_order_release);
                     inflight[i] = inflight.back();
                     inflight.pop_back();
+                    if (inflight.empty())
+                        S.busy_ns += std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - S.busy_from).count();
                     progress = true;
                     continue;
                 }
@@ -261,6 +265,7 @@ void processor(Shared &S) {
                     S.stop = 1;
                     break;
                 }
+                if (inflight.empty()) S.busy_from = Clock::now();
                 inflight.push_back(pick);
                 progress = true;
             }
@@ -511,7 +516,7 @@ struct Solver {
     std::vector<std::unique_ptr<Batch>> batches;
     int64_t evaluated = 0, nbatches = 0, search_batches = 0;
     int64_t hist[CBDFS_BATCH_HIST] = {};
-    int64_t fill_ns = 0, flight_ns = 0, submit_ns = 0;
+    int64_t fill_ns = 0, flight_ns = 0, submit_ns = 0, busy_ns = 0;
     double seconds = 0;
     int64_t expanded_total = 0;
 
@@ -720,6 +725,7 @@ struct Solver {
         fill_ns += S.fill_ns;
         flight_ns += S.flight_ns;
         submit_ns += S.submit_ns;
+        busy_ns += S.busy_ns;
         if (S.error.load()) return fail(S.error.load(), "%s", S.error_msg.c_str());
         o.expanded += S.expanded.load();
         o.generated += S.generated.load();
@@ -1030,6 +1036,7 @@ int cbdfs_solve(cbdfs_ctx *ctx, int domain, const uint64_t *start, int algo, int
     out->batch_fill_us = sv.fill_ns / nb / 1e3;
     out->batch_flight_us = sv.flight_ns / nb / 1e3;
     out->submit_us = sv.submit_ns / nb / 1e3;
+    out->gpu_busy_s = sv.busy_ns / 1e9;
     out->d_init = sv.d_init;
     out->work_items = sv.tree.empty() ? 0 : (int64_t)(sv.level_start[sv.d_init + 1] - sv.level_start[sv.d_init]);
     out->seconds = std::chrono::duration<double>(Clock::now() - t0).count();
