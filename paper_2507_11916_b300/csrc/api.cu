@@ -3,6 +3,7 @@
 // pipeline, and the host-buffer / device-buffer evaluation calls.
 #include <cuda_fp8.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -57,6 +58,10 @@ static void free_net_buffers(NetGPU &n) {
     }
     if (n.w_split) cudaFree(n.w_split);
 }
+
+// tables of an additive PDB that together fit in this many bytes are kept in L2 (half of
+// the B300's 126 MB)
+constexpr size_t kL2KeepBytes = 64ull << 20;
 
 static bool chain_ok(const NetGPU &net) {
     if (net.prec == CBDFS_PREC_FP32) return false;
@@ -474,6 +479,21 @@ int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
                 P.tiles[q][i] = p.tiles[q][i];
                 P.weight[q][i] = (uint32_t)npk(N - 1 - i, p.k[q] - 1 - i);
             }
+        }
+        // L2 priorities: the smallest tables that fit in half the L2 together stay resident
+        // (their lookups hit it once warm), and the larger tables' random lines are evicted
+        // first so that they do not push the small ones out
+        {
+            size_t kept = 0;
+            uint32_t order[4] = {0, 1, 2, 3};
+            std::sort(order, order + p.n_patterns, [&](uint32_t a, uint32_t b) { return p.entries[a] < p.entries[b]; });
+            for (int j = 0; j < p.n_patterns; ++j) {
+                const uint32_t q = order[j];
+                if (kept + p.entries[q] > kL2KeepBytes) break;
+                kept += p.entries[q];
+                P.l2_keep |= 1u << q;
+            }
+            if (P.l2_keep == (1u << p.n_patterns) - 1) P.l2_keep = 0;  // all fit: plain caching
         }
         int r = pdb_gather(domain, P, d_states, n, d_g, bound, d_h, d_mask, d_minf, st);
         return r ? r : mark(s, st);

@@ -104,6 +104,8 @@ struct PdbParams {
     uint32_t entries[4];     // table sizes: N!/(N-k)!, or ceil of that / div
     uint32_t div;            // DIV compression of every table (1: none)
     const uint8_t *table[4];
+    uint32_t l2_keep;        // bit q: table q's lines are kept in L2 (evict-last), the other
+                             // tables' lines go first (evict-first); 0: no priorities
 };
 
 // composite heuristic: [MD] + sum over groups of the minimum over each group's members

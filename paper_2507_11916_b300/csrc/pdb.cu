@@ -3,7 +3,9 @@
 // k_pdb_gather: the plain heuristic and fallback.  One state per lane: the packed state is
 // inverted in registers (where[tile] = cell, a 64-bit nibble word), each pattern's cells
 // are ranked lexicographically among the k-permutations of the N cells with popcounts, the
-// table bytes are gathered (all patterns' loads issued together) and summed; the warp then
+// table bytes are gathered (all patterns' loads issued together; when the host marks some
+// tables to keep in L2, with an evict-last priority for theirs and evict-first for the
+// others') and summed; the warp then
 // forms the bound-test mask word with a ballot and the least f above the bound with a
 // reduction.  (Paper, Background: PDB heuristics; Experimental Setup: additive tile PDBs.)
 //
@@ -23,6 +25,13 @@ namespace cbdfs {
 namespace {
 
 using namespace dev;
+
+// a table byte through L2 with an eviction priority (a cache-policy operand from createpolicy)
+__device__ __forceinline__ uint32_t ld_table_byte(const uint8_t *p, uint64_t policy) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(policy));
+    return v;
+}
 
 template <int SIDE>
 __global__ void __launch_bounds__(256)
@@ -64,8 +73,21 @@ k_pdb_gather(const uint64_t *__restrict__ states, uint32_t n, const PdbParams P,
 #pragma unroll
     // a malformed state (a repeated tile) can rank past its table: clamp, so that such input
     // gives a meaningless h but no out-of-bounds read
+    if (P.l2_keep) {
+        // the kept tables' lines are evicted last, the others' first (L2 eviction priority)
+        uint64_t keep, stream;
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream));
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = (q < P.n_patterns) ? __ldg(P.table[q] + min(rank[q] / P.div, P.entries[q] - 1u)) : 0u;
+        for (int q = 0; q < 4; ++q)
+            v[q] = (q < P.n_patterns)
+                       ? ld_table_byte(P.table[q] + min(rank[q] / P.div, P.entries[q] - 1u),
+                                       ((P.l2_keep >> q) & 1u) ? keep : stream)
+                       : 0u;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = (q < P.n_patterns) ? __ldg(P.table[q] + min(rank[q] / P.div, P.entries[q] - 1u)) : 0u;
+    }
     uint32_t hv = v[0] + v[1] + v[2] + v[3];
     hv = (s == goal) ? 0u : min(hv, 255u);
     uint32_t f = 0xFFFFFFFFu;
