@@ -579,45 +579,62 @@ def train_leg(P, args):
 
 
 def serve_leg(P, args):
-    """Mixed requests (15-puzzle 81-class network and cube network, BF16; sizes log-uniform in
-    32..4096) from many threads through the continuous-batching server."""
-    import concurrent.futures as cf
+    """Mixed requests (15-puzzle 81-class network and cube network; sizes log-uniform in
+    32..4096) through the continuous-batching server, from native client threads that each
+    block on their request (64 search threads, each waiting on its batch), in BF16, E4M3 and
+    FP32.  The server merges the requests queued behind the launch in flight (32-row aligned)
+    and tests each request's own bound on the device.  Every result is checked against the
+    request evaluated alone (a sample of 100)."""
     import numpy as np
     ctx = P.cbdfs_create(0, max_batch=8192, n_slots=6)
     try:
         W3, b3 = W.net_weights(**W.NET_C3)
         W2, b2 = W.net_weights(**W.NET_C2)
-        ids = [P.cbdfs_net_load(ctx, P.DOM_STP4, W3, b3, P.PREC_BF16, P.HEAD_CLASSIFIER, 1),
-               P.cbdfs_net_load(ctx, P.DOM_RC3, W2, b2, P.PREC_BF16, P.HEAD_CLASSIFIER, 0)]
+        prec_ids = {"bf16": P.PREC_BF16, "fp8": P.PREC_FP8, "fp32": P.PREC_FP32}
+        nets = {}
+        for name, pr in prec_ids.items():
+            kw3 = {"act_scales": calib_scales(W3, b3, P.DOM_STP4)} if name == "fp8" else {}
+            kw2 = {"act_scales": calib_scales(W2, b2, P.DOM_RC3)} if name == "fp8" else {}
+            nets[name] = [P.cbdfs_net_load(ctx, P.DOM_STP4, W3, b3, pr, P.HEAD_CLASSIFIER, 1, **kw3),
+                          P.cbdfs_net_load(ctx, P.DOM_RC3, W2, b2, pr, P.HEAD_CLASSIFIER, 0, **kw2)]
         rng = W.SplitMix64(0xC4)
         reqs = []
         for i in range(args.serve_requests):
             size = int(round(32 * (4096 / 32) ** rng.uniform()))
             kind = rng.below(2)
             st = W.random_stp_states(4, size, i) if kind == 0 else W.random_rc_states(size, i).reshape(-1)
-            reqs.append((kind, st, np.zeros(size, np.uint8)))
-        P.cbdfs_server_start(ctx, max_inflight=5, bucket_max=4096, coalesce=1)
-        # warm the graphs, then the timed mix
-        for kind, st, g in reqs[:16]:
-            P.heur_request_submit(ctx, ids[kind], P.DOM_STP4 if kind == 0 else P.DOM_RC3, st, g, 60).wait()
-        P.cbdfs_server_stop(ctx)
-        P.cbdfs_server_start(ctx, max_inflight=5, bucket_max=4096, coalesce=1)
-
-        def run(k):
-            for j in range(k, len(reqs), args.serve_threads):
-                kind, st, g = reqs[j]
-                P.heur_request_submit(ctx, ids[kind], P.DOM_STP4 if kind == 0 else P.DOM_RC3, st, g, 60).wait()
-
-        t0 = time.perf_counter()
-        with cf.ThreadPoolExecutor(args.serve_threads) as ex:
-            list(ex.map(run, range(args.serve_threads)))
-        wall = time.perf_counter() - t0
-        stats = P.cbdfs_server_get_stats(ctx)
-        P.cbdfs_server_stop(ctx)
-        stats["wall_states_per_s"] = stats["states"] / wall
-        stats["threads"] = args.serve_threads
-        stats["workload"] = "15-puzzle 81-class and cube 21-class BF16 networks, request sizes log-uniform 32..4096"
-        return stats
+            g = (W.splitmix64_array(i + 17, size) % np.uint64(30)).astype(np.uint8)
+            reqs.append((kind, st, g, 20 + rng.below(40)))
+        doms = (P.DOM_STP4, P.DOM_RC3)
+        out = {"workload": "15-puzzle 81-class and cube 21-class networks, request sizes log-uniform 32..4096, "
+                           "bounds 20..59", "requests": len(reqs), "states": int(sum(len(r[2]) for r in reqs)),
+               "clients": f"{args.serve_threads} native threads, each blocking on its request",
+               "server": "max_inflight 3, bucket_max 8192, coalesce, graphs prepared before the timed requests"}
+        for name, ids in nets.items():
+            batch = [(ids[k], doms[k], st, g, b) for k, st, g, b in reqs]
+            P.cbdfs_server_start(ctx, max_inflight=3, bucket_max=8192, coalesce=1)
+            for k in (0, 1):  # every bucket's graph captured before the timed requests
+                P.cbdfs_server_prepare(ctx, ids[k], doms[k])
+            P.cbdfs_server_drive(ctx, batch[:64], threads=8, depth=1)
+            P.cbdfs_server_reset_stats(ctx)
+            secs, got = P.cbdfs_server_drive(ctx, batch, threads=args.serve_threads, depth=1)
+            st = P.cbdfs_server_get_stats(ctx)
+            P.cbdfs_server_stop(ctx)
+            for j in range(0, len(reqs), max(1, len(reqs) // 100)):
+                want = P.heur_submit_batch(ctx, batch[j][0], batch[j][1], batch[j][2], batch[j][3], batch[j][4])
+                assert np.array_equal(got[j][0], want[0]) and np.array_equal(got[j][1], want[1]) \
+                    and got[j][2] == want[2], "served result differs from the request alone"
+            out[name] = {"states_per_s": st["states"] / secs, "p50_us": st["p50_us"], "p99_us": st["p99_us"],
+                         "mean_us": st["mean_us"], "launches": st["launches"],
+                         "requests_per_launch": st["requests"] / max(st["launches"], 1), "seconds": secs,
+                         "host_us_per_launch": {"stage": st["stage_us_per_launch"], "replay": st["replay_us_per_launch"],
+                                                "in_flight": st["flight_us_per_launch"],
+                                                "finish": st["finish_us_per_launch"]}}
+        for name in ("bf16", "fp8"):
+            out[f"{name}_over_fp32"] = out[name]["states_per_s"] / out["fp32"]["states_per_s"]
+        out["states_per_s"] = out["bf16"]["states_per_s"]
+        assert P.cbdfs_device_status(ctx) == 0
+        return out
     finally:
         P.cbdfs_destroy(ctx)
 

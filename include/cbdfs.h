@@ -356,8 +356,9 @@ int cbdfs_debug_withhold_publish(cbdfs_ctx *ctx, int row_block);
  * as soon as an evaluation slot is free and the memory budget allows, replays the CUDA
  * graph captured for (slot, heuristic, size bucket = next power of two), and lets launches
  * on different slots overlap on the device.  Each request's h is exactly what it would get
- * alone (rows are independent); its mask and least f above its own bound are formed at
- * completion.  Caller buffers must stay valid until heur_request_wait returns.
+ * alone (rows are independent); each request starts on a 32-row boundary of its launch, so
+ * its mask and least f above its own bound are formed on the device in the same graph.
+ * Caller buffers must stay valid until heur_request_wait returns.
  * ------------------------------------------------------------------------------------- */
 
 typedef struct {
@@ -366,12 +367,18 @@ typedef struct {
     uint32_t bucket_max;    /* largest launch size and largest request (0 = 4096) */
     size_t mem_budget;      /* device bytes in-flight launches may use; 0 = no limit */
     int coalesce;           /* 1: merge queued requests of one heuristic into a launch */
+    int direct;             /* 1: enqueue each launch's pipeline on the slot's stream instead of
+                               replaying the captured graph of its bucket */
 } cbdfs_server_cfg;
 
 typedef struct {
     uint64_t requests, states, launches;
     double p50_us, p99_us, mean_us;   /* request latency, submit to completion */
     double states_per_s;              /* states completed / (last completion - first submit) */
+    /* the server thread's time per launch: taking requests, staging and launching; from the
+       launch until its completion was seen; copying results out and waking the callers */
+    double stage_us_per_launch, flight_us_per_launch, finish_us_per_launch;
+    double replay_us_per_launch;      /* of the staging time: the graph launch call itself */
 } cbdfs_server_stats;
 
 /* Start the server (at most one per context).  Errors: EINVAL (no free slot, buckets),
@@ -390,6 +397,32 @@ int heur_request_submit(cbdfs_ctx *ctx, int heur_id, int domain, const uint64_t 
 int heur_request_wait(cbdfs_ctx *ctx, cbdfs_ticket t, uint64_t timeout_us);
 /* Latency and throughput of the requests completed so far. */
 int cbdfs_server_get_stats(cbdfs_ctx *ctx, cbdfs_server_stats *out);
+/* Forget the statistics gathered so far (for instance after a warm-up). */
+int cbdfs_server_reset_stats(cbdfs_ctx *ctx);
+/* Capture the CUDA graph of every size bucket of one heuristic on every server slot now,
+ * instead of on each bucket's first request (a capture takes milliseconds).  Waits for slots
+ * in use.  Errors: EINVAL (no server, heuristic id), EDEVICE. */
+int cbdfs_server_prepare(cbdfs_ctx *ctx, int heur_id, int domain);
+
+/* One request of cbdfs_server_drive (the arguments of heur_request_submit; caller-owned
+ * buffers that stay valid until the call returns). */
+typedef struct {
+    int heur_id, domain;
+    const uint64_t *states;
+    const uint8_t *g;
+    uint32_t bound, n;
+    uint8_t *h_out;
+    uint32_t *mask_out, *minf_out;
+} cbdfs_request;
+
+/* Measurement of the running server with native clients (no counterpart in the paper; the
+ * paper's clients are its search threads): `threads` client threads submit reqs[t],
+ * reqs[t + threads], ... and each keeps at most `depth` of its own requests outstanding (depth
+ * 1: a client blocks on every request, as a search thread blocks on its batch).  Returns when
+ * every request is done; *seconds is the wall time from the first submission to the last
+ * completion.  Errors: EINVAL, or the first failed request's status. */
+int cbdfs_server_drive(cbdfs_ctx *ctx, const cbdfs_request *reqs, uint32_t n_reqs, int threads, int depth,
+                       double *seconds);
 
 /* ---------------------------------------------------------------------------------------
  * Learning the network heuristic (paper: Experimental Setup -- the heuristics are trained

@@ -97,6 +97,12 @@ class TrainReport(ctypes.Structure):
                 ("first_loss", ctypes.c_float), ("last_loss", ctypes.c_float)]
 
 
+class DriveRequest(ctypes.Structure):
+    _fields_ = [("heur_id", ctypes.c_int), ("domain", ctypes.c_int), ("states", ctypes.c_void_p),
+                ("g", ctypes.c_void_p), ("bound", ctypes.c_uint32), ("n", ctypes.c_uint32),
+                ("h_out", ctypes.c_void_p), ("mask_out", ctypes.c_void_p), ("minf_out", ctypes.c_void_p)]
+
+
 class Ticket(ctypes.Structure):
     _fields_ = [("id", ctypes.c_uint64)]
 
@@ -104,13 +110,15 @@ class Ticket(ctypes.Structure):
 class ServerCfg(ctypes.Structure):
     _fields_ = [("max_inflight", ctypes.c_int), ("bucket_min", ctypes.c_uint32),
                 ("bucket_max", ctypes.c_uint32), ("mem_budget", ctypes.c_size_t),
-                ("coalesce", ctypes.c_int)]
+                ("coalesce", ctypes.c_int), ("direct", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("requests", ctypes.c_uint64), ("states", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
-                ("states_per_s", ctypes.c_double)]
+                ("states_per_s", ctypes.c_double), ("stage_us_per_launch", ctypes.c_double),
+                ("flight_us_per_launch", ctypes.c_double), ("finish_us_per_launch", ctypes.c_double),
+                ("replay_us_per_launch", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):
@@ -133,6 +141,8 @@ class Result(ctypes.Structure):
 _vp, _u64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)
 _lib.cbdfs_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(_vp)]
 _lib.cbdfs_destroy.argtypes = [_vp]
+_lib.cbdfs_server_drive.argtypes = [_vp, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_double)]
 _lib.cbdfs_debug_withhold_publish.argtypes = [_vp, ctypes.c_int]
 _lib.cbdfs_destroy.restype = None
 _lib.cbdfs_last_error.restype = ctypes.c_char_p
@@ -203,7 +213,7 @@ EXPORTED = ["cbdfs_create", "cbdfs_destroy", "cbdfs_last_error", "cbdfs_mem_used
             "cbdfs_device_status", "cbdfs_debug_withhold_publish", "cbdfs_eval_profile", "cbdfs_eval_trace", "net_train",
             "cbdfs_train_grad", "cbdfs_net_read", "cbdfs_train_save", "cbdfs_train_load",
             "cbdfs_pdb_file_write", "cbdfs_pdb_file_read", "cbdfs_gen_walk_states", "cbdfs_server_start",
-            "cbdfs_server_stop", "heur_request_submit", "heur_request_wait", "cbdfs_server_get_stats", "cbdfs_apply_moves", "cbdfs_manhattan", "cbdfs_solve",
+            "cbdfs_server_stop", "cbdfs_server_drive", "cbdfs_server_prepare", "cbdfs_server_reset_stats", "heur_request_submit", "heur_request_wait", "cbdfs_server_get_stats", "cbdfs_apply_moves", "cbdfs_manhattan", "cbdfs_solve",
             "cbdfs_search_defaults", "cbdfs_cancel"]
 
 
@@ -503,13 +513,41 @@ def cbdfs_gen_walk_states(ctx, domain, tag, first, n, max_len) -> np.ndarray:
     return out
 
 
-def cbdfs_server_start(ctx, max_inflight=0, bucket_min=32, bucket_max=4096, mem_budget=0, coalesce=1):
+def cbdfs_server_start(ctx, max_inflight=0, bucket_min=32, bucket_max=4096, mem_budget=0, coalesce=1, direct=0):
     _check(_lib.cbdfs_server_start(ctx, ctypes.byref(ServerCfg(max_inflight, bucket_min, bucket_max,
-                                                               mem_budget, coalesce))))
+                                                               mem_budget, coalesce, direct))))
 
 
 def cbdfs_server_stop(ctx):
     _check(_lib.cbdfs_server_stop(ctx))
+
+
+def cbdfs_server_prepare(ctx, heur_id, domain):
+    _check(_lib.cbdfs_server_prepare(ctx, heur_id, domain))
+
+
+def cbdfs_server_reset_stats(ctx):
+    _check(_lib.cbdfs_server_reset_stats(ctx))
+
+
+def cbdfs_server_drive(ctx, reqs, threads=64, depth=1):
+    """reqs: (heur_id, domain, states, g, bound) tuples, driven through the running server by
+    native client threads.  Returns (seconds, [(h, mask, minf), ...]) in request order."""
+    keep, outs = [], []
+    arr = (DriveRequest * max(1, len(reqs)))()
+    for k, (heur, dom, s, g, bound) in enumerate(reqs):
+        s = np.ascontiguousarray(s, dtype=np.uint64)
+        g = np.ascontiguousarray(g, dtype=np.uint8)
+        n = len(g)
+        h = np.empty(n, np.uint8)
+        m = np.empty((n + 31) // 32, np.uint32)
+        f = np.empty(1, np.uint32)
+        keep.append((s, g))
+        outs.append((h, m, f))
+        arr[k] = DriveRequest(heur, dom, _ptr(s), _ptr(g), bound, n, _ptr(h), _ptr(m), _ptr(f))
+    sec = ctypes.c_double()
+    _check(_lib.cbdfs_server_drive(ctx, arr, len(reqs), threads, depth, ctypes.byref(sec)))
+    return sec.value, [(h, m, int(f[0])) for h, m, f in outs]
 
 
 class Request:

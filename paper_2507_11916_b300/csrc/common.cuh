@@ -201,6 +201,14 @@ int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states,
              const uint8_t *d_g, uint32_t bound, uint32_t n, uint8_t *d_h, uint32_t *d_mask,
              uint32_t *d_minf, float *d_y, cudaStream_t st);
 
+// the bound test of the requests packed into one served launch, each starting on a 32-row
+// boundary (segbound.cu): word w of the mask is request word_req[w]'s (0xFFFF: padding), its
+// rows end at req_end and pass at g + h <= req_bound; minw[w] gets the word's least f above
+// the bound (0xFFFFFFFF: none) and h_out a copy of h (pointers may be mapped host memory)
+int segment_bound(const uint8_t *d_h, const uint8_t *d_g, const uint16_t *d_word_req, const uint32_t *d_req_end,
+                  const uint32_t *d_req_bound, uint32_t n_words, uint8_t *h_out, uint32_t *d_mask, uint32_t *d_minw,
+                  cudaStream_t st);
+
 // a slot's outputs, one allocation: h [max_batch_pad] bytes, then mask [max_batch_pad / 32]
 // words, then minf (one word)
 // a network with the real-valued head (FP32 bounds and f-costs)

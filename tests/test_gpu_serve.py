@@ -125,3 +125,58 @@ def test_memory_budget_and_errors(P):
             P.heur_request_submit(ctx, hid, P.DOM_STP4, np.zeros(8, np.uint64), np.zeros(8, np.uint8), 1)
     finally:
         P.cbdfs_destroy(ctx)
+
+
+@pytest.mark.parametrize("threads,depth", [(64, 1), (8, 8)])
+def test_native_clients_mixed_burst(P, threads, depth):
+    # a burst of 15-puzzle (81-class and regression networks, Manhattan distance) and cube
+    # requests from native client threads; requests queue behind the launch in flight, are
+    # packed at 32-row boundaries and bound-tested on the device with their own bounds: each
+    # result is bit for bit the one the request gets alone
+    ctx = P.cbdfs_create(0, max_batch=8192, n_slots=4)
+    try:
+        W1, b1 = W.net_weights(**W.NET_C3)
+        W2, b2 = W.net_weights(**W.NET_C2)
+        ids = {0: P.cbdfs_net_load(ctx, P.DOM_STP4, W1, b1, PREC["bf16"], P.HEAD_CLASSIFIER, 1),
+               1: P.cbdfs_net_load(ctx, P.DOM_RC3, W2, b2, PREC["bf16"], P.HEAD_CLASSIFIER, 0),
+               2: P.HEUR_MD}
+        reqs = _mix(P, 300, 901 + threads)
+        inputs = [_inputs(P, kind, size, seed) for kind, size, bound, seed in reqs]
+        alone = [P.heur_submit_batch(ctx, ids[kind], dom, s, g, bound)
+                 for (kind, size, bound, seed), (dom, s, g) in zip(reqs, inputs)]
+        P.cbdfs_server_start(ctx, max_inflight=2, bucket_max=8192, coalesce=1)
+        secs, got = P.cbdfs_server_drive(
+            ctx, [(ids[kind], dom, s, g, bound) for (kind, size, bound, seed), (dom, s, g) in zip(reqs, inputs)],
+            threads=threads, depth=depth)
+        st = P.cbdfs_server_get_stats(ctx)
+        P.cbdfs_server_stop(ctx)
+        for i, ((h, mask, minf), (ah, amask, aminf)) in enumerate(zip(got, alone)):
+            assert np.array_equal(h, ah), f"request {i}: h differs"
+            assert np.array_equal(mask, amask) and minf == aminf, f"request {i}: bound test differs"
+        print(f"{threads} clients x {depth}: {st['launches']} launches for {len(reqs)} requests, "
+              f"{st['states'] / secs / 1e6:.1f} M states/s, p50 {st['p50_us']:.0f} us")
+        assert st["requests"] == len(reqs) and st["launches"] < len(reqs)  # requests were merged
+        assert P.cbdfs_device_status(ctx) == 0
+    finally:
+        P.cbdfs_destroy(ctx)
+
+
+def test_request_sizes_at_the_bucket_limit(P):
+    # requests whose 32-row packing reaches the largest bucket, with a bucket limit that is not
+    # a multiple of 32: every one is served and equals its stand-alone result
+    ctx = P.cbdfs_create(0, max_batch=4096, n_slots=2)
+    try:
+        ids = {2: P.HEUR_MD}
+        P.cbdfs_server_start(ctx, max_inflight=1, bucket_min=24, bucket_max=1000, coalesce=1)
+        reqs = [(2, n, 40, 7000 + n) for n in (1, 31, 33, 1000, 999, 968, 500, 501, 32, 64)]
+        inputs = [_inputs(P, kind, size, seed) for kind, size, bound, seed in reqs]
+        alone = [P.heur_submit_batch(ctx, P.HEUR_MD, dom, s, g, bound)
+                 for (kind, size, bound, seed), (dom, s, g) in zip(reqs, inputs)]
+        secs, got = P.cbdfs_server_drive(
+            ctx, [(ids[kind], dom, s, g, bound) for (kind, size, bound, seed), (dom, s, g) in zip(reqs, inputs)],
+            threads=2, depth=5)
+        P.cbdfs_server_stop(ctx)
+        for (h, mask, minf), (ah, amask, aminf) in zip(got, alone):
+            assert np.array_equal(h, ah) and np.array_equal(mask, amask) and minf == aminf
+    finally:
+        P.cbdfs_destroy(ctx)
