@@ -320,19 +320,26 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     ChainParams P{};
     P.nh = nh;
     for (int l = 0; l <= L; ++l) P.dims[l] = net.dims[l];
-    const uint32_t rows_pad = (n + kBM - 1) / kBM * kBM;
+    uint32_t rows_pad = (n + kBM - 1) / kBM * kBM;
+    // small batches: 64-wide tiles, so that a layer's tiles spread over more CTAs (the head
+    // partials then need four times the floats per row, within the slot's allocation)
+    const int bn = rows_pad / kBM <= kChainSmallMBlocks && 4 * rows_pad <= c->max_batch_pad ? kChainBNSmall : kChainBN;
+    // larger batches: CTA pairs (two row blocks per tile, tcgen05 cta_group::2), when the
+    // batch padded to 256 rows fits the slot and the device holds every pair at once
+    const uint32_t rows_pair = (n + 2 * kBM - 1) / (2 * kBM) * (2 * kBM);
+    const bool pair = bn == kChainBN && rows_pad / kBM >= kChainPairMinMBlocks && rows_pair <= c->max_batch_pad &&
+                      (c->num_sms & 1) == 0 && chain_pairs_fit(c->num_sms);
+    if (pair) rows_pad = rows_pair;
     P.mblocks = rows_pad / kBM;
     P.rows_pad = rows_pad;
     P.n = n;
-    // small batches: 64-wide tiles, so that a layer's tiles spread over more CTAs (the head
-    // partials then need four times the floats per row, within the slot's allocation)
-    const int bn = P.mblocks <= kChainSmallMBlocks && 4 * rows_pad <= c->max_batch_pad ? kChainBNSmall : kChainBN;
+    const int seq_mblocks = pair ? P.mblocks / 2 : P.mblocks;  // row blocks (pairs) in the tile sequence
     int max_tiles = 0;
     P.tile_start[0] = 0;
     P.fused_head = net.dims[L] <= kMaxHeadC && !net.head_cpad;
     P.bf16_store_layer = !P.fused_head && fp8 ? nh - 1 : -1;
     for (int l = 0; l < nh; ++l) {
-        maps.w[l] = bn == kChainBNSmall ? net.tm_w64[l] : net.tm_w[l];
+        maps.w[l] = bn == kChainBNSmall ? net.tm_w64[l] : pair ? net.tm_w128[l] : net.tm_w[l];
         if (l > 0) {
             const CUtensorMap *m = act_map(s, c, (l - 1) & 1, net.dims[l], eb);
             if (!m) return CBDFS_EDEVICE;
@@ -352,8 +359,8 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
         P.kdim[l] = l == 0 ? net.k1pad : net.dims[l] / net.groups;
         P.nt[l] = net.dims[l + 1] / bn;
         P.group_nt[l] = l > 0 && net.groups > 1 ? P.nt[l] / net.groups : 0;
-        P.tile_start[l + 1] = P.tile_start[l] + P.nt[l] * P.mblocks;
-        max_tiles = std::max(max_tiles, P.nt[l] * P.mblocks);
+        P.tile_start[l + 1] = P.tile_start[l] + P.nt[l] * seq_mblocks;
+        max_tiles = std::max(max_tiles, P.nt[l] * seq_mblocks);
         P.bias[l] = net.b32[l];
         P.acc_scale[l] = fp8 ? net.w_scale[l] * (l == 0 ? 1.f : net.a_scale[l - 1]) : 1.f;
         P.out_qscale[l] = fp8 ? 1.f / net.a_scale[l] : 1.f;
@@ -380,14 +387,14 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     P.err = c->d_err;
     P.wait_ns = c->wait_ns;
     P.hold_mblock = c->hold_mblock.exchange(-1);
-    const int grid = std::min(c->num_sms, max_tiles);
+    const int grid = pair ? 2 * std::min(c->num_sms / 2, max_tiles) : std::min(c->num_sms, max_tiles);
     if (s.trace) {
         P.trace = s.trace;
         P.trace_tiles = s.trace_tiles;
         *s.trace_grid = grid;
         CUDA_TRY(cudaMemsetAsync(s.trace, 0, sizeof(unsigned long long) * grid * s.trace_tiles * 8, st));
     }
-    int rc = chain_launch(domain, fp8, bn, maps, P, grid, st);
+    int rc = chain_launch(domain, fp8, bn, pair, maps, P, grid, st);
     if (rc || (rc = mark(s, st)) || P.fused_head) return rc;
     // the last layer over the stored BF16 activations of the last hidden layer: on the tensor
     // cores (split FP32 weights) for a prepared classifier head, else FP32 on the CUDA cores
@@ -746,6 +753,11 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
                 (rc = make_tmap_2d(&N.tm_w64[l], N.w_lp[l],
                                    fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                                    fp8 ? 1 : 2, (uint64_t)Kp, (uint64_t)O, kblk, kChainBNSmall)))
+                return rc;
+            if (O % kChainBN == 0 &&
+                (rc = make_tmap_2d(&N.tm_w128[l], N.w_lp[l],
+                                   fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                                   fp8 ? 1 : 2, (uint64_t)Kp, (uint64_t)O, kblk, kChainBN / 2)))
                 return rc;
         }
     }

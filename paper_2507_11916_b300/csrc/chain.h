@@ -8,6 +8,8 @@ constexpr int kChainBN = 256;     // output columns of a tile (one TMEM accumula
 constexpr int kChainBNSmall = 64; // the same for small batches (more tiles in flight per layer)
 constexpr int kChainSmallMBlocks = 2;  // batches of at most this many 128-state row blocks
 constexpr int kChainStages = 4;
+constexpr int kChainPairStages = 6;  // CTA pairs: 32 KB k-block stages (A rows + half the weights)
+constexpr int kChainPairMinMBlocks = 8;  // CTA pairs from this many 128-state row blocks on
 constexpr int kChainThreads = 192;
 constexpr int kMaxHeadC = 32;     // widest last layer the in-epilogue head takes
 
@@ -87,8 +89,12 @@ struct HeadTcParams {
 int head_tc(int domain, const CUtensorMap &tmA, const CUtensorMap &tmW, const HeadTcParams &P, uint32_t rows_pad,
             cudaStream_t st);
 
-// bn: kChainBN, or kChainBNSmall (maps.w with 64-row boxes)
-int chain_launch(int domain, bool fp8, int bn, const ChainMaps &maps, const ChainParams &P, int grid,
+// bn: kChainBN, or kChainBNSmall (maps.w with 64-row boxes).  pair: CTA pairs (bn = kChainBN,
+// maps.w with 128-row boxes, an even number of row blocks and of CTAs; the tile sequence in
+// P counts pair tiles)
+int chain_launch(int domain, bool fp8, int bn, bool pair, const ChainMaps &maps, const ChainParams &P, int grid,
                  cudaStream_t st);
+// whether the device holds all the CTA pairs of a one-CTA-per-SM launch at once
+bool chain_pairs_fit(int num_sms);
 
 }  // namespace cbdfs

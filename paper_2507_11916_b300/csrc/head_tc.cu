@@ -79,7 +79,7 @@ k_head_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             }
             // every load issued has landed before the CTA can exit (bounded)
             for (uint32_t j = issued > (uint32_t)kHtStages ? issued - kHtStages : 0; j < issued; ++j)
-                mbar_wait(smem_u32(&full[j % kHtStages]), (j / kHtStages) & 1, P.err, DEVERR_TMA_FULL, 100000000ull);
+                mbar_wait_drain(smem_u32(&full[j % kHtStages]), (j / kHtStages) & 1, P.err, DEVERR_TMA_FULL, 100000000ull);
         }
     } else if (warp == 1) {
         if (lane == 0) {

@@ -33,6 +33,7 @@
 // another bound) and reports through the error flag.
 #include <cuda_fp8.h>
 
+#include <map>
 #include <mutex>
 #include <set>
 
@@ -89,11 +90,15 @@ __device__ __forceinline__ void stamp(const ChainParams &P, uint32_t i, int k) {
 struct Tile {
     int l, m, n;
 };
-__device__ __forceinline__ Tile tile_of(const ChainParams &P, int t) {
+// tile t of the sequence as this CTA sees it: with CTA pairs, the sequence counts pair tiles
+// (two row blocks, 2p and 2p+1) and the CTA of rank r works on row block 2p + r
+template <bool PAIR>
+__device__ __forceinline__ Tile tile_of(const ChainParams &P, int t, uint32_t rank) {
     int l = 0;
     while (l + 1 < P.nh && t >= P.tile_start[l + 1]) ++l;
     const int local = t - P.tile_start[l];
-    return Tile{l, local / P.nt[l], local % P.nt[l]};
+    const int m = local / P.nt[l];
+    return Tile{l, PAIR ? 2 * m + (int)rank : m, local % P.nt[l]};
 }
 
 // The one-hot encoding (the network's input): slot j of the state (STP: tile j, whose value
@@ -225,11 +230,14 @@ __device__ __forceinline__ void finish_row(const ChainParams &P, uint32_t row_g,
     }
 }
 
-// BN: outputs of a tile (one TMEM accumulator); STAGES: depth of the (A, B) k-block ring
-template <int DOMAIN, bool FP8, int CMAX, int BN, int STAGES>
+// BN: outputs of a tile (one TMEM accumulator); STAGES: depth of the (A, B) k-block ring.
+// PAIR: a cluster of two CTAs computes each 256-row x BN tile with tcgen05 cta_group::2 MMAs
+// issued by the even CTA; each CTA loads its own 128 rows of A and half of the BN weight rows,
+// so a k-block stage is 32 KB per SM instead of 48 KB and the ring holds more stages.
+template <int DOMAIN, bool FP8, int CMAX, int BN, int STAGES, bool PAIR>
 __global__ void __launch_bounds__(kChainThreads, 1)
 k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainParams P) {
-    constexpr int kStageB = BN * 128;
+    constexpr int kStageB = (PAIR ? BN / 2 : BN) * 128;
     constexpr int HS = BN < 128 ? BN : 128;  // columns of a last-layer slice in shared memory
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -246,6 +254,10 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int total = P.tile_start[P.nh];
+    const uint32_t rank = PAIR ? cluster_ctarank() : 0;
+    const bool leader = rank == 0;
+    const int t0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;    // this CTA's first tile
+    const int tstride = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
     // stage and accumulator waits wait on work that itself waits on row-block counts: their
     // bound is twice the count wait's, so that a count that never comes is the wait that runs
     // out first and names the cause
@@ -259,10 +271,11 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&acc_full[b]), 1);
-            mbar_init(smem_u32(&acc_empty[b]), 4);
+            mbar_init(smem_u32(&acc_empty[b]), PAIR ? 8 : 4);  // the epilogue warps of both CTAs
         }
         mbar_init(smem_u32(drain), 1);
         fence_mbar_init();
+        if (PAIR) fence_mbar_init_cluster();
     }
     if (warp == 0 && lane == 0) {
         for (int l = 0; l < P.nh; ++l) {
@@ -271,11 +284,17 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
         }
     }
     if (warp == 1) {
-        tmem_alloc(smem_u32(tmem_slot), 2 * BN);
-        tmem_relinquish();
+        if (PAIR) {
+            tmem_alloc_pair(smem_u32(tmem_slot), 2 * BN);
+            tmem_relinquish_pair();
+        } else {
+            tmem_alloc(smem_u32(tmem_slot), 2 * BN);
+            tmem_relinquish();
+        }
     }
     tc_fence_before();
     __syncthreads();
+    if (PAIR) cluster_sync_all();  // the peer's barriers are initialised before any signal
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     constexpr int KBLK = FP8 ? 128 : 64;
@@ -344,8 +363,8 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
         // ------------------------------------------------------------- producer
         uint32_t it = 0, pi = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++pi) {
-            const Tile T = tile_of(P, t);
+        for (int t = t0; t < total && ok; t += tstride, ++pi) {
+            const Tile T = tile_of<PAIR>(P, t, rank);
             const int KB = P.kdim[T.l] / KBLK;
             const int kb0 = P.group_nt[T.l] ? (T.n / P.group_nt[T.l]) * KB : 0;  // member's K block
             if (lane == 0) stamp(P, pi, 0);
@@ -371,31 +390,43 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                     if (!w) { ok = false; break; }
                 }
                 if (lane == 0) {
-                    mbar_arrive_expect_tx(smem_u32(&full[s]), kStageA + kStageB);
-                    tma_load_2d(smem_u32(A + s * kStageA), &maps.a[T.l], smem_u32(&full[s]), (kb + kb0) * KBLK,
-                                T.m * kBM);
-                    tma_load_2d(smem_u32(B + s * kStageB), &maps.w[T.l], smem_u32(&full[s]), kb * KBLK,
-                                T.n * BN);
+                    if (PAIR) {
+                        // both CTAs' loads count on the leader's stage barrier, which the leader
+                        // arms for the pair's bytes; each CTA loads its rows and its half of B
+                        const uint32_t fb = mapa_shared(smem_u32(&full[s]), 0);
+                        if (leader) mbar_arrive_expect_tx(smem_u32(&full[s]), 2 * (kStageA + kStageB));
+                        tma_load_2d_pair(smem_u32(A + s * kStageA), &maps.a[T.l], fb, (kb + kb0) * KBLK, T.m * kBM);
+                        tma_load_2d_pair(smem_u32(B + s * kStageB), &maps.w[T.l], fb, kb * KBLK,
+                                         T.n * BN + (int)rank * (BN / 2));
+                    } else {
+                        mbar_arrive_expect_tx(smem_u32(&full[s]), kStageA + kStageB);
+                        tma_load_2d(smem_u32(A + s * kStageA), &maps.a[T.l], smem_u32(&full[s]), (kb + kb0) * KBLK,
+                                    T.m * kBM);
+                        tma_load_2d(smem_u32(B + s * kStageB), &maps.w[T.l], smem_u32(&full[s]), kb * KBLK,
+                                    T.n * BN);
+                    }
                 }
                 __syncwarp();
             }
             if (lane == 0) stamp(P, pi, 2);
         }
-        // every TMA load this CTA issued has landed before the CTA can exit (bounded)
-        if (lane == 0) {
+        // every TMA load this CTA issued has landed before the CTA can exit (bounded); with
+        // pairs the leader's barriers count both CTAs' loads, and the peer's loads have all been
+        // consumed by the leader's MMAs unless a wait ran out (see the end of the kernel)
+        if (lane == 0 && leader) {
             const uint32_t first = it > STAGES ? it - STAGES : 0;
             for (uint32_t j = first; j < it; ++j)
-                mbar_wait(smem_u32(&full[j % STAGES]), (j / STAGES) & 1, P.err,
-                          DEVERR_TMA_FULL, 100000000ull);
+                mbar_wait_drain(smem_u32(&full[j % STAGES]), (j / STAGES) & 1, P.err, DEVERR_TMA_FULL, 100000000ull);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------- MMA issuer
-        if (lane == 0) {
-            constexpr uint32_t idesc = FP8 ? make_idesc(kBM, BN, 0, 0) : make_idesc(kBM, BN, 1, 1);
+        if (lane == 0 && leader) {
+            constexpr int MM = PAIR ? 2 * kBM : kBM;  // the pair's MMA covers both CTAs' rows
+            constexpr uint32_t idesc = FP8 ? make_idesc(MM, BN, 0, 0) : make_idesc(MM, BN, 1, 1);
             uint32_t it = 0, i = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
-                const Tile T = tile_of(P, t);
+            for (int t = t0; t < total && ok; t += tstride, ++i) {
+                const Tile T = tile_of<PAIR>(P, t, rank);
                 const int KB = P.kdim[T.l] / KBLK;
                 const uint32_t b = i & 1, u = i >> 1;
                 if (i >= 2 && !mbar_wait(smem_u32(&acc_empty[b]), (u - 1) & 1, P.err, DEVERR_ACCUM, stage_ns)) break;
@@ -413,17 +444,32 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                     const uint64_t bd = sw128_desc(smem_u32(B + s * kStageB));
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        if (FP8) umma_fp8(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
-                        else umma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                        if (PAIR) {
+                            if (FP8) umma_fp8_pair(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                            else umma_bf16_pair(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                        } else {
+                            if (FP8) umma_fp8(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                            else umma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                        }
                     }
-                    umma_commit(smem_u32(&empty[s]));
+                    if (PAIR) umma_commit_pair(smem_u32(&empty[s]));  // both CTAs' stage is free
+                    else umma_commit(smem_u32(&empty[s]));
                 }
-                if (ok) umma_commit(smem_u32(&acc_full[b]));
+                if (ok) {
+                    if (PAIR) umma_commit_pair(smem_u32(&acc_full[b]));
+                    else umma_commit(smem_u32(&acc_full[b]));
+                }
                 stamp(P, i, 4);
             }
-            // all MMAs this thread issued have completed before TMEM is released (bounded)
-            umma_commit(smem_u32(drain));
-            mbar_wait(smem_u32(drain), 0, P.err, DEVERR_ACCUM, 100000000ull);
+            // all MMAs this thread issued have completed before TMEM is released (bounded); the
+            // pair's drain arrives in both CTAs
+            if (PAIR) umma_commit_pair(smem_u32(drain));
+            else umma_commit(smem_u32(drain));
+            mbar_wait_drain(smem_u32(drain), 0, P.err, DEVERR_ACCUM, 100000000ull);
+        } else if (PAIR && lane == 0) {
+            // the peer's TMEM is written by the leader's MMAs: wait for the leader's drain, which
+            // comes after the leader's whole tile loop
+            mbar_wait_drain(smem_u32(drain), 0, P.err, DEVERR_ACCUM, stage_ns + 100000000ull);
         }
     } else {
         // ------------------------------------------------------------- epilogue
@@ -431,8 +477,13 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
         const int row = q * 32 + lane;
         const int ep_tid = threadIdx.x - 64;
         uint32_t i = 0;
-        for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
-            const Tile T = tile_of(P, t);
+        // an accumulator is released to the (leader's) MMA issuer once this warp has read it
+        auto release_acc = [&](uint32_t b) {
+            if (PAIR && !leader) mbar_arrive_cluster(mapa_shared(smem_u32(&acc_empty[b]), 0));
+            else mbar_arrive(smem_u32(&acc_empty[b]));
+        };
+        for (int t = t0; t < total; t += tstride, ++i) {
+            const Tile T = tile_of<PAIR>(P, t, rank);
             const uint32_t b = i & 1, u = i >> 1;
             // the tile's biases into shared memory while the MMAs run (buffer i & 1 was last
             // read two tiles ago, before everyone passed the previous tile's barrier)
@@ -519,7 +570,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) {
-                    mbar_arrive(smem_u32(&acc_empty[b]));
+                    release_acc(b);
                     // publish this warp's 32 rows: stores complete, then the count (4 per tile)
                     bulk_wait_all();
                     fence_proxy_async_global();
@@ -572,7 +623,7 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
+                if (lane == 0) release_acc(b);
                 float *pp = P.partial + ((size_t)T.n * P.rows_pad + rg) * P.C;
 #pragma unroll
                 for (int o = 0; o < CMAX; ++o)
@@ -611,16 +662,29 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
     }
     tc_fence_before();
     __syncthreads();
+    if (PAIR) {
+        // after a wait ran out, loads the peer issued may not have been consumed: give them
+        // time to land (they always complete) before the CTA's shared memory goes away
+        if (threadIdx.x == 0 && *reinterpret_cast<volatile int *>(P.err) != 0) {
+            const uint64_t t_end = globaltimer() + 200000ull;
+            while (globaltimer() < t_end) __nanosleep(1000);
+        }
+        __syncthreads();
+        cluster_sync_all();  // neither CTA frees the pair's TMEM while the other still reads it
+    }
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, 2 * BN);
+        if (PAIR) tmem_dealloc_pair(tmem, 2 * BN);
+        else tmem_dealloc(tmem, 2 * BN);
     }
 }
 
 }  // namespace
 
-template <int BN, int STAGES>
-static size_t chain_smem_bytes() { return 1024 + STAGES * (kStageA + BN * 128) + kStaging + kBiasSmem + 256; }
+template <int BN, int STAGES, bool PAIR>
+static size_t chain_smem_bytes() {
+    return 1024 + STAGES * (kStageA + (PAIR ? BN / 2 : BN) * 128) + kStaging + kBiasSmem + 256;
+}
 
 // the kernel's dynamic shared-memory limit, raised once per kernel and device
 static int allow_smem(const void *kern, size_t smem) {
@@ -637,46 +701,96 @@ static int allow_smem(const void *kern, size_t smem) {
 
 // Launch the chain for one batch.  P.counters must be zero (they are after the previous
 // launch on the same counters, and after allocation).
-template <int D, bool F, int BN, int STAGES>
+template <int D, bool F, int BN, int STAGES, bool PAIR>
 static int launch_t(const ChainMaps &maps, const ChainParams &P, int grid, cudaStream_t st) {
-    const size_t smem = chain_smem_bytes<BN, STAGES>();
+    const size_t smem = chain_smem_bytes<BN, STAGES, PAIR>();
     void (*kern)(const ChainMaps, const ChainParams) =
-        P.C == 1 || !P.fused_head ? k_chain<D, F, 1, BN, STAGES>
-        : P.C <= 24              ? k_chain<D, F, 24, BN, STAGES>
-                                 : k_chain<D, F, kMaxHeadC, BN, STAGES>;
+        P.C == 1 || !P.fused_head ? k_chain<D, F, 1, BN, STAGES, PAIR>
+        : P.C <= 24              ? k_chain<D, F, 24, BN, STAGES, PAIR>
+                                 : k_chain<D, F, kMaxHeadC, BN, STAGES, PAIR>;
     if (int rc = allow_smem(reinterpret_cast<const void *>(kern), smem)) return rc;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kChainThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = PAIR ? 2 : 1;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, maps, P));
+    cfg.numAttrs = PAIR ? 2 : 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, P);
+    if (e != cudaSuccess && PAIR) {
+        // a driver that does not take the cooperative attribute with a cluster shape: the
+        // pairs are launched as a plain cluster launch (chain_pairs_fit has checked that the
+        // device holds all of them at once)
+        cudaGetLastError();
+        attr[0] = attr[1];
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, kern, maps, P);
+    }
+    if (e != cudaSuccess) return fail(CBDFS_EDEVICE, "chain launch: %s", cudaGetErrorString(e));
     return CBDFS_OK;
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool PAIR>
 static int launch_bn(int domain, bool fp8, const ChainMaps &maps, const ChainParams &P, int grid, cudaStream_t st) {
     if (fp8) {
-        if (domain == CBDFS_DOM_STP3) return launch_t<CBDFS_DOM_STP3, true, BN, STAGES>(maps, P, grid, st);
-        if (domain == CBDFS_DOM_STP4) return launch_t<CBDFS_DOM_STP4, true, BN, STAGES>(maps, P, grid, st);
-        return launch_t<CBDFS_DOM_RC3, true, BN, STAGES>(maps, P, grid, st);
+        if (domain == CBDFS_DOM_STP3) return launch_t<CBDFS_DOM_STP3, true, BN, STAGES, PAIR>(maps, P, grid, st);
+        if (domain == CBDFS_DOM_STP4) return launch_t<CBDFS_DOM_STP4, true, BN, STAGES, PAIR>(maps, P, grid, st);
+        return launch_t<CBDFS_DOM_RC3, true, BN, STAGES, PAIR>(maps, P, grid, st);
     }
-    if (domain == CBDFS_DOM_STP3) return launch_t<CBDFS_DOM_STP3, false, BN, STAGES>(maps, P, grid, st);
-    if (domain == CBDFS_DOM_STP4) return launch_t<CBDFS_DOM_STP4, false, BN, STAGES>(maps, P, grid, st);
-    return launch_t<CBDFS_DOM_RC3, false, BN, STAGES>(maps, P, grid, st);
+    if (domain == CBDFS_DOM_STP3) return launch_t<CBDFS_DOM_STP3, false, BN, STAGES, PAIR>(maps, P, grid, st);
+    if (domain == CBDFS_DOM_STP4) return launch_t<CBDFS_DOM_STP4, false, BN, STAGES, PAIR>(maps, P, grid, st);
+    return launch_t<CBDFS_DOM_RC3, false, BN, STAGES, PAIR>(maps, P, grid, st);
 }
 
-int chain_launch(int domain, bool fp8, int bn, const ChainMaps &maps, const ChainParams &P, int grid,
+int chain_launch(int domain, bool fp8, int bn, bool pair, const ChainMaps &maps, const ChainParams &P, int grid,
                  cudaStream_t st) {
     if (P.fused_head && (P.C < 1 || P.C > kMaxHeadC)) return fail(CBDFS_EINVAL, "fused head width %d", P.C);
-    if (bn == kChainBNSmall) return launch_bn<kChainBNSmall, 8>(domain, fp8, maps, P, grid, st);
-    if (bn == kChainBN) return launch_bn<kChainBN, kChainStages>(domain, fp8, maps, P, grid, st);
+    if (pair) {
+        if (bn != kChainBN || (grid & 1) || (P.mblocks & 1)) return fail(CBDFS_EINVAL, "CTA-pair chain shape");
+        return launch_bn<kChainBN, kChainPairStages, true>(domain, fp8, maps, P, grid, st);
+    }
+    if (bn == kChainBNSmall) return launch_bn<kChainBNSmall, 8, false>(domain, fp8, maps, P, grid, st);
+    if (bn == kChainBN) return launch_bn<kChainBN, kChainStages, false>(domain, fp8, maps, P, grid, st);
     return fail(CBDFS_EINVAL, "chain tile width %d", bn);
+}
+
+// whether this device can hold every CTA pair of a one-CTA-per-SM chain launch at once
+bool chain_pairs_fit(int num_sms) {
+    static std::mutex mu;
+    static std::map<int, bool> known;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = known.find(dev);
+    if (it != known.end()) return it->second;
+    void (*kern)(const ChainMaps, const ChainParams) = k_chain<CBDFS_DOM_STP4, false, 1, kChainBN, kChainPairStages, true>;
+    const size_t smem = chain_smem_bytes<kChainBN, kChainPairStages, true>();
+    bool ok = allow_smem(reinterpret_cast<const void *>(kern), smem) == CBDFS_OK;
+    if (ok) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(num_sms & ~1);
+        cfg.blockDim = dim3(kChainThreads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        ok = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess && clusters >= num_sms / 2;
+        cudaGetLastError();
+    }
+    known[dev] = ok;
+    return ok;
 }
 
 }  // namespace cbdfs

@@ -99,7 +99,7 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             }
             // bounded drain of this thread's loads before the CTA can exit
             for (uint32_t j = issued > (uint32_t)stages ? issued - stages : 0; j < issued; ++j)
-                mbar_wait(smem_u32(&full[j % stages]), (j / stages) & 1, err, DEVERR_TMA_FULL, 100000000ull);
+                mbar_wait_drain(smem_u32(&full[j % stages]), (j / stages) & 1, err, DEVERR_TMA_FULL, 100000000ull);
         }
     } else if (warp == 1) {
         if (lane == 0) {
