@@ -327,7 +327,7 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     // larger batches: CTA pairs (two row blocks per tile, tcgen05 cta_group::2), when the
     // batch padded to 256 rows fits the slot and the device holds every pair at once
     const uint32_t rows_pair = (n + 2 * kBM - 1) / (2 * kBM) * (2 * kBM);
-    const bool pair = bn == kChainBN && rows_pad / kBM >= kChainPairMinMBlocks && rows_pair <= c->max_batch_pad &&
+    const bool pair = net.has_w128 && bn == kChainBN && rows_pad / kBM >= kChainPairMinMBlocks && rows_pair <= c->max_batch_pad &&
                       (c->num_sms & 1) == 0 && chain_pairs_fit(c->num_sms);
     if (pair) rows_pad = rows_pair;
     P.mblocks = rows_pad / kBM;
@@ -722,6 +722,7 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
         const bool fp8 = d->prec == CBDFS_PREC_FP8;
         const int kblk = fp8 ? 128 : 64;
         N.k1pad = (d->dims[0] + kblk - 1) / kblk * kblk;
+        int w128_layers = 0;
         for (int l = 0; l < L - 1; ++l) {
             const int O = d->dims[l + 1], I = d->dims[l];
             const int Kp = l == 0 ? N.k1pad : I;
@@ -759,7 +760,9 @@ int cbdfs_net_load(cbdfs_ctx *ctx, const cbdfs_net_desc *d, int *heur_id) {
                                    fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                                    fp8 ? 1 : 2, (uint64_t)Kp, (uint64_t)O, kblk, kChainBN / 2)))
                 return rc;
+            w128_layers += O % kChainBN == 0;
         }
+        N.has_w128 = w128_layers == L - 1;
     }
     // the tensor-core head: a classifier of 17..128 outputs behind BF16 / E4M3 hidden layers
     // (the fused chain stores the last hidden layer in BF16 for it); W = W1 + W2 + W3 in BF16,
@@ -946,10 +949,13 @@ static int fuse_group(Ctx *c, const int *ids, int k, std::unique_ptr<NetGPU> *ou
         if ((rc = make_tmap_2d(&F.tm_w[l], F.w_lp[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (uint64_t)Kp, (uint64_t)E * O,
                                64, F.bn[l])) ||
             (rc = make_tmap_2d(&F.tm_w64[l], F.w_lp[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (uint64_t)Kp,
-                               (uint64_t)E * O, 64, kChainBNSmall)))
+                               (uint64_t)E * O, 64, kChainBNSmall)) ||
+            (rc = make_tmap_2d(&F.tm_w128[l], F.w_lp[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (uint64_t)Kp,
+                               (uint64_t)E * O, 64, kChainBN / 2)))
             return rc;
         maxw = std::max(maxw, (size_t)E * O);
     }
+    F.has_w128 = true;  // the grouped network runs on the chain only (every hidden width a multiple of 256)
     const int C = a.dims[L], KL = a.dims[L - 1], cpad = a.head_cpad;
     if ((rc = stack(&F.w_split, (size_t)3 * cpad * KL * 2, [&](const NetGPU &n) { return (const void *)n.w_split; })) ||
         (rc = stack((void **)&F.b32[L - 1], (size_t)C * 4, [&](const NetGPU &n) { return (const void *)n.b32[L - 1]; })))

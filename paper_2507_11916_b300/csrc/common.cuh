@@ -68,6 +68,7 @@ struct NetGPU {
     CUtensorMap tm_w[kMaxLayers];      // TMA maps of w_lp (k-block x bn rows)
     CUtensorMap tm_w64[kMaxLayers];    // the same with 64-row boxes (small-batch chain tiles)
     CUtensorMap tm_w128[kMaxLayers];   // the same with 128-row boxes (a CTA pair's half of a tile)
+    bool has_w128 = false;             // tm_w128 is built for every hidden layer (CTA pairs allowed)
     int bn[kMaxLayers] = {};           // N tile per layer
     // classifier heads of 17..128 outputs on a BF16/E4M3 network: the last layer split into three
     // BF16 parts [3][head_cpad][K] for the tensor-core head (head_cpad = 0: none)
