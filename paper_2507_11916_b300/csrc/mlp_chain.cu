@@ -2,7 +2,8 @@
 //
 // Every hidden layer is cut into 128-state x 256-output tiles; the tiles of all layers form
 // one sequence, layer by layer and, inside a layer, row block by row block.  Each CTA (one
-// per SM, a cooperative launch, so all are resident) takes tiles i, i+G, i+2G, ... .  A tile
+// per SM, all resident: a cooperative launch, or a cluster launch of CTA pairs that the
+// device holds at once) takes tiles i, i+G, i+2G, ... (CTA pairs: pair tiles, see k_chain).  A tile
 // of layer l+1 for row block m starts as soon as every tile of layer l for that row block is
 // stored: the epilogue counts finished tiles per (layer, row block) with a release atomic and
 // the producer waits for the count with a bounded acquire poll.  Dependencies only point to
@@ -714,25 +715,23 @@ static int launch_t(const ChainMaps &maps, const ChainParams &P, int grid, cudaS
     cfg.blockDim = dim3(kChainThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[2];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    attr[1].id = cudaLaunchAttributeClusterDimension;
-    attr[1].val.clusterDim.x = PAIR ? 2 : 1;
-    attr[1].val.clusterDim.y = 1;
-    attr[1].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = PAIR ? 2 : 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, P);
-    if (e != cudaSuccess && PAIR) {
-        // a driver that does not take the cooperative attribute with a cluster shape: the
-        // pairs are launched as a plain cluster launch (chain_pairs_fit has checked that the
-        // device holds all of them at once)
-        cudaGetLastError();
-        attr[0] = attr[1];
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, kern, maps, P);
+    // one CTA per SM, all resident at once: a cooperative launch for single CTAs; CTA pairs
+    // are a plain cluster launch, for which chain_pairs_fit has checked that the device holds
+    // every pair at once (a launch queued behind another starts its CTAs as the earlier
+    // launch's retire, and the earlier launch never waits on the later one)
+    cudaLaunchAttribute attr[1];
+    if (PAIR) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+    } else {
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
     }
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, P);
     if (e != cudaSuccess) return fail(CBDFS_EDEVICE, "chain launch: %s", cudaGetErrorString(e));
     return CBDFS_OK;
 }
