@@ -214,7 +214,7 @@ def run_reference(args):
     g = (W.splitmix64_array(4243, chunk) % np.uint64(60)).astype(np.uint8)
 
     def step():
-        y = oracle.mlp_forward(Wq, bs, oracle.one_hot(oracle.DOM_STP4, states))
+        y = oracle.mlp_forward(Wq, bs, oracle.one_hot(oracle.DOM_STP4, states), bf16_acts=True)
         h = oracle.h_regression(y[:, 0], oracle.md_states(oracle.DOM_STP4, states),
                                 oracle.is_goal_states(oracle.DOM_STP4, states))
         oracle.bound_test(g, h, BOUND)
