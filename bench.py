@@ -320,62 +320,74 @@ def search_rates(P, ctx, hids, seconds, work_num=256):
 
 
 def search_c1_leg(P, ctx, hids, args):
-    """IDA* nodes/s at the 15-puzzle regression configuration: 100 starts from seeded 200-move
-    walks (seed_for(0xC1, i)), one search thread per host core, batch capacities 512, 2048 and
-    8192, the network in BF16, E4M3 and FP32.  Fixed tree (section "Fixed-Tree Evaluation"):
-    Manhattan distance prunes and the network is evaluated on every generated node, so every
-    precision and batch size searches the same tree (checked: the completed iterations'
-    counts agree) and nodes/s compares the evaluation paths.  Starts 200 moves from the goal
-    take far longer than a bench run to solve, so each search is time-boxed and the rate is
-    the nodes expanded within the box over its wall time.  Each figure is run `repeats` times;
-    the line gives the median and the spread."""
+    """IDA* nodes/s at the 15-puzzle regression configuration: starts from seeded 200-move walks
+    (seed_for(0xC1, i)), one search thread per host core, batch capacities 512, 2048 and 8192,
+    the network in BF16, E4M3 and FP32.  Fixed tree (section "Fixed-Tree Evaluation"): Manhattan
+    distance prunes and the network is evaluated on every generated node, so every precision and
+    batch size searches the same tree (checked: the completed iterations' counts agree) and
+    nodes/s compares the evaluation paths.  Starts 200 moves from the goal take far longer than a
+    bench run to solve, so each search is time-boxed (`--search-box` seconds; shorter boxes are
+    dominated by the start-up and the first, tiny iterations) and the rate is the nodes expanded
+    within the box over its wall time.  All 100 starts run once per precision at capacity 8192;
+    the repeats (for the spread) and the other capacities run on the first 10 starts."""
     starts = [P.cbdfs_apply_moves(P.DOM_STP4, W.stp_goal(4), W.stp_walk(4, 200, W.seed_for(W.TAG_C1, i)))
               for i in range(100)]
     threads = os.cpu_count() or 4
-    box, reps = args.search_box, args.search_repeats
+    box, reps, sub = args.search_box, args.search_repeats, 10
     out = {"instances": "100 seeded 200-move 15-puzzle walks (seed_for(0xC1, i), i < 100)",
            "threads": threads, "host_cores": os.cpu_count(), "work_num": 256, "timeout_us": 500,
-           "time_box_s_per_instance": box, "repeats": reps, "mode": "fixed tree (MD prunes, network on every node)"}
+           "time_box_s_per_instance": box, "mode": "fixed tree (MD prunes, network on every node)",
+           "plan": f"100 starts once per precision at capacity 8192; {reps} passes over the first {sub} "
+                   "starts at each capacity for the spread"}
     done = {}
+
+    def run(hid, batch, idx, work_num=256):
+        exp = gen = nb = ev = 0
+        secs = busy = 0.0
+        hist = [0] * 16
+        for i in idx:
+            r = P.cbdfs_solve(ctx, P.DOM_STP4, starts[i], P.ALGO_IDA, hid, partial_ok=True, threads=threads,
+                              work_num=work_num, batch=batch, timeout_us=500, time_limit_s=box,
+                              fixed_tree_heur=P.HEUR_MD)
+            exp += r["expanded"]
+            gen += r["generated"]
+            secs += r["seconds"]
+            nb += r["batches"]
+            ev += r["evaluated"]
+            busy += r["gpu_busy_s"]
+            hist = [x + y for x, y in zip(hist, r["batch_hist"])]
+            its = r["iters"] if r["status"] == 0 else r["iters"][:-1]
+            done.setdefault(i, []).append([tuple(t) for t in its])
+        return {"expanded_per_s": exp / secs, "generated_per_s": gen / secs, "seconds": secs,
+                "expanded": exp, "avg_batch": ev / max(nb, 1), "gpu_busy_frac": busy / secs,
+                "batch_hist": {f"{1 << k}-{(1 << (k + 1)) - 1}": c for k, c in enumerate(hist) if c}}
+
     for prec, hid in hids.items():
+        res = {"all_100_b8192": run(hid, 8192, range(100))}
         for batch in (512, 2048, 8192):
-            runs = []
-            for rep in range(reps):
-                exp = gen = nb = ev = 0
-                secs = busy = 0.0
-                hist = [0] * 16
-                for i, s in enumerate(starts):
-                    r = P.cbdfs_solve(ctx, P.DOM_STP4, s, P.ALGO_IDA, hid, partial_ok=True, threads=threads,
-                                      work_num=256, batch=batch, timeout_us=500, time_limit_s=box,
-                                      fixed_tree_heur=P.HEUR_MD)
-                    exp += r["expanded"]
-                    gen += r["generated"]
-                    secs += r["seconds"]
-                    nb += r["batches"]
-                    ev += r["evaluated"]
-                    busy += r["gpu_busy_s"]
-                    hist = [x + y for x, y in zip(hist, r["batch_hist"])]
-                    its = r["iters"] if r["status"] == 0 else r["iters"][:-1]
-                    done.setdefault(i, []).append([tuple(t) for t in its])
-                runs.append({"expanded_per_s": exp / secs, "generated_per_s": gen / secs, "seconds": secs,
-                             "expanded": exp, "avg_batch": ev / max(nb, 1), "gpu_busy_frac": busy / secs,
-                             "hist": hist})
-            med = sorted(runs, key=lambda x: x["expanded_per_s"])[len(runs) // 2]
-            rates = [x["expanded_per_s"] for x in runs]
-            out.setdefault(prec, {})[batch] = {
-                "expanded_per_s": med["expanded_per_s"], "generated_per_s": med["generated_per_s"],
-                "expanded_per_s_runs": rates, "spread": (max(rates) - min(rates)) / med["expanded_per_s"],
-                "avg_batch": med["avg_batch"], "gpu_busy_frac": med["gpu_busy_frac"],
-                "batch_hist": {f"{1 << k}-{(1 << (k + 1)) - 1}": c for k, c in enumerate(med["hist"]) if c}}
-    # the same tree in every precision, batch size and repeat: completed iterations agree
+            runs = [run(hid, batch, range(sub)) for _ in range(reps)]
+            rates = sorted(x["expanded_per_s"] for x in runs)
+            med = rates[len(rates) // 2]
+            res[f"first{sub}_b{batch}"] = {"expanded_per_s": med, "expanded_per_s_runs": rates,
+                                           "spread": (rates[-1] - rates[0]) / med,
+                                           "avg_batch": runs[0]["avg_batch"],
+                                           "gpu_busy_frac": runs[0]["gpu_busy_frac"]}
+        if prec == "bf16":
+            # more work items per thread fill larger batches once the tree is wide
+            r = run(hid, 8192, range(sub), work_num=1024)
+            res[f"first{sub}_b8192_work_num1024"] = {k: r[k] for k in ("expanded_per_s", "avg_batch",
+                                                                        "gpu_busy_frac")}
+        out[prec] = res
+    # the same tree in every precision, batch size and pass: completed iterations agree
     out["equal_counts"] = all(
         its[:m] == runs_i[0][:m] for runs_i in done.values() for its in runs_i
         for m in [min(len(its), len(runs_i[0]))])
     out["completed_iterations_per_instance"] = statistics.median(len(r[0]) for r in done.values())
-    for batch in (512, 2048, 8192):
+    if "fp32" in out:
         for prec in ("bf16", "fp8"):
-            if prec in out and "fp32" in out:
-                out[f"{prec}_over_fp32_nodes_b{batch}"] = out[prec][batch]["expanded_per_s"] / out["fp32"][batch]["expanded_per_s"]
+            if prec in out:
+                out[f"{prec}_over_fp32_nodes"] = (out[prec]["all_100_b8192"]["expanded_per_s"] /
+                                                  out["fp32"]["all_100_b8192"]["expanded_per_s"])
     return out
 
 
@@ -1256,7 +1268,7 @@ def main():
     ap.add_argument("--pdb-states", type=int, default=1 << 22)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--search-seconds", type=float, default=3.0)
-    ap.add_argument("--search-box", type=float, default=0.05,
+    ap.add_argument("--search-box", type=float, default=0.3,
                     help="time box per instance of the 100-start search leg (s)")
     ap.add_argument("--search-repeats", type=int, default=3)
     ap.add_argument("--ida-cmp-starts", type=int, default=3,
