@@ -416,11 +416,12 @@ typedef struct {
 } cbdfs_request;
 
 /* Measurement of the running server with native clients (no counterpart in the paper; the
- * paper's clients are its search threads): `threads` client threads submit reqs[t],
- * reqs[t + threads], ... and each keeps at most `depth` of its own requests outstanding (depth
- * 1: a client blocks on every request, as a search thread blocks on its batch).  Returns when
- * every request is done; *seconds is the wall time from the first submission to the last
- * completion.  Errors: EINVAL, or the first failed request's status. */
+ * paper's clients are its search threads): `threads` client threads take the requests in
+ * order, each the next one not yet taken, and each keeps at most `depth` of its own requests
+ * outstanding (depth 1: a client blocks on every request, as a search thread blocks on its
+ * batch).  Returns when every request is done; *seconds is the wall time from the moment every
+ * client thread is running to the last completion.  Errors: EINVAL, or the first failed
+ * request's status. */
 int cbdfs_server_drive(cbdfs_ctx *ctx, const cbdfs_request *reqs, uint32_t n_reqs, int threads, int depth,
                        double *seconds);
 

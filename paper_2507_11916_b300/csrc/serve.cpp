@@ -553,8 +553,14 @@ int cbdfs_server_drive(cbdfs_ctx *ctx, const cbdfs_request *reqs, uint32_t n_req
                        double *seconds) {
     if (!ctx || (!reqs && n_reqs) || threads < 1 || depth < 1 || !seconds) return fail(CBDFS_EINVAL, "arguments");
     std::atomic<int> first_error{0};
-    const auto t0 = std::chrono::steady_clock::now();
-    auto client = [&](int t) {
+    // clients take the next request as they free up (an open stream of requests, no tail of
+    // idle clients), and the clock starts once every client thread is running
+    std::atomic<uint32_t> next{0};
+    std::atomic<int> ready{0};
+    std::atomic<bool> go{false};
+    auto client = [&](int) {
+        ready.fetch_add(1);
+        while (!go.load(std::memory_order_acquire)) std::this_thread::yield();
         std::deque<cbdfs_ticket> pending;
         auto wait_one = [&]() {
             const int rc = heur_request_wait(ctx, pending.front(), 60000000ull);
@@ -562,7 +568,7 @@ int cbdfs_server_drive(cbdfs_ctx *ctx, const cbdfs_request *reqs, uint32_t n_req
             int zero = 0;
             if (rc) first_error.compare_exchange_strong(zero, rc);
         };
-        for (uint32_t j = (uint32_t)t; j < n_reqs && !first_error.load(); j += (uint32_t)threads) {
+        for (uint32_t j = next.fetch_add(1); j < n_reqs && !first_error.load(); j = next.fetch_add(1)) {
             const cbdfs_request &q = reqs[j];
             cbdfs_ticket tk;
             const int rc = heur_request_submit(ctx, q.heur_id, q.domain, q.states, q.g, q.bound, q.n, q.h_out,
@@ -579,6 +585,9 @@ int cbdfs_server_drive(cbdfs_ctx *ctx, const cbdfs_request *reqs, uint32_t n_req
     };
     std::vector<std::thread> ts;
     for (int t = 0; t < threads; ++t) ts.emplace_back(client, t);
+    while (ready.load() < threads) std::this_thread::yield();
+    const auto t0 = std::chrono::steady_clock::now();
+    go.store(true, std::memory_order_release);
     for (auto &t : ts) t.join();
     *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     const int rc = first_error.load();
