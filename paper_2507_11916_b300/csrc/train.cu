@@ -478,7 +478,17 @@ struct AdamParams {
     int nseg;
     int copies_only;  // no update: only the copies of the masters as they are (a loaded checkpoint)
     float lr, b1, b2, eps, c1, c2;
+    // optional: c1, c2 of step ctr[0] of a run from a table [2 x steps] (one captured step
+    // serves every step of the run)
+    const float *c12;
+    const int *ctr;
 };
+
+// the run's step and batch counters, after a step
+__global__ void k_step_advance(int *ctr) {
+    ctr[0]++;
+    ctr[1]++;
+}
 
 __global__ void __launch_bounds__(256) k_adam_all(const __grid_constant__ AdamParams P) {
     int s = 0;
@@ -488,13 +498,18 @@ __global__ void __launch_bounds__(256) k_adam_all(const __grid_constant__ AdamPa
     if (idx >= S.O * S.I) return;
     float nw = S.w[idx];
     if (!P.copies_only) {
+        float c1 = P.c1, c2 = P.c2;
+        if (P.c12) {
+            c1 = P.c12[2 * P.ctr[0]];
+            c2 = P.c12[2 * P.ctr[0] + 1];
+        }
         float gg = 0.f;
         for (int z = 0; z < S.parts; ++z) gg += S.g[z * S.pstride + idx];
         const float m = P.b1 * S.m[idx] + (1.f - P.b1) * gg;
         const float v = P.b2 * S.v[idx] + (1.f - P.b2) * gg * gg;
         S.m[idx] = m;
         S.v[idx] = v;
-        const float mh = m / P.c1, vh = v / P.c2;
+        const float mh = m / c1, vh = v / c2;
         nw = S.w[idx] - P.lr * mh / (sqrtf(vh) + P.eps);
         S.w[idx] = nw;
     }
@@ -513,11 +528,15 @@ __global__ void k_write_t(const float *__restrict__ w, int O, int I, __nv_bfloat
     wt[(size_t)(idx % I) * O + idx / I] = __float2bfloat16(w[idx]);
 }
 
+// batch rows i < n from the epoch's permutation, starting at row ctr[1] * batch of it (the
+// counter is the batch's index in the epoch, advanced on the device after each step, so that
+// one captured step serves every full batch)
 __global__ void k_gather(const uint64_t *__restrict__ src, const uint8_t *__restrict__ lab, const uint32_t *__restrict__ idx,
-                         int words, uint32_t n, uint64_t *__restrict__ dst, uint8_t *__restrict__ dlab) {
+                         const int *__restrict__ ctr, uint32_t batch, int words, uint32_t n,
+                         uint64_t *__restrict__ dst, uint8_t *__restrict__ dlab) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint32_t j = idx[i];
+    const uint32_t j = idx[(size_t)ctr[1] * batch + i];
     for (int w = 0; w < words; ++w) dst[(size_t)i * words + w] = src[(size_t)j * words + w];
     dlab[i] = lab[j];
 }
@@ -888,10 +907,14 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
 }
 
 // one Adam launch over every tensor (copies_only: no update, the copies of the masters)
-static int launch_adam(NetGPU &net, const cbdfs_train_cfg *tc, bool copies_only, cudaStream_t st) {
+// c12/ctr: the bias corrections from a table at the device step counter (see AdamParams)
+static int launch_adam(NetGPU &net, const cbdfs_train_cfg *tc, bool copies_only, cudaStream_t st,
+                       const float *c12 = nullptr, const int *ctr = nullptr) {
     TrainState &T = *net.train;
     AdamParams A{};
     A.copies_only = copies_only ? 1 : 0;
+    A.c12 = c12;
+    A.ctr = ctr;
     if (tc) {
         A.lr = tc->lr;
         A.b1 = tc->beta1;
@@ -945,10 +968,6 @@ static int launch_adam(NetGPU &net, const cbdfs_train_cfg *tc, bool copies_only,
     return CBDFS_OK;
 }
 
-static int train_update(Ctx *, NetGPU &net, const cbdfs_train_cfg &tc, cudaStream_t st) {
-    net.train->step++;
-    return launch_adam(net, &tc, false, st);
-}
 
 
 // ---- training checkpoints ---------------------------------------------------------------
@@ -1097,17 +1116,53 @@ int net_train(cbdfs_ctx *ctx, int net_id, const uint64_t *states, const uint8_t 
     uint64_t *d_states = nullptr;
     uint8_t *d_labels = nullptr;
     uint32_t *d_idx = nullptr;
-    if ((rc = dev_alloc(c, (void **)&d_states, n * 8 * w))) return rc;
-    if ((rc = dev_alloc(c, (void **)&d_labels, n))) { dev_free(c, d_states, n * 8 * w); return rc; }
-    if ((rc = dev_alloc(c, (void **)&d_idx, n * 4))) {
-        dev_free(c, d_states, n * 8 * w);
-        dev_free(c, d_labels, n);
-        return rc;
-    }
+    const uint64_t per_epoch = (n + tc.batch - 1) / tc.batch;
+    int64_t total = (int64_t)tc.epochs * (int64_t)per_epoch;
+    if (tc.max_steps > 0) total = std::min<int64_t>(total, tc.max_steps);
+    // the run's device counters (step in the run, batch in the epoch) and every step's Adam bias
+    // corrections, computed here as a single step computes them, so that one captured step
+    // (a CUDA graph: gather, forward, backward, update) replays for every full batch
+    int *d_ctr = nullptr;
+    float *d_c12 = nullptr;
+    cudaGraphExec_t step_graph = nullptr;
     auto cleanup = [&]() {
+        if (step_graph) cudaGraphExecDestroy(step_graph);
         dev_free(c, d_states, n * 8 * w);
         dev_free(c, d_labels, n);
         dev_free(c, d_idx, n * 4);
+        dev_free(c, d_ctr, 2 * sizeof(int));
+        dev_free(c, d_c12, 2 * sizeof(float) * (size_t)total);
+    };
+    if ((rc = dev_alloc(c, (void **)&d_states, n * 8 * w)) || (rc = dev_alloc(c, (void **)&d_labels, n)) ||
+        (rc = dev_alloc(c, (void **)&d_idx, n * 4)) || (rc = dev_alloc(c, (void **)&d_ctr, 2 * sizeof(int))) ||
+        (rc = dev_alloc(c, (void **)&d_c12, 2 * sizeof(float) * (size_t)total))) {
+        cleanup();
+        return rc;
+    }
+    {
+        std::vector<float> c12(2 * (size_t)total);
+        for (int64_t j = 0; j < total; ++j) {
+            const float t = (float)(T.step + 1 + j);
+            c12[2 * j] = 1.f - powf(tc.beta1, t);
+            c12[2 * j + 1] = 1.f - powf(tc.beta2, t);
+        }
+        if (cudaMemcpy(d_c12, c12.data(), c12.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemset(d_ctr, 0, 2 * sizeof(int)) != cudaSuccess) {
+            cleanup();
+            return fail(CBDFS_EDEVICE, "training counters");
+        }
+    }
+    // one step on the stream: rows from the permutation at the batch counter, forward,
+    // backward, Adam at the step counter, then both counters advance
+    auto enqueue_step = [&](uint32_t bn) -> int {
+        k_gather<<<(bn + 255) / 256, 256, 0, st>>>(d_states, d_labels, d_idx, d_ctr, tc.batch, w, bn, T.states, T.labels);
+        int r = train_fwd_bwd(c, *net, (int)bn, tc.loss, st, false);
+        if (!r) r = launch_adam(*net, &tc, false, st, d_c12, d_ctr);
+        if (!r) {
+            k_step_advance<<<1, 1, 0, st>>>(d_ctr);
+            if (cudaGetLastError() != cudaSuccess) r = fail(CBDFS_EDEVICE, "training step launch");
+        }
+        return r;
     };
     if (cudaMemcpy(d_states, states, n * 8 * w, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d_labels, labels, n, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -1116,7 +1171,6 @@ int net_train(cbdfs_ctx *ctx, int net_id, const uint64_t *states, const uint8_t 
     }
     std::vector<uint32_t> perm(n);
     const auto t0 = std::chrono::steady_clock::now();
-    const uint64_t per_epoch = (n + tc.batch - 1) / tc.batch;
     float loss = 0.f;
     int64_t steps = 0;
     for (int ep = 0; ep < tc.epochs && !rc; ++ep) {
@@ -1131,7 +1185,8 @@ int net_train(cbdfs_ctx *ctx, int net_id, const uint64_t *states, const uint8_t 
             z ^= z >> 31;
             std::swap(perm[i], perm[z % (i + 1)]);
         }
-        if (cudaMemcpyAsync(d_idx, perm.data(), n * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        if (cudaMemcpyAsync(d_idx, perm.data(), n * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemsetAsync(d_ctr + 1, 0, sizeof(int), st) != cudaSuccess) {
             rc = fail(CBDFS_EDEVICE, "permutation upload");
             break;
         }
@@ -1139,9 +1194,28 @@ int net_train(cbdfs_ctx *ctx, int net_id, const uint64_t *states, const uint8_t 
             if (tc.max_steps > 0 && steps >= tc.max_steps) break;
             const uint32_t off = (uint32_t)(k * tc.batch);
             const uint32_t bn = (uint32_t)std::min<uint64_t>(tc.batch, n - off);
-            k_gather<<<(bn + 255) / 256, 256, 0, st>>>(d_states, d_labels, d_idx + off, w, bn, T.states, T.labels);
-            rc = train_fwd_bwd(c, *net, (int)bn, tc.loss, st, false);
-            if (!rc) rc = train_update(c, *net, tc, st);
+            if (bn == tc.batch) {
+                if (!step_graph) {
+                    cudaGraph_t g = nullptr;
+                    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                        rc = fail(CBDFS_EDEVICE, "step capture");
+                        break;
+                    }
+                    rc = enqueue_step(bn);
+                    const cudaError_t e = cudaStreamEndCapture(st, &g);
+                    if (!rc && e != cudaSuccess) rc = fail(CBDFS_EDEVICE, "step capture: %s", cudaGetErrorString(e));
+                    if (!rc && cudaGraphInstantiate(&step_graph, g, 0) != cudaSuccess) {
+                        step_graph = nullptr;
+                        rc = fail(CBDFS_EDEVICE, "step graph instantiate");
+                    }
+                    if (g) cudaGraphDestroy(g);
+                    if (rc) break;
+                }
+                if (cudaGraphLaunch(step_graph, st) != cudaSuccess) rc = fail(CBDFS_EDEVICE, "step graph launch");
+            } else {
+                rc = enqueue_step(bn);  // the epoch's last, partial batch
+            }
+            T.step++;
             if (!rc && (steps == 0 || (steps & 255) == 255)) {
                 if (cudaMemcpyAsync(&loss, T.loss, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                     cudaStreamSynchronize(st) != cudaSuccess) {
