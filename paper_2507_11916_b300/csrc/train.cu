@@ -11,8 +11,8 @@
 //             W_L as three, every product exact and accumulated in FP32:
 //             dW_L = dZ_L^T A_{L-2} (split-K over the batch), db_L = colsum(dZ_L),
 //             dZ_{L-2} = (dZ_L W_L) * [A_{L-2} > 0] (BF16)
-//             hidden l: dW_l = dZ_l^T A_{l-1} as a tcgen05 GEMM over the batch (both operands
-//             transposed to K-major by a tiled transpose; A_{-1} is the transposed one-hot),
+//             hidden l: dW_l = dZ_l^T A_{l-1} as a tcgen05 GEMM over the batch with both
+//             operands MN-major as stored (A_{-1} is the one-hot, written transposed),
 //             db_l = colsum(dZ_l), dZ_{l-1} = (dZ_l W_l) * [A_{l-1} > 0] as a tcgen05 GEMM
 //             with the mask fused in the epilogue (W_l^T kept in BF16 beside W_l)
 //   update    Adam (bias-corrected) on the FP32 masters of every tensor in one launch, adding
@@ -47,13 +47,30 @@ constexpr int kThreads = 192;
 constexpr int kSumRows = 64;   // rows of one chunk of a column sum
 constexpr int kStageA = kBM * 128;
 
+// Shared-memory descriptor of an MN-major operand with 128-byte swizzle: 64-element (128-byte)
+// rows along M (or N), one per k, eight k rows to a 1024-byte swizzle atom; `lbo` is the byte
+// distance between 64-element blocks along M (N), the k atoms follow each other (1024 bytes).
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t saddr, uint32_t lbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);   // start address
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;  // leading byte offset: the next 64 along M (N)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: the next 8 k rows
+    d |= (uint64_t)1 << 46;                     // descriptor version for sm_100 family
+    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+    return d;
+}
+constexpr int kMnBox = 64 * 128;  // one 64-element x 64-row TMA box of an MN-major operand
+
 // ---------------------------------------------------------------------------------------
-// TN GEMM on tcgen05: C[M][N] = A[M][K] B[N][K]^T, both BF16 K-major, FP32 accumulate.
+// TN GEMM on tcgen05: C[M][N] = A[M][K] B[N][K]^T, BF16, FP32 accumulate.
+// Operands K-major ([M][K], [N][K]), or MN-major (MNA / MNB: stored [K][M], [K][N], as the
+// backward has dZ and the activations, so dW = dZ^T A needs no transposes): an MN-major stage
+// is loaded as 64 x 64 boxes, 8 KB apart along M (N).
 // EPI 1: C FP32.  EPI 2: C BF16 = acc * (mask[m][n] > 0) (mask BF16 [M][N]).
 // Split K (gridDim.z > 1, EPI 1): CTA z contracts k-blocks [z KB/S, (z+1) KB/S) into its own
 // partial out + z M N; k_sum_splits then adds the partials in split order.
 // ---------------------------------------------------------------------------------------
-template <int BN, int EPI>
+template <int BN, int EPI, bool MNA = false, bool MNB = false>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gemm_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int K, int N,
           void *__restrict__ out, const __nv_bfloat16 *__restrict__ mask, int stages, int *err) {
@@ -93,8 +110,21 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 const int s = kb % stages, u = kb / stages;
                 if (kb >= stages && !mbar_wait(smem_u32(&empty[s]), (u - 1) & 1, err, DEVERR_STAGE_EMPTY)) break;
                 mbar_arrive_expect_tx(smem_u32(&full[s]), kStageA + kStageB);
-                tma_load_2d(smem_u32(A + s * kStageA), &tmA, smem_u32(&full[s]), (kb0 + kb) * 64, m0);
-                tma_load_2d(smem_u32(B + s * kStageB), &tmB, smem_u32(&full[s]), (kb0 + kb) * 64, n0);
+                const int k0 = (kb0 + kb) * 64;
+                if (MNA) {
+#pragma unroll
+                    for (int h = 0; h < kBM / 64; ++h)
+                        tma_load_2d(smem_u32(A + s * kStageA + h * kMnBox), &tmA, smem_u32(&full[s]), m0 + 64 * h, k0);
+                } else {
+                    tma_load_2d(smem_u32(A + s * kStageA), &tmA, smem_u32(&full[s]), k0, m0);
+                }
+                if (MNB) {
+#pragma unroll
+                    for (int h = 0; h < BN / 64; ++h)
+                        tma_load_2d(smem_u32(B + s * kStageB + h * kMnBox), &tmB, smem_u32(&full[s]), n0 + 64 * h, k0);
+                } else {
+                    tma_load_2d(smem_u32(B + s * kStageB), &tmB, smem_u32(&full[s]), k0, n0);
+                }
                 ++issued;
             }
             // bounded drain of this thread's loads before the CTA can exit
@@ -103,15 +133,20 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = make_idesc(kBM, BN, 1, 1);
+            // bits 15 / 16 of the instruction descriptor: A / B MN-major
+            constexpr uint32_t idesc = make_idesc(kBM, BN, 1, 1) | (MNA ? 1u << 15 : 0u) | (MNB ? 1u << 16 : 0u);
             bool ok = true;
             for (int kb = 0; kb < KB; ++kb) {
                 const int s = kb % stages, u = kb / stages;
                 if (!mbar_wait(smem_u32(&full[s]), u & 1, err, DEVERR_TMA_FULL)) { ok = false; break; }
                 tc_fence_after();
-                const uint64_t ad = sw128_desc(smem_u32(A + s * kStageA)), bd = sw128_desc(smem_u32(B + s * kStageB));
+                // a 16-deep MMA step advances 32 bytes along a K-major row, or two 8-row k atoms
+                // (2048 bytes) of an MN-major stage
+                const uint64_t ad = MNA ? sw128_mn_desc(smem_u32(A + s * kStageA), kMnBox) : sw128_desc(smem_u32(A + s * kStageA));
+                const uint64_t bd = MNB ? sw128_mn_desc(smem_u32(B + s * kStageB), kMnBox) : sw128_desc(smem_u32(B + s * kStageB));
+                constexpr uint64_t da = MNA ? 2048 >> 4 : 2, db = MNB ? 2048 >> 4 : 2;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) umma_bf16(tmem_d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                for (int k = 0; k < 4; ++k) umma_bf16(tmem_d, ad + da * k, bd + db * k, idesc, (kb | k) != 0);
                 umma_commit(smem_u32(&empty[s]));
             }
             umma_commit(smem_u32(accum));
@@ -169,14 +204,14 @@ __global__ void k_sum_splits(const float *__restrict__ part, int S, int len, flo
 
 // splits > 1 (EPI 1 only): the partials go to `part` (splits x M x N floats), then (sum) their
 // sum in split order to `out`
-template <int BN, int EPI>
+template <int BN, int EPI, bool MNA = false, bool MNB = false>
 int gemm_tn(const CUtensorMap &tmA, const CUtensorMap &tmB, int M, int N, int K, void *out,
             const __nv_bfloat16 *mask, int *err, cudaStream_t st, int splits = 1, float *part = nullptr,
             bool sum = true) {
     constexpr int kStageB = BN * 128;
     const int stages = 4;
     const size_t smem = 1024 + 256 + (size_t)stages * (kStageA + kStageB);
-    auto kern = k_gemm_tn<BN, EPI>;
+    auto kern = k_gemm_tn<BN, EPI, MNA, MNB>;
     CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const bool split = EPI == 1 && splits > 1 && part;
     kern<<<dim3(N / BN, M / kBM, split ? splits : 1), kThreads, smem, st>>>(tmA, tmB, K, N, split ? part : out,
@@ -598,7 +633,7 @@ struct TrainState {
     __nv_bfloat16 *wt[kMaxLayers] = {};                    // W_l^T BF16 (hidden layers >= 1)
     __nv_bfloat16 *act[kMaxLayers] = {};                   // A_l, l = 0..L-2, [Bp][dims[l+1]]
     __nv_bfloat16 *dz[kMaxLayers] = {};                    // dZ_l BF16 [Bp][dims[l+1]]
-    __nv_bfloat16 *t_dz = nullptr, *t_a = nullptr;         // transposes (largest)
+    __nv_bfloat16 *t_a = nullptr;                          // the transposed one-hot of the batch
     float *logits = nullptr, *dzl = nullptr, *row_loss = nullptr, *loss = nullptr;
     // partial sums of every gradient tensor: the weights' row (split-K) partials and the
     // biases' row-chunk partials, [parts][len] each; the gradient is their sum in part order
@@ -673,8 +708,6 @@ static int train_setup(Ctx *c, NetGPU &net, int B, const float *const *host_w, c
         T->Bp = (B + kBM - 1) / kBM * kBM;
         const int L = net.L, Bp = T->Bp;
         int rc = CBDFS_OK;
-        size_t maxw = 0;
-        for (int l = 1; l < L; ++l) maxw = std::max(maxw, (size_t)net.dims[l]);
         const size_t k1 = (size_t)net.k1pad;
         for (int l = 0; l < L && !rc; ++l) {
             const size_t O = net.dims[l + 1], I = l == 0 ? k1 : (size_t)net.dims[l];
@@ -691,8 +724,7 @@ static int train_setup(Ctx *c, NetGPU &net, int B, const float *const *host_w, c
             if (!rc && l < L - 1) rc = talloc(c, *T, (void **)&T->act[l], (size_t)Bp * O * 2);
             if (!rc && l < L - 1) rc = talloc(c, *T, (void **)&T->dz[l], (size_t)Bp * O * 2);
         }
-        if (!rc) rc = talloc(c, *T, (void **)&T->t_dz, (size_t)Bp * maxw * 2);
-        if (!rc) rc = talloc(c, *T, (void **)&T->t_a, (size_t)Bp * std::max(maxw, k1) * 2);
+        if (!rc) rc = talloc(c, *T, (void **)&T->t_a, (size_t)Bp * k1 * 2);
         const int C = net.dims[L];
         if (!rc) rc = talloc(c, *T, (void **)&T->logits, (size_t)Bp * C * 4);
         if (!rc) rc = talloc(c, *T, (void **)&T->dzl, (size_t)Bp * C * 4);
@@ -861,36 +893,37 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
     // hidden layers, last to first
     for (int l = L - 2; l >= 0; --l) {
         const int O = net.dims[l + 1], I = l == 0 ? net.k1pad : net.dims[l];
-        // dW_l = dZ_l^T A_{l-1}: transpose both to K-major over the batch
-        // (and db_l's row-chunk partials: the column sums of each 64-row tile)
-        k_transpose<<<dim3(O / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.dz[l], T.t_dz, Bp, O, O, Bp, nullptr, T.gb_buf[l]);
+        // dW_l = dZ_l^T A_{l-1}, both operands MN-major as the backward stores them ([batch][O],
+        // [batch][I]); layer 0's A is the one-hot, written transposed (K-major over the batch)
         if (l == 0) {
             CUDA_TRY(cudaMemsetAsync(T.t_a, 0, (size_t)I * Bp * 2, st));
             if (net.domain == CBDFS_DOM_STP3) k_onehot_t<CBDFS_DOM_STP3><<<(Bp + 255) / 256, 256, 0, st>>>(T.states, n, Bp, T.t_a);
             else if (net.domain == CBDFS_DOM_STP4) k_onehot_t<CBDFS_DOM_STP4><<<(Bp + 255) / 256, 256, 0, st>>>(T.states, n, Bp, T.t_a);
             else k_onehot_t<CBDFS_DOM_RC3><<<(Bp + 255) / 256, 256, 0, st>>>(T.states, n, Bp, T.t_a);
-        } else {
-            k_transpose<<<dim3(I / 64, Bp / 64), dim3(32, 8), 0, st>>>(T.act[l - 1], T.t_a, Bp, I, I, Bp, nullptr, nullptr);
         }
         // the output width is the (padded) input width; padding columns of the one-hot are
         // zero, so their gradient is exactly zero
-        const CUtensorMap *ma = bmap(T, T.t_dz, Bp, O, kBM);
-        const CUtensorMap *mb = bmap(T, T.t_a, Bp, I, I % 256 == 0 ? 256 : 128);
+        const CUtensorMap *ma = bmap(T, T.dz[l], O, T.Bp, 64);
+        const CUtensorMap *mb = l == 0 ? bmap(T, T.t_a, Bp, I, I % 256 == 0 ? 256 : 128) : bmap(T, T.act[l - 1], I, T.Bp, 64);
         if (!ma || !mb) return CBDFS_EDEVICE;
         const int S = dw_splits(c, O, I, Bp);
         if ((size_t)S * O * I > T.gw_buf_floats[l]) return fail(CBDFS_EINVAL, "dW scratch");
-        rc = (I % 256 == 0) ? gemm_tn<256, 1>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st, S, T.gw_buf[l], sum)
-                            : gemm_tn<128, 1>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st, S, T.gw_buf[l], sum);
+        if (l == 0)
+            rc = (I % 256 == 0) ? gemm_tn<256, 1, true, false>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st, S, T.gw_buf[l], sum)
+                                : gemm_tn<128, 1, true, false>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st, S, T.gw_buf[l], sum);
+        else
+            rc = (I % 256 == 0) ? gemm_tn<256, 1, true, true>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st, S, T.gw_buf[l], sum)
+                                : gemm_tn<128, 1, true, true>(*ma, *mb, O, I, Bp, T.gw[l], nullptr, c->d_err, st, S, T.gw_buf[l], sum);
         if (rc) return rc;
         T.gw_src[l] = S > 1 && !sum ? T.gw_buf[l] : T.gw[l];
         T.gw_parts[l] = S > 1 && !sum ? S : 1;
         T.gw_pstride[l] = (size_t)O * I;
         {
-            // db_l: the transpose's row-chunk partials (rows n..Bp-1 of dZ_l are zero)
-            const int R = Bp / kSumRows;
-            if (sum) k_sum_splits<<<(O + 255) / 256, 256, 0, st>>>(T.gb_buf[l], R, O, T.gb[l]);
+            // db_l: the column sums of dZ_l per 64-row chunk, rows in order (rows n..Bp-1 are zero)
+            int parts = 0;
+            if (int r = colsum(T.dz[l], n, O, T.gb_buf[l], T.gb_buf_floats[l], T.gb[l], sum, &parts, st)) return r;
             T.gb_src[l] = sum ? T.gb[l] : T.gb_buf[l];
-            T.gb_parts[l] = sum ? 1 : R;
+            T.gb_parts[l] = sum ? 1 : parts;
         }
         if (l > 0) {
             // dZ_{l-1} = (dZ_l W_l) * [A_{l-1} > 0]
