@@ -14,10 +14,10 @@
 //             hidden l: dW_l = dZ_l^T A_{l-1} as a tcgen05 GEMM over the batch with both
 //             operands MN-major as stored (A_{-1} is the one-hot, written transposed),
 //             db_l = colsum(dZ_l), dZ_{l-1} = (dZ_l W_l) * [A_{l-1} > 0] as a tcgen05 GEMM
-//             with the mask fused in the epilogue (W_l read MN-major: the BF16 weights)
+//             with the mask fused in the epilogue (W_l^T kept in BF16 beside W_l)
 //   update    Adam (bias-corrected) on the FP32 masters of every tensor in one launch, adding
 //             the gradient's split partials in order; BF16 copies W_l (K-padded, the
-//             inference layout) and the last layer's parts rewritten by the same kernel
+//             inference layout), W_l^T and the last layer's parts rewritten by the same kernel
 // Every reduction has a fixed order, so a step is deterministic.
 #include <algorithm>
 #include <cerrno>
@@ -496,8 +496,8 @@ __global__ void k_mean(const float *__restrict__ v, int n, float *__restrict__ o
 
 // Adam on the FP32 masters of every tensor in one launch: segment s (a layer's weights [O][I]
 // or biases [O]) owns blocks [block0, next block0).  Besides the master it writes the copies
-// the other kernels read: the BF16 weights w_lp[o][Kp] (inference, and the backward's dZ W as an
-// MN-major operand), an FP32 inference copy (the last layer, the biases) and the last layer's
+// the other kernels read: the BF16 inference weights w_lp[o][Kp], their transpose wt[i][O] for
+// the backward GEMM, an FP32 inference copy (the last layer, the biases) and the last layer's
 // three BF16 parts for the tensor-core head.
 struct AdamSeg {
     float *w;
@@ -505,7 +505,7 @@ struct AdamSeg {
     float *m, *v;
     int O, I, block0, Kp, cpad, parts, cs;
     size_t pstride;  // floats from one gradient part to the next
-    __nv_bfloat16 *w_lp, *split, *w_ext;
+    __nv_bfloat16 *w_lp, *wt, *split, *w_ext;
     float *w_out;
 };
 struct AdamParams {
@@ -550,9 +550,17 @@ __global__ void __launch_bounds__(256) k_adam_all(const __grid_constant__ AdamPa
     }
     const int o = idx / S.I, i = idx % S.I;
     if (S.w_lp) S.w_lp[(size_t)o * S.Kp + i] = __float2bfloat16(nw);
+    if (S.wt) S.wt[(size_t)i * S.O + o] = __float2bfloat16(nw);
     if (S.w_out) S.w_out[idx] = nw;
     if (S.split) split3_store(nw, o, i, S.I, S.cpad, S.split);
     if (S.w_ext) ext_store_w(nw, o, i, S.cs, S.w_ext);
+}
+
+// wt[i][O] = BF16(w[o][i])
+__global__ void k_write_t(const float *__restrict__ w, int O, int I, __nv_bfloat16 *__restrict__ wt) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= O * I) return;
+    wt[(size_t)(idx % I) * O + idx / I] = __float2bfloat16(w[idx]);
 }
 
 // batch rows i < n from the epoch's permutation, starting at row ctr[1] * batch of it (the
@@ -622,6 +630,7 @@ struct TrainState {
     float *w[kMaxLayers] = {}, *b[kMaxLayers] = {};        // FP32 masters
     float *mw[kMaxLayers] = {}, *vw[kMaxLayers] = {}, *mb[kMaxLayers] = {}, *vb[kMaxLayers] = {};
     float *gw[kMaxLayers] = {}, *gb[kMaxLayers] = {};      // gradients
+    __nv_bfloat16 *wt[kMaxLayers] = {};                    // W_l^T BF16 (hidden layers >= 1)
     __nv_bfloat16 *act[kMaxLayers] = {};                   // A_l, l = 0..L-2, [Bp][dims[l+1]]
     __nv_bfloat16 *dz[kMaxLayers] = {};                    // dZ_l BF16 [Bp][dims[l+1]]
     __nv_bfloat16 *t_a = nullptr;                          // the transposed one-hot of the batch
@@ -711,6 +720,7 @@ static int train_setup(Ctx *c, NetGPU &net, int B, const float *const *host_w, c
             // the last layer's gradient has C rounded up to 128 rows (its GEMM's row tile)
             if (!rc) rc = talloc(c, *T, (void **)&T->gw[l], (l == L - 1 ? (O + 127) / 128 * 128 : O) * I * 4);
             if (!rc) rc = talloc(c, *T, (void **)&T->gb[l], O * 4);
+            if (!rc && l >= 1 && l < L - 1) rc = talloc(c, *T, (void **)&T->wt[l], O * I * 2);
             if (!rc && l < L - 1) rc = talloc(c, *T, (void **)&T->act[l], (size_t)Bp * O * 2);
             if (!rc && l < L - 1) rc = talloc(c, *T, (void **)&T->dz[l], (size_t)Bp * O * 2);
         }
@@ -766,7 +776,11 @@ static int train_setup(Ctx *c, NetGPU &net, int B, const float *const *host_w, c
             train_free(c, old);
         }
         net.train = T;
-        // the last layer's stacked parts
+        // W^T copies of the hidden layers >= 1, the last layer's stacked parts
+        for (int l = 1; l < L - 1; ++l) {
+            const int O = net.dims[l + 1], I = net.dims[l];
+            k_write_t<<<(O * I + 255) / 256, 256>>>(T->w[l], O, I, T->wt[l]);
+        }
         k_write_ext<<<(C * net.dims[L - 1] + 255) / 256, 256>>>(T->w[L - 1], C, net.dims[L - 1], T->cs, T->w_ext);
         CUDA_TRY(cudaDeviceSynchronize());
     }
@@ -913,12 +927,11 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
         }
         if (l > 0) {
             // dZ_{l-1} = (dZ_l W_l) * [A_{l-1} > 0]
-            // (W_l [O][I] is the B operand MN-major: the BF16 weights the forward reads)
             const CUtensorMap *mz = bmap(T, T.dz[l], O, T.Bp, kBM);
-            const CUtensorMap *mw = bmap(T, net.w_lp[l], I, O, 64);
+            const CUtensorMap *mw = bmap(T, T.wt[l], O, I, I % 256 == 0 ? 256 : 128);
             if (!mz || !mw) return CBDFS_EDEVICE;
-            rc = (I % 256 == 0) ? gemm_tn<256, 2, false, true>(*mz, *mw, Bp, I, O, T.dz[l - 1], T.act[l - 1], c->d_err, st)
-                                : gemm_tn<128, 2, false, true>(*mz, *mw, Bp, I, O, T.dz[l - 1], T.act[l - 1], c->d_err, st);
+            rc = (I % 256 == 0) ? gemm_tn<256, 2>(*mz, *mw, Bp, I, O, T.dz[l - 1], T.act[l - 1], c->d_err, st)
+                                : gemm_tn<128, 2>(*mz, *mw, Bp, I, O, T.dz[l - 1], T.act[l - 1], c->d_err, st);
             if (rc) return rc;
         }
     }
@@ -964,6 +977,7 @@ static int launch_adam(NetGPU &net, const cbdfs_train_cfg *tc, bool copies_only,
         w.I = I;
         w.w_lp = last ? nullptr : static_cast<__nv_bfloat16 *>(net.w_lp[l]);
         w.Kp = I;
+        w.wt = (l >= 1 && !last) ? T.wt[l] : nullptr;
         w.w_out = last ? net.w32[l] : nullptr;  // the inference head reads the FP32 last layer
         w.split = last ? static_cast<__nv_bfloat16 *>(net.w_split) : nullptr;  // and the tensor-core head its parts
         w.cpad = net.head_cpad;
