@@ -538,8 +538,19 @@ __global__ void __launch_bounds__(256) k_adam_all(const __grid_constant__ AdamPa
             c1 = P.c12[2 * P.ctr[0]];
             c2 = P.c12[2 * P.ctr[0] + 1];
         }
+        // the split partials added in split order; loaded four at a time, so that the loads are
+        // in flight together instead of one after another
         float gg = 0.f;
-        for (int z = 0; z < S.parts; ++z) gg += S.g[z * S.pstride + idx];
+        int z = 0;
+        for (; z + 4 <= S.parts; z += 4) {
+            const float g0 = __ldg(S.g + (size_t)z * S.pstride + idx), g1 = __ldg(S.g + (size_t)(z + 1) * S.pstride + idx);
+            const float g2 = __ldg(S.g + (size_t)(z + 2) * S.pstride + idx), g3 = __ldg(S.g + (size_t)(z + 3) * S.pstride + idx);
+            gg += g0;
+            gg += g1;
+            gg += g2;
+            gg += g3;
+        }
+        for (; z < S.parts; ++z) gg += __ldg(S.g + (size_t)z * S.pstride + idx);
         const float m = P.b1 * S.m[idx] + (1.f - P.b1) * gg;
         const float v = P.b2 * S.v[idx] + (1.f - P.b2) * gg * gg;
         S.m[idx] = m;
