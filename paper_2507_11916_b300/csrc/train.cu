@@ -26,6 +26,7 @@
 #include <cstdio>
 #include <cstring>
 #include <random>
+#include <thread>
 #include <type_traits>
 
 #include "chain.h"
@@ -1213,14 +1214,12 @@ int net_train(cbdfs_ctx *ctx, int net_id, const uint64_t *states, const uint8_t 
         cleanup();
         return fail(CBDFS_EDEVICE, "training set upload");
     }
-    std::vector<uint32_t> perm(n);
-    const auto t0 = std::chrono::steady_clock::now();
-    float loss = 0.f;
-    int64_t steps = 0;
-    for (int ep = 0; ep < tc.epochs && !rc; ++ep) {
-        // epoch order: Fisher-Yates driven by splitmix64(seed + epoch), j = draw mod (i+1)
+    // epoch order: Fisher-Yates driven by splitmix64(seed + epoch), j = draw mod (i+1).  The next
+    // epoch's order is drawn on a host thread while this epoch's steps run, into the other of
+    // two page-locked buffers (a buffer is rewritten once its previous upload has completed)
+    auto make_perm = [n, seed = tc.seed](int ep, uint32_t *perm) {
         for (uint64_t i = 0; i < n; ++i) perm[i] = (uint32_t)i;
-        uint64_t sm = tc.seed + 0x9E3779B97F4A7C15ull * (uint64_t)(ep + 1);
+        uint64_t sm = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(ep + 1);
         for (uint64_t i = n - 1; i > 0; --i) {
             sm += 0x9E3779B97F4A7C15ull;
             uint64_t z = sm;
@@ -1229,10 +1228,45 @@ int net_train(cbdfs_ctx *ctx, int net_id, const uint64_t *states, const uint8_t 
             z ^= z >> 31;
             std::swap(perm[i], perm[z % (i + 1)]);
         }
-        if (cudaMemcpyAsync(d_idx, perm.data(), n * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+    };
+    uint32_t *hperm[2] = {nullptr, nullptr};
+    cudaEvent_t up_ev[2] = {nullptr, nullptr};
+    std::thread drawer;
+    auto perm_cleanup = [&]() {
+        if (drawer.joinable()) drawer.join();
+        cudaStreamSynchronize(st);  // no upload still reads the buffers
+        for (int b = 0; b < 2; ++b) {
+            if (up_ev[b]) cudaEventDestroy(up_ev[b]);
+            if (hperm[b]) cudaFreeHost(hperm[b]);
+        }
+    };
+    for (int b = 0; b < 2; ++b)
+        if (cudaHostAlloc((void **)&hperm[b], n * 4, cudaHostAllocDefault) != cudaSuccess ||
+            cudaEventCreateWithFlags(&up_ev[b], cudaEventDisableTiming) != cudaSuccess) {
+            perm_cleanup();
+            cleanup();
+            return fail(CBDFS_ENOMEM, "page-locked permutation buffers");
+        }
+    const auto t0 = std::chrono::steady_clock::now();
+    make_perm(0, hperm[0]);
+    float loss = 0.f;
+    int64_t steps = 0;
+    for (int ep = 0; ep < tc.epochs && !rc; ++ep) {
+        if (drawer.joinable()) drawer.join();  // this epoch's order is in hperm[ep & 1]
+        if (cudaMemcpyAsync(d_idx, hperm[ep & 1], n * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaEventRecord(up_ev[ep & 1], st) != cudaSuccess ||
             cudaMemsetAsync(d_ctr + 1, 0, sizeof(int), st) != cudaSuccess) {
             rc = fail(CBDFS_EDEVICE, "permutation upload");
             break;
+        }
+        const bool more = ep + 1 < tc.epochs && !(tc.max_steps > 0 && steps + (int64_t)per_epoch >= tc.max_steps);
+        if (more) {
+            // the other buffer was last read by the previous epoch's upload
+            if (ep >= 1 && cudaEventSynchronize(up_ev[(ep + 1) & 1]) != cudaSuccess) {
+                rc = fail(CBDFS_EDEVICE, "permutation upload");
+                break;
+            }
+            drawer = std::thread(make_perm, ep + 1, hperm[(ep + 1) & 1]);
         }
         for (uint64_t k = 0; k < per_epoch && !rc; ++k) {
             if (tc.max_steps > 0 && steps >= tc.max_steps) break;
@@ -1282,6 +1316,7 @@ int net_train(cbdfs_ctx *ctx, int net_id, const uint64_t *states, const uint8_t 
     rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     rep->samples = 0;
     for (int64_t i = 0; i < steps; ++i) rep->samples += std::min<uint64_t>(tc.batch, n);
+    perm_cleanup();
     cleanup();
     if (!rc) {
         int flag = 0;
