@@ -471,11 +471,23 @@ __global__ void k_colsum_part2(const __nv_bfloat16 *__restrict__ X, int n, int J
     if (j >= J) return;
     const int mb = r * chunk, me = min(n, mb + chunk);
     float s0 = 0.f, s1 = 0.f;
-#pragma unroll 8
-    for (int m = mb; m < me; ++m) {
-        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(X + (size_t)m * J + j));
-        s0 += v.x;
-        s1 += v.y;
+    if (me - mb == 64) {
+        // a full chunk: all 64 rows' loads in flight, then the sums in row order
+        uint32_t w[64];
+#pragma unroll
+        for (int q = 0; q < 64; ++q) w[q] = __ldg(reinterpret_cast<const unsigned int *>(X + (size_t)(mb + q) * J + j));
+#pragma unroll
+        for (int q = 0; q < 64; ++q) {
+            const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[q]));
+            s0 += v.x;
+            s1 += v.y;
+        }
+    } else {
+        for (int m = mb; m < me; ++m) {
+            const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(X + (size_t)m * J + j));
+            s0 += v.x;
+            s1 += v.y;
+        }
     }
     part[(size_t)r * J + j] = s0;
     part[(size_t)r * J + j + 1] = s1;
