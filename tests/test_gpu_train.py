@@ -190,3 +190,48 @@ def test_checkpoint_resume_continues_exactly(P, ctx, orc, tmp_path):
     with pytest.raises(P.CbdfsError):
         P.cbdfs_train_load(ctx, b, tmp_path / "bad.ckpt")
     assert all(np.array_equal(x, y) for x, y in zip(P.cbdfs_net_read(ctx, b, dims)[0], Wb))
+
+
+def _fresh_c3(P, ctx):
+    Ws, bs = W.net_weights(**W.NET_C3)
+    return P.cbdfs_net_load(ctx, P.DOM_STP4, Ws, bs, P.PREC_BF16, P.HEAD_CLASSIFIER, 0)
+
+
+def _same_weights(P, ctx, a, b):
+    wa, ba = P.cbdfs_net_read(ctx, a, W.NET_C3["dims"])
+    wb, bb = P.cbdfs_net_read(ctx, b, W.NET_C3["dims"])
+    return all(np.array_equal(x, y) for x, y in zip(wa + ba, wb + bb))
+
+
+def test_step_graph_matches_eager_steps(P, ctx):
+    # a full batch is one replay of the captured step; a batch smaller than the configured
+    # batch size runs the same kernels launched one by one.  512 states with batch 512 (three
+    # replays) and with batch 640 (three eager steps of the same 512 rows in the same
+    # permutations) must end bit-identical
+    s = W.random_stp_states(4, 512, 41)
+    labels = (W.splitmix64_array(42, 512) % np.uint64(81)).astype(np.uint8)
+    a, b = _fresh_c3(P, ctx), _fresh_c3(P, ctx)
+    ra = P.net_train(ctx, a, s, labels, batch=512, epochs=3, lr=1e-3, seed=7)
+    rb = P.net_train(ctx, b, s, labels, batch=640, epochs=3, lr=1e-3, seed=7)
+    assert ra["steps"] == rb["steps"] == 3
+    assert ra["last_loss"] == rb["last_loss"]
+    assert _same_weights(P, ctx, a, b)
+    assert P.cbdfs_device_status(ctx) == 0
+
+
+def test_epochs_with_a_partial_batch_are_deterministic(P, ctx):
+    # 1124 states in batches of 512: two replays and one partial eager step per epoch, the next
+    # epoch's order drawn while the current one runs; two runs end bit-identical, and a step
+    # limit stops inside an epoch
+    s = W.random_stp_states(4, 1124, 43)
+    labels = (W.splitmix64_array(44, 1124) % np.uint64(81)).astype(np.uint8)
+    a, b, c = _fresh_c3(P, ctx), _fresh_c3(P, ctx), _fresh_c3(P, ctx)
+    ra = P.net_train(ctx, a, s, labels, batch=512, epochs=3, lr=1e-3, seed=9)
+    rb = P.net_train(ctx, b, s, labels, batch=512, epochs=3, lr=1e-3, seed=9)
+    assert ra["steps"] == rb["steps"] == 9
+    assert np.isfinite(ra["last_loss"]) and ra["last_loss"] < ra["first_loss"]
+    assert _same_weights(P, ctx, a, b)
+    rc = P.net_train(ctx, c, s, labels, batch=512, epochs=3, lr=1e-3, seed=9, max_steps=4)
+    assert rc["steps"] == 4
+    assert not _same_weights(P, ctx, a, c)
+    assert P.cbdfs_device_status(ctx) == 0
