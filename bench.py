@@ -441,6 +441,35 @@ def cube_search_leg(P, args):
         for n in ("bf16", "fp8"):
             res[f"{n}_over_fp32_nodes"] = res[n]["expanded_per_s"] / max(res["fp32"]["expanded_per_s"], 1e-9)
         out["fixed_tree"] = res
+        # deeper scrambles (14-16 turns), which take far longer than a bench run to solve: the
+        # same fixed tree, each search time-boxed, nodes/s over the box, equal counts over the
+        # completed iterations
+        deep = [P.cbdfs_apply_moves(P.DOM_RC3, W.rc_goal(), W.rc_scramble(t, W.seed_for(W.TAG_C2, 200 + i)))
+                for i, t in enumerate((14, 15, 16, 16))]
+        box = args.cube_box
+        dres, dits = {"instances": "4 seeded cube scrambles of 14, 15, 16 and 16 turns", "time_box_s_per_instance": box}, {}
+        for name, hid in hids.items():
+            exp = nb = ev = 0
+            secs = busy = 0.0
+            dits[name] = []
+            for st in deep:
+                r = P.cbdfs_solve(ctx, P.DOM_RC3, st, P.ALGO_IDA, hid, partial_ok=True, time_limit_s=box,
+                                  fixed_tree_heur=pid, **cfg)
+                exp += r["expanded"]
+                secs += r["seconds"]
+                nb += r["batches"]
+                ev += r["evaluated"]
+                busy += r["gpu_busy_s"]
+                dits[name].append([tuple(it) for it in (r["iters"] if r["status"] == 0 else r["iters"][:-1])])
+            dres[name] = {"expanded_per_s": exp / secs, "expanded": exp, "avg_batch": ev / max(nb, 1),
+                          "gpu_busy_frac": busy / secs}
+        dres["equal_counts"] = all(
+            dits[n][i][:m] == dits["bf16"][i][:m] for i in range(len(deep)) for n in hids
+            for m in [min(len(dits[n][i]), len(dits["bf16"][i]))])
+        dres["completed_iterations"] = [len(x) for x in dits["bf16"]]
+        for n in ("bf16", "fp8"):
+            dres[f"{n}_over_fp32_nodes"] = dres[n]["expanded_per_s"] / max(dres["fp32"]["expanded_per_s"], 1e-9)
+        out["fixed_tree_deep"] = dres
         return out
     finally:
         P.cbdfs_destroy(ctx)
@@ -1280,6 +1309,8 @@ def main():
     ap.add_argument("--search-box", type=float, default=0.3,
                     help="time box per instance of the 100-start search leg (s)")
     ap.add_argument("--search-repeats", type=int, default=3)
+    ap.add_argument("--cube-box", type=float, default=0.5,
+                    help="time box per instance of the 14-16-turn cube fixed-tree searches (s)")
     ap.add_argument("--ida-cmp-starts", type=int, default=3,
                     help="200-move starts tried for the trained network vs PDB comparison")
     ap.add_argument("--ida-cmp-cap", type=float, default=6.0, help="the PDB search's cap (s); network 3x, DIV 4x")
