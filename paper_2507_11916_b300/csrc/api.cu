@@ -321,9 +321,15 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     P.nh = nh;
     for (int l = 0; l <= L; ++l) P.dims[l] = net.dims[l];
     uint32_t rows_pad = (n + kBM - 1) / kBM * kBM;
-    // small batches: 64-wide tiles, so that a layer's tiles spread over more CTAs (the head
-    // partials then need four times the floats per row, within the slot's allocation)
-    const int bn = rows_pad / kBM <= kChainSmallMBlocks && 4 * rows_pad <= c->max_batch_pad ? kChainBNSmall : kChainBN;
+    // small batches: 64-wide tiles, so that a layer's tiles spread over more CTAs, while the
+    // widest layer's 64-wide tiles are at most 4/3 of the SM count (beyond that the extra
+    // epilogues cost more than the spread gains: 15-puzzle network, 1024 wide, up to 1536
+    // states; cube network, 2048 wide, up to 768); the head partials then need four times the
+    // floats per row, within the slot's allocation
+    int widest = 0;
+    for (int l = 0; l < nh; ++l) widest = std::max(widest, net.dims[l + 1]);
+    const bool small = (int)(rows_pad / kBM) * (widest / kChainBNSmall) <= c->num_sms + c->num_sms / 3;
+    const int bn = small && 4 * rows_pad <= c->max_batch_pad ? kChainBNSmall : kChainBN;
     // larger batches: CTA pairs (two row blocks per tile, tcgen05 cta_group::2), when the
     // batch padded to 256 rows fits the slot and the device holds every pair at once
     const uint32_t rows_pair = (n + 2 * kBM - 1) / (2 * kBM) * (2 * kBM);

@@ -6,7 +6,6 @@ namespace cbdfs {
 
 constexpr int kChainBN = 256;     // output columns of a tile (one TMEM accumulator)
 constexpr int kChainBNSmall = 64; // the same for small batches (more tiles in flight per layer)
-constexpr int kChainSmallMBlocks = 2;  // batches of at most this many 128-state row blocks
 constexpr int kChainStages = 4;
 constexpr int kChainPairStages = 6;  // CTA pairs: 32 KB k-block stages (A rows + half the weights)
 constexpr int kChainPairMinMBlocks = 8;  // CTA pairs from this many 128-state row blocks on
