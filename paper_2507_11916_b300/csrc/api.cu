@@ -309,10 +309,13 @@ static int mark(Slot &s, cudaStream_t st) {
     return CBDFS_OK;
 }
 
-// the whole network in one persistent launch (mlp_chain.cu)
+// the whole network in one persistent launch (mlp_chain.cu).  outs (training's forward pass):
+// every hidden layer l stored to outs[l] ([out_rows][dims[l+1]] BF16) instead of the slot's
+// two alternating buffers, and no last layer (the caller runs it)
 static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint64_t *d_states,
                      const uint8_t *d_g, uint32_t bound, uint32_t n, uint8_t *d_h, uint32_t *d_mask,
-                     uint32_t *d_minf, float *d_y, cudaStream_t st) {
+                     uint32_t *d_minf, float *d_y, cudaStream_t st, void *const *outs = nullptr,
+                     uint32_t out_rows = 0) {
     const bool fp8 = net.prec == CBDFS_PREC_FP8;
     const int eb = fp8 ? 1 : 2;
     const int L = net.L, nh = L - 1;
@@ -334,7 +337,7 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     // batch padded to 256 rows fits the slot and the device holds every pair at once
     const uint32_t rows_pair = (n + 2 * kBM - 1) / (2 * kBM) * (2 * kBM);
     const bool pair = net.has_w128 && bn == kChainBN && rows_pad / kBM >= kChainPairMinMBlocks && rows_pair <= c->max_batch_pad &&
-                      (c->num_sms & 1) == 0 && chain_pairs_fit(c->num_sms);
+                      (!outs || rows_pair <= out_rows) && (c->num_sms & 1) == 0 && chain_pairs_fit(c->num_sms);
     if (pair) rows_pad = rows_pair;
     P.mblocks = rows_pad / kBM;
     P.rows_pad = rows_pad;
@@ -342,11 +345,15 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     const int seq_mblocks = pair ? P.mblocks / 2 : P.mblocks;  // row blocks (pairs) in the tile sequence
     int max_tiles = 0;
     P.tile_start[0] = 0;
-    P.fused_head = net.dims[L] <= kMaxHeadC && !net.head_cpad;
+    P.fused_head = !outs && net.dims[L] <= kMaxHeadC && !net.head_cpad;
     P.bf16_store_layer = !P.fused_head && fp8 ? nh - 1 : -1;
     for (int l = 0; l < nh; ++l) {
         maps.w[l] = bn == kChainBNSmall ? net.tm_w64[l] : pair ? net.tm_w128[l] : net.tm_w[l];
-        if (l > 0) {
+        if (l > 0 && outs) {
+            if (int rc = make_tmap_2d(&maps.a[l], outs[l - 1], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                                      (uint64_t)net.dims[l], out_rows, 64, kBM))
+                return rc;
+        } else if (l > 0) {
             const CUtensorMap *m = act_map(s, c, (l - 1) & 1, net.dims[l], eb);
             if (!m) return CBDFS_EDEVICE;
             maps.a[l] = *m;
@@ -355,7 +362,11 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
             if (!m) return CBDFS_EDEVICE;
             maps.a[0] = *m;
         }
-        if (l < nh - 1 || !P.fused_head) {  // stored activations: 32 x 32 boxes, by TMA stores
+        if (outs) {
+            if (int rc = make_tmap_2d(&maps.o[l], outs[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                                      (uint64_t)net.dims[l + 1], out_rows, 32, 32, CU_TENSOR_MAP_SWIZZLE_64B))
+                return rc;
+        } else if (l < nh - 1 || !P.fused_head) {  // stored activations: 32 x 32 boxes, by TMA stores
             const CUtensorMap *m = act_store_map(s, c, l & 1, net.dims[l + 1], l == P.bf16_store_layer ? 2 : eb);
             if (!m) return CBDFS_EDEVICE;
             maps.o[l] = *m;
@@ -392,7 +403,7 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
     P.y = d_y;
     P.err = c->d_err;
     P.wait_ns = c->wait_ns;
-    P.hold_mblock = c->hold_mblock.exchange(-1);
+    P.hold_mblock = outs ? -1 : c->hold_mblock.exchange(-1);
     const int grid = pair ? 2 * std::min(c->num_sms / 2, max_tiles) : std::min(c->num_sms, max_tiles);
     if (s.trace) {
         P.trace = s.trace;
@@ -401,7 +412,7 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
         CUDA_TRY(cudaMemsetAsync(s.trace, 0, sizeof(unsigned long long) * grid * s.trace_tiles * 8, st));
     }
     int rc = chain_launch(domain, fp8, bn, pair, maps, P, grid, st);
-    if (rc || (rc = mark(s, st)) || P.fused_head) return rc;
+    if (rc || (rc = mark(s, st)) || P.fused_head || outs) return rc;
     // the last layer over the stored BF16 activations of the last hidden layer: on the tensor
     // cores (split FP32 weights) for a prepared classifier head, else FP32 on the CUDA cores
     if (net.head_cpad) {
@@ -433,6 +444,18 @@ static int run_chain(Ctx *c, Slot &s, const NetGPU &net, int domain, const uint6
                   d_y, st);
     }
     return rc ? rc : mark(s, st);
+}
+
+// Training's forward pass through the fused chain: every hidden layer of a BF16 network stored
+// to outs[l] (out_rows rows); CBDFS_ENOTFOUND when the chain does not take this network or
+// slot (the caller then runs the layers one by one)
+int chain_forward_store(Ctx *c, Slot &s, const NetGPU &net, const uint64_t *d_states, uint32_t n,
+                        void *const *outs, uint32_t out_rows, cudaStream_t st) {
+    if (net.prec != CBDFS_PREC_BF16 || net.groups > 1 || !chain_ok(net) || !s.counters || !s.onehot ||
+        n > out_rows)
+        return CBDFS_ENOTFOUND;
+    return run_chain(c, s, net, net.domain, d_states, nullptr, 255, n, nullptr, nullptr, nullptr, nullptr, st, outs,
+                     out_rows);
 }
 
 int run_eval(Ctx *c, Slot &s, int heur_id, int domain, const uint64_t *d_states, const uint8_t *d_g,

@@ -39,6 +39,9 @@ int tc_layer(bool first, int domain, bool fp8, bool out_fp8, int bn, const CUten
              int N, const float *bias, void *out, float acc_scale, float out_qscale, int *err,
              cudaStream_t st);
 uint64_t npk(int n, int k);
+// the forward pass through the fused chain, every hidden layer stored (api.cu)
+int chain_forward_store(Ctx *c, Slot &s, const NetGPU &net, const uint64_t *d_states, uint32_t n,
+                        void *const *outs, uint32_t out_rows, cudaStream_t st);
 
 namespace {
 
@@ -839,8 +842,14 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
     const int L = net.L, C = net.dims[L];
     const int Bp = (n + kBM - 1) / kBM * kBM;
     int rc;
-    // forward through the tensor-core layers
-    for (int l = 0; l < L - 1; ++l) {
+    // forward through the tensor-core layers: one fused-chain launch storing every hidden layer
+    // where the chain takes the network, else layer by layer
+    void *outs[kMaxLayers];
+    for (int l = 0; l < L - 1; ++l) outs[l] = T.act[l];
+    rc = chain_forward_store(c, c->slots[0], net, T.states, (uint32_t)n, outs, (uint32_t)T.Bp, st);
+    if (rc != CBDFS_OK && rc != CBDFS_ENOTFOUND) return rc;
+    const bool per_layer = rc == CBDFS_ENOTFOUND;
+    for (int l = 0; per_layer && l < L - 1; ++l) {
         const bool first = l == 0;
         const int K = first ? net.k1pad : net.dims[l];
         const CUtensorMap *tmA = first ? &net.tm_w[0] : bmap(T, T.act[l - 1], K, T.Bp, kBM);
