@@ -496,8 +496,10 @@ __global__ void k_colsum_part2(const __nv_bfloat16 *__restrict__ X, int n, int J
     part[(size_t)r * J + j + 1] = s1;
 }
 
-// sum of per-row losses (one block, fixed order), divided by n
-__global__ void k_mean(const float *__restrict__ v, int n, float *__restrict__ out) {
+// sum of per-row losses (one block, fixed order), divided by n; ctr (a training run): the
+// step and batch counters advance here, after this step's gather has read the batch counter
+// and before its Adam reads the step counter (which then holds the step's number + 1)
+__global__ void k_mean(const float *__restrict__ v, int n, float *__restrict__ out, int *ctr) {
     __shared__ float part[256];
     float s = 0.f;
     for (int i = threadIdx.x; i < n; i += 256) s += v[i];
@@ -507,6 +509,10 @@ __global__ void k_mean(const float *__restrict__ v, int n, float *__restrict__ o
         float t = 0.f;
         for (int i = 0; i < 256; ++i) t += part[i];
         *out = t / (float)n;
+        if (ctr) {
+            ctr[0]++;
+            ctr[1]++;
+        }
     }
 }
 
@@ -529,17 +535,13 @@ struct AdamParams {
     int nseg;
     int copies_only;  // no update: only the copies of the masters as they are (a loaded checkpoint)
     float lr, b1, b2, eps, c1, c2;
-    // optional: c1, c2 of step ctr[0] of a run from a table [2 x steps] (one captured step
-    // serves every step of the run)
+    // optional: c1, c2 of step ctr[0] - 1 of a run from a table [2 x steps] (one captured step
+    // serves every step of the run; k_mean has advanced the counter)
     const float *c12;
     const int *ctr;
 };
 
-// the run's step and batch counters, after a step
-__global__ void k_step_advance(int *ctr) {
-    ctr[0]++;
-    ctr[1]++;
-}
+
 
 __global__ void __launch_bounds__(256) k_adam_all(const __grid_constant__ AdamParams P) {
     int s = 0;
@@ -551,8 +553,8 @@ __global__ void __launch_bounds__(256) k_adam_all(const __grid_constant__ AdamPa
     if (!P.copies_only) {
         float c1 = P.c1, c2 = P.c2;
         if (P.c12) {
-            c1 = P.c12[2 * P.ctr[0]];
-            c2 = P.c12[2 * P.ctr[0] + 1];
+            c1 = P.c12[2 * (P.ctr[0] - 1)];
+            c2 = P.c12[2 * (P.ctr[0] - 1) + 1];
         }
         // the split partials added in split order; loaded four at a time, so that the loads are
         // in flight together instead of one after another
@@ -837,7 +839,7 @@ static int colsum(const T *X, int n, int J, float *part, size_t part_floats, flo
 // forward + loss + backward on the batch already in T.states / T.labels (n rows).  sum: every
 // gradient summed into gw / gb; otherwise the partials stay where gw_src / gb_src say (the
 // training step's Adam adds them)
-static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t st, bool sum) {
+static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t st, bool sum, int *ctr = nullptr) {
     TrainState &T = *net.train;
     const int L = net.L, C = net.dims[L];
     const int Bp = (n + kBM - 1) / kBM * kBM;
@@ -882,7 +884,7 @@ static int train_fwd_bwd(Ctx *c, NetGPU &net, int n, int loss_kind, cudaStream_t
             T.act[L - 2], KL, 1, T.w[L - 1], 1, KL, n, C, KL, T.logits, T.b[L - 1]);
     }
     k_loss<<<(Bp + 7) / 8, 256, 0, st>>>(T.logits, T.labels, n, Bp, C, loss_kind, T.dzl, T.row_loss, T.dz_ext, T.cs);
-    k_mean<<<1, 256, 0, st>>>(T.row_loss, n, T.loss);
+    k_mean<<<1, 256, 0, st>>>(T.row_loss, n, T.loss, ctr);
     // last layer backward: dW[c][k] = sum_m dZ[m][c] A[m][k] with dZ = D1 + D2 (BF16 parts, the
     // products exact, FP32 accumulation) as one split-K tensor-core GEMM over 2 Bp columns;
     // db = column sums of dZ; dZ_prev = (dZ W) * [A > 0] in BF16
@@ -1218,16 +1220,12 @@ int net_train(cbdfs_ctx *ctx, int net_id, const uint64_t *states, const uint8_t 
             return fail(CBDFS_EDEVICE, "training counters");
         }
     }
-    // one step on the stream: rows from the permutation at the batch counter, forward,
-    // backward, Adam at the step counter, then both counters advance
+    // one step on the stream: rows from the permutation at the batch counter, forward, loss
+    // (whose mean kernel advances both counters), backward, Adam at the step counter
     auto enqueue_step = [&](uint32_t bn) -> int {
         k_gather<<<(bn + 255) / 256, 256, 0, st>>>(d_states, d_labels, d_idx, d_ctr, tc.batch, w, bn, T.states, T.labels);
-        int r = train_fwd_bwd(c, *net, (int)bn, tc.loss, st, false);
+        int r = train_fwd_bwd(c, *net, (int)bn, tc.loss, st, false, d_ctr);
         if (!r) r = launch_adam(*net, &tc, false, st, d_c12, d_ctr);
-        if (!r) {
-            k_step_advance<<<1, 1, 0, st>>>(d_ctr);
-            if (cudaGetLastError() != cudaSuccess) r = fail(CBDFS_EDEVICE, "training step launch");
-        }
         return r;
     };
     if (cudaMemcpy(d_states, states, n * 8 * w, cudaMemcpyHostToDevice) != cudaSuccess ||
