@@ -62,6 +62,10 @@ k_head_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // launched as a programmatic dependent of the kernel that stores the activations (the fused
+    // chain): the set-up above overlaps that kernel's end; nothing it writes is read before
+    // here, where the whole grid before this one has completed and its writes are visible
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     if (warp == 0) {
         if (lane == 0) {
@@ -203,8 +207,20 @@ int launch(const CUtensorMap &tmA, const CUtensorMap &tmW, const HeadTcParams &P
     CUDA_TRY(cudaFuncSetAttribute(k_head_tc<DOMAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     uint32_t cols = 32;
     while ((int)cols < P.cpad) cols <<= 1;
-    k_head_tc<DOMAIN><<<dim3(rows_pad / kBM, P.groups > 1 ? P.groups : 1), kHtThreads, smem, st>>>(tmA, tmW, P, cols);
-    CUDA_TRY(cudaGetLastError());
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(rows_pad / kBM, P.groups > 1 ? P.groups : 1);
+    cfg.blockDim = dim3(kHtThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    // programmatic dependent launch: the CTAs may start (and set up) while the previous kernel
+    // on the stream ends; they wait for it (griddepcontrol.wait) before reading its output
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_head_tc<DOMAIN>, tmA, tmW, P, cols);
+    if (e != cudaSuccess) return fail(CBDFS_EDEVICE, "head launch: %s", cudaGetErrorString(e));
     return CBDFS_OK;
 }
 

@@ -678,6 +678,9 @@ k_chain(const __grid_constant__ ChainMaps maps, const __grid_constant__ ChainPar
         if (PAIR) tmem_dealloc_pair(tmem, 2 * BN);
         else tmem_dealloc(tmem, 2 * BN);
     }
+    // a programmatic dependent (the separate head kernel) may be scheduled once every CTA has
+    // got here; it still waits for this grid's completion before reading what it stored
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 }  // namespace
