@@ -2,8 +2,8 @@
 //
 // Every hidden layer is cut into 128-state x 256-output tiles; the tiles of all layers form
 // one sequence, layer by layer and, inside a layer, row block by row block.  Each CTA (one
-// per SM, all resident: a cooperative launch, or a cluster launch of CTA pairs that the
-// device holds at once) takes tiles i, i+G, i+2G, ... (CTA pairs: pair tiles, see k_chain).  A tile
+// per SM, all resident: a cooperative launch, of single CTAs or of CTA pairs) takes tiles
+// i, i+G, i+2G, ... (CTA pairs: pair tiles, see k_chain).  A tile
 // of layer l+1 for row block m starts as soon as every tile of layer l for that row block is
 // stored: the epilogue counts finished tiles per (layer, row block) with a release atomic and
 // the producer waits for the count with a bounded acquire poll.  Dependencies only point to
@@ -33,6 +33,8 @@
 // Every wait is bounded (ChainParams::wait_ns of %globaltimer, 2 s unless the context sets
 // another bound) and reports through the error flag.
 #include <cuda_fp8.h>
+
+#include <cstdlib>
 
 #include <map>
 #include <mutex>
@@ -718,22 +720,34 @@ static int launch_t(const ChainMaps &maps, const ChainParams &P, int grid, cudaS
     cfg.blockDim = dim3(kChainThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    // one CTA per SM, all resident at once: a cooperative launch for single CTAs; CTA pairs
-    // are a plain cluster launch, for which chain_pairs_fit has checked that the device holds
-    // every pair at once (a launch queued behind another starts its CTAs as the earlier
-    // launch's retire, and the earlier launch never waits on the later one)
-    cudaLaunchAttribute attr[1];
+    // one CTA per SM, all resident at once: a cooperative launch (CTA pairs: with a cluster
+    // dimension of 2; chain_pairs_fit has checked that the device holds every pair).  A plain
+    // cluster launch can start only some of its pairs while other work holds SMs; its CTAs
+    // then wait on tiles of pairs not yet started, and a full-device cooperative launch queued
+    // on another stream waits for those SMs: neither proceeds until the bounded waits run out.
+    // CBDFS_PLAIN_CLUSTER_LAUNCH=1 (read once) launches pairs without the cooperative attribute
+    // for profilers that cannot replay a cooperative cluster launch; only for runs with one
+    // launch in flight at a time
+    static const bool plain_pairs = [] {
+        const char *v = getenv("CBDFS_PLAIN_CLUSTER_LAUNCH");
+        return v && v[0] == '1';
+    }();
+    cudaLaunchAttribute attr[2];
+    int na = 0;
     if (PAIR) {
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-    } else {
-        attr[0].id = cudaLaunchAttributeCooperative;
-        attr[0].val.cooperative = 1;
+        attr[na].id = cudaLaunchAttributeClusterDimension;
+        attr[na].val.clusterDim.x = 2;
+        attr[na].val.clusterDim.y = 1;
+        attr[na].val.clusterDim.z = 1;
+        ++na;
+    }
+    if (!PAIR || !plain_pairs) {
+        attr[na].id = cudaLaunchAttributeCooperative;
+        attr[na].val.cooperative = 1;
+        ++na;
     }
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = na;
     const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, P);
     if (e != cudaSuccess) return fail(CBDFS_EDEVICE, "chain launch: %s", cudaGetErrorString(e));
     return CBDFS_OK;

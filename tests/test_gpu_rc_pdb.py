@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from helpers import PREC
+from helpers import PREC, fp8_act_scales
 
 pytestmark = pytest.mark.gpu
 
@@ -121,3 +121,33 @@ def test_ida_with_the_corner_table_and_the_fixed_tree(P, ctx, orc, table, pid):
         # the network ran on the batches too (the initial partition's nodes are evaluated once,
         # while `generated` counts them in every iteration)
         assert f["batches"] > 0 and f["evaluated"] > 0
+
+
+def test_fixed_tree_with_batches_in_flight_on_several_slots(P, orc):
+    # 10-turn scrambles searched with four slots and 16 threads: batches of every size class are
+    # in flight at once, so chain launches of both tile widths and of CTA pairs (batches of 8 or
+    # more row blocks) meet the heads and gathers of other slots on the device.  Every chain
+    # launch must have all its CTAs resident (a cooperative launch): a launch only partly
+    # started can wait on tiles of CTAs that never start while a full-device launch queued on
+    # another stream waits for its SMs.  Short device waits make such a stall an error here.
+    ctx = P.cbdfs_create(0, max_batch=8192, n_slots=4, device_wait_ns=300_000_000)
+    try:
+        dpid = P.cbdfs_pdb_load(ctx, P.DOM_RC3, [list(range(8))])
+        Ws, bs = W.net_weights(**W.NET_C2)
+        scales = fp8_act_scales(orc, P.DOM_RC3, Ws, bs, W.random_rc_states(1024, 77))
+        nets = {"bf16": P.cbdfs_net_load(ctx, P.DOM_RC3, Ws, bs, P.PREC_BF16, P.HEAD_CLASSIFIER, 0),
+                "fp8": P.cbdfs_net_load(ctx, P.DOM_RC3, Ws, bs, P.PREC_FP8, P.HEAD_CLASSIFIER, 0,
+                                        act_scales=scales)}
+        starts = [P.cbdfs_apply_moves(P.DOM_RC3, W.rc_goal(), W.rc_scramble(10, W.seed_for(W.TAG_C2, 100 + i)))
+                  for i in range(4)]
+        want = [P.cbdfs_solve(ctx, P.DOM_RC3, s, P.ALGO_IDA, dpid, threads=16, work_num=256, batch=4096,
+                              timeout_us=500, time_limit_s=60.0) for s in starts]
+        for name, nid in nets.items():
+            for s, w in zip(starts, want):
+                r = P.cbdfs_solve(ctx, P.DOM_RC3, s, P.ALGO_IDA, nid, threads=16, work_num=256, batch=4096,
+                                  timeout_us=500, time_limit_s=60.0, fixed_tree_heur=dpid)
+                assert r["cost"] == w["cost"] == 10, name
+                assert r["iters"] == w["iters"], name
+            assert P.cbdfs_device_status(ctx) == 0, name
+    finally:
+        P.cbdfs_destroy(ctx)
