@@ -383,6 +383,11 @@ def search_c1_leg(P, ctx, hids, args):
         its[:m] == runs_i[0][:m] for runs_i in done.values() for its in runs_i
         for m in [min(len(its), len(runs_i[0]))])
     out["completed_iterations_per_instance"] = statistics.median(len(r[0]) for r in done.values())
+    # a time-boxed search and a device wait that ran out both end in ETIMEDOUT: the device
+    # status tells them apart (0: no wait ran out)
+    out["device_status"] = P.cbdfs_device_status(ctx)
+    if out["device_status"]:
+        print(f"search: device status {out['device_status']}", file=sys.stderr)
     if "fp32" in out:
         for prec in ("bf16", "fp8"):
             if prec in out:
@@ -467,6 +472,11 @@ def cube_search_leg(P, args):
             dits[n][i][:m] == dits["bf16"][i][:m] for i in range(len(deep)) for n in hids
             for m in [min(len(dits[n][i]), len(dits["bf16"][i]))])
         dres["completed_iterations"] = [len(x) for x in dits["bf16"]]
+        # a time-boxed search and a device wait that ran out both end in ETIMEDOUT: the device
+        # status tells them apart (0: no wait ran out)
+        out["device_status"] = P.cbdfs_device_status(ctx)
+        if out["device_status"]:
+            print(f"cube search: device status {out['device_status']}", file=sys.stderr)
         for n in ("bf16", "fp8"):
             dres[f"{n}_over_fp32_nodes"] = dres[n]["expanded_per_s"] / max(dres["fp32"]["expanded_per_s"], 1e-9)
         out["fixed_tree_deep"] = dres
