@@ -25,6 +25,11 @@
  *   - Heuristic values are uint8; the goal state always gets h = 0.
  *   - A context is bound to one device.  heur_submit_batch and cbdfs_solve may be called
  *     from several threads at once on one context; the other calls may not.
+ *   - Environment: CBDFS_PLAIN_CLUSTER_LAUNCH=1 (read once per process) launches the fused
+ *     network kernel's CTA pairs without the cooperative attribute, for profilers that cannot
+ *     replay a cooperative cluster launch.  Use it only where one evaluation is in flight at a
+ *     time: a partly started plain launch can stall against a launch on another stream until
+ *     the device waits run out (CBDFS_ETIMEDOUT).
  */
 #ifndef CBDFS_H
 #define CBDFS_H
