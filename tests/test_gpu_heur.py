@@ -126,7 +126,7 @@ def test_c0_fp32_regression(P, ctx, orc, n):
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
-@pytest.mark.parametrize("n", [1, 31, 129, 2000])
+@pytest.mark.parametrize("n", [1, 31, 129, 2000, 5000])
 def test_c0_chain_8puzzle(P, ctx, orc, prec, n):
     # the 8-puzzle network 81-256-256-1 in the fused chain (the one-hot rows 81 wide, padded to
     # 128; 16-row pre-pass units), against the oracle on the same rounded weights
@@ -177,8 +177,9 @@ def test_c1_regression_without_md_exposes_rounding(P, ctx, orc):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
-@pytest.mark.parametrize("n", [1, 129, 1000])
+@pytest.mark.parametrize("n", [1, 129, 700, 1000])
 def test_c2_classifier(P, ctx, orc, prec, n):
+    # 700 states: six row blocks of 64-wide tiles (192 per 2048-wide layer), 1000: CTA pairs
     Ws, bs, hid = _net(P, ctx, W.NET_C2, P.DOM_RC3, prec, P.HEAD_CLASSIFIER, 0)
     s = W.random_rc_states(n, 60 + n)
     s[0] = W.rc_goal()
@@ -221,7 +222,7 @@ def c1_md_plus(orc):
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
-@pytest.mark.parametrize("n", [1, 129, 1000, 8192])
+@pytest.mark.parametrize("n", [1, 129, 1000, 1500, 8192])
 def test_c1_network_decides_h(P, ctx, orc, c1_md_plus, prec, n):
     Ws, bs, sc = c1_md_plus
     kw = {"act_scales": sc} if prec == "fp8" else {}
@@ -287,7 +288,7 @@ def test_c1_fp8(P, ctx, orc, n):
     print(f"c1 fp8 n={n}: per-logit error vs plain float64 {logit_ratio(y, y64, 'fp8'):.2f} x tolerance (reported)")
 
 
-@pytest.mark.parametrize("n", [129, 1000])
+@pytest.mark.parametrize("n", [129, 700, 1000])
 def test_c2_fp8(P, ctx, orc, n):
     Ws, bs = W.net_weights(**W.NET_C2)
     sc = fp8_act_scales(orc, 2, Ws, bs, W.random_rc_states(4096, 12))
